@@ -1,0 +1,329 @@
+"""CPU oracle for the GKBA + second-Born hot path (FP64 / complex128).
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import or call
+this package: only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+CPU-baseline leg (``cpu_baseline`` / ``--impl reference``) use it.  It shares
+no code with the CUDA path; both sides take their inputs from ``gkba_inputs``.
+
+Every function restates one passage of Tuovinen, Covito & Sentef,
+"Efficient computation of the second-Born self-energy using tensor-contraction
+operations" (arXiv:1905.01180).  Plain definitions are written out as such;
+a library primitive (``numpy.einsum`` on two operands, ``numpy.linalg.eigh``)
+serves as one step where the paper itself names that step.  Units of the
+same formula are batched along a leading axis, nothing else is reordered.
+
+Notation (Sec. III): for the self-energy S(G, Gbar) the first argument is
+G = G^{<>}(t, t') and the second Gbar = G^{><}(t', t).
+
+Readings of the paper that the oracle fixes (each is pinned by a test in
+``tests/test_oracle_*.py``):
+
+* Sigma is Eq. (2bse) with prefactors 2 and -1 and no extra factor i^2;
+  Eq. (2bse) reduces to the Hubbard form Eq. (2b-diag) with exactly these.
+* The lower limit t0 of the HF propagator in Eq. (prop) is read as t'
+  (otherwise G^R(t, t) != -i); T(t_n, t_k) = U_{n-1} ... U_k.
+* The collision integral I(t) is the first line of Eq. (collint); the second
+  line is its adjoint, so the equation of motion uses I + I^dagger.
+* The time integral in Eq. (collint) is the trapezoid rule over t_0 .. t_n.
+* The time stepper is Heun's method with the propagator built from the
+  average of h_HF at both ends of the step (the paper used no
+  predictor-corrector; a second-order scheme is required here).
+* Spin-restricted: rho, I and Sigma are per spin (Sec. II).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "sigma_loops",
+    "sigma_bruteforce",
+    "sigma_paper",
+    "sigma_independent",
+    "sigma_hubbard",
+    "sigma_symmetric",
+    "sigma_bubble",
+    "sigma_exchange_diag",
+    "gkba_greens",
+    "self_energies",
+    "trapezoid_weights",
+    "collision",
+    "hf_self_energy",
+    "expm_hermitian",
+    "Propagation",
+    "propagate",
+    "energy",
+]
+
+# --------------------------------------------------------------------------
+# Second-Born self-energy, Sec. III
+# --------------------------------------------------------------------------
+
+
+def sigma_loops(v, G, Gb):
+    """Eq. (2bse) as eight explicit Python loops (use at N <= 3 only).
+
+    Sigma_ij = 2 sum v_irpn v_mqsj G_nm Gb_sr G_pq
+             -   sum v_irpn v_mqsj G_nq Gb_sr G_pm
+    """
+    N = G.shape[0]
+    S = np.zeros((N, N), np.complex128)
+    for i in range(N):
+        for j in range(N):
+            acc = 0.0 + 0.0j
+            for m in range(N):
+                for n in range(N):
+                    for p in range(N):
+                        for q in range(N):
+                            for r in range(N):
+                                for s in range(N):
+                                    vv = v[i, r, p, n] * v[m, q, s, j]
+                                    acc += vv * (2.0 * G[n, m] * Gb[s, r] * G[p, q]
+                                                 - G[n, q] * Gb[s, r] * G[p, m])
+            S[i, j] = acc
+    return S
+
+
+def sigma_bruteforce(v, G, Gb):
+    """Eq. (2bse) summed over all eight indices at once (N^8; N <= 6).
+
+    ``optimize=False`` makes numpy iterate the full index space directly.
+    G, Gb may carry a leading batch axis.
+    """
+    if G.ndim == 3:
+        return np.stack([sigma_bruteforce(v, g, gb) for g, gb in zip(G, Gb)])
+    d = np.einsum("irpn,mqsj,nm,sr,pq->ij", v, v, G, Gb, G, optimize=False)
+    x = np.einsum("irpn,mqsj,nq,sr,pm->ij", v, v, G, Gb, G, optimize=False)
+    return 2.0 * d - x
+
+
+def sigma_paper(v, G, Gb):
+    """The paper's N^5 contraction path, Eq. (2b-opt) / Fig. 2.
+
+    T1_nqsj = sum_m v_mqsj G_nm
+    T2_ispn = sum_r v_irpn Gb_sr
+    T3_isqn = sum_p G_pq T2_ispn
+    Sigma_ij = sum_nqs (2 T1_nqsj T3_isqn - T1_qnjs T3_isnq)
+    The exchange term re-uses T1 with permuted indices, which relies on the
+    permutation symmetry of Eq. (symmetries).  Batched over a leading axis.
+    """
+    batched = G.ndim == 3
+    if not batched:
+        G, Gb = G[None], Gb[None]
+    T1 = np.einsum("mqsj,bnm->bnqsj", v, G)
+    T2 = np.einsum("irpn,bsr->bispn", v, Gb)
+    T3 = np.einsum("bpq,bispn->bisqn", G, T2)
+    S = 2.0 * np.einsum("bnqsj,bisqn->bij", T1, T3) - np.einsum("bqnjs,bisnq->bij", T1, T3)
+    return S if batched else S[0]
+
+
+def exchange_folded(v):
+    """w_mqsj = 2 v_mqsj - v_qmsj: the direct (weight 2) and exchange
+    (weight -1) terms of Eq. (2bse) after relabelling m <-> q in the second
+    term.  For v with the symmetry v_ijkl = v_jilk this equals
+    2 v_mqsj - v_mqjs ("w = 2v - v_exch")."""
+    return 2.0 * v - v.transpose(1, 0, 2, 3)
+
+
+def sigma_independent(v, G, Gb):
+    """An N^5 ordering that shares no intermediate with Eq. (2b-opt).
+
+    W1_mqrj = sum_s w_mqsj Gb_sr
+    W2_mprj = sum_q G_pq W1_mqrj
+    W3_nprj = sum_m G_nm W2_mprj
+    Sigma_ij = sum_rpn v_irpn W3_nprj
+    with w from ``exchange_folded`` (no symmetry of v is assumed).
+    Batched over a leading axis.
+    """
+    batched = G.ndim == 3
+    if not batched:
+        G, Gb = G[None], Gb[None]
+    w = exchange_folded(v)
+    W1 = np.einsum("mqsj,bsr->bmqrj", w, Gb)
+    W2 = np.einsum("bpq,bmqrj->bmprj", G, W1)
+    W3 = np.einsum("bnm,bmprj->bnprj", G, W2)
+    S = np.einsum("irpn,bnprj->bij", v, W3)
+    return S if batched else S[0]
+
+
+def sigma_hubbard(U, G, Gb):
+    """Diagonal basis, Eq. (2b-diag): Sigma_ij = U_i U_j G_ij Gb_ji G_ij
+    for v_ijkl = U_i delta_ij delta_ik delta_il."""
+    return np.outer(U, U) * G * Gb.T * G
+
+
+def sigma_symmetric(V, G, Gb):
+    """Symmetric basis, Eq. (2b-symm), for v_ijkl = V_ij delta_il delta_jk:
+    Sigma_ij = 2 sum_kl V_ik V_jl G_ij Gb_lk G_kl - sum_kl V_ik V_jl G_il Gb_lk G_kj."""
+    b = 2.0 * np.einsum("ik,jl,ij,lk,kl->ij", V, V, G, Gb, G, optimize=False)
+    x = np.einsum("ik,jl,il,lk,kj->ij", V, V, G, Gb, G, optimize=False)
+    return b - x
+
+
+def sigma_bubble(V, G, Gb):
+    """Bubble one-liner, Eq. (bubble-contract):
+    Sigma^b = 2 G o [(V x {[V x (Gb^T o G)]^T})^T]."""
+    inner = V @ (Gb.T * G)
+    return 2.0 * G * (V @ inner.T).T
+
+
+def sigma_exchange_diag(V, G, Gb):
+    """Diagonal of the exchange term, Eq. (x-contract):
+    Sigma^x_ii = -{(V o G) x [Gb x (V^T o G)]}_ii."""
+    return -np.diag((V * G) @ (Gb @ (V.T * G)))
+
+
+# --------------------------------------------------------------------------
+# GKBA reconstruction and collision integral, Sec. II
+# --------------------------------------------------------------------------
+
+
+def gkba_greens(T, rho):
+    """Eqs. (gkba), (prop) and G^>(t,t) = -i + G^<(t,t), for t >= t_k:
+
+    G^<(t, t_k) =  i T rho_k          G^>(t, t_k) = -i T (1 - rho_k)
+    G^<(t_k, t) = -[G^<(t, t_k)]^dag  G^>(t_k, t) = -[G^>(t, t_k)]^dag
+    with T = T(t, t_k) and G^<(t, t) = i rho (rho = -i G^<(t, t), Sec. II).
+    Returns (Gl_tk, Gg_tk, Gl_kt, Gg_kt) batched over k.
+    """
+    N = rho.shape[-1]
+    eye = np.eye(N)
+    Gl_tk = 1j * (T @ rho)
+    Gg_tk = -1j * (T @ (eye - rho))
+    Gl_kt = -np.conj(np.swapaxes(Gl_tk, -1, -2))
+    Gg_kt = -np.conj(np.swapaxes(Gg_tk, -1, -2))
+    return Gl_tk, Gg_tk, Gl_kt, Gg_kt
+
+
+def self_energies(v, T, rho, route="independent"):
+    """Sigma^<(t, t_k) and Sigma^>(t, t_k) from Eq. (2bse) with the GKBA
+    Green's functions (explicit i phases).  Sigma^{<>} = S(G^{<>}(t,t_k),
+    G^{><}(t_k,t)).  ``route`` picks the contraction order."""
+    fn = {"independent": sigma_independent, "paper": sigma_paper,
+          "bruteforce": sigma_bruteforce}[route]
+    Gl_tk, Gg_tk, Gl_kt, Gg_kt = gkba_greens(T, rho)
+    Sl = fn(v, Gl_tk, Gg_kt)
+    Sg = fn(v, Gg_tk, Gl_kt)
+    return Sl, Sg
+
+
+def trapezoid_weights(L, dt):
+    """Trapezoid rule over t_0 .. t_{L-1}: dt/2 at both ends, dt inside;
+    one point spans a zero-length interval and gets weight 0."""
+    w = np.full(L, dt, dtype=np.float64)
+    if L == 1:
+        return np.zeros(1)
+    w[0] = w[-1] = 0.5 * dt
+    return w
+
+
+def collision(v, rho_hist, T_hist, weights, route="independent", chunk=256):
+    """First line of Eq. (collint) with the time integral as a weighted sum:
+
+    I(t) = sum_k c_k [Sigma^>(t,t_k) G^<(t_k,t) - Sigma^<(t,t_k) G^>(t_k,t)]
+
+    rho_hist[k] = rho(t_k), T_hist[k] = T(t, t_k), weights[k] = c_k.
+    """
+    L, N, _ = rho_hist.shape
+    I = np.zeros((N, N), np.complex128)
+    for a in range(0, L, chunk):
+        b = min(L, a + chunk)
+        T, rho, c = T_hist[a:b], rho_hist[a:b], weights[a:b]
+        Gl_tk, Gg_tk, Gl_kt, Gg_kt = gkba_greens(T, rho)
+        fn = {"independent": sigma_independent, "paper": sigma_paper,
+              "bruteforce": sigma_bruteforce}[route]
+        Sl = fn(v, Gl_tk, Gg_kt)
+        Sg = fn(v, Gg_tk, Gl_kt)
+        terms = Sg @ Gl_kt - Sl @ Gg_kt
+        I += np.einsum("k,kij->ij", c, terms)
+    return I
+
+
+def hf_self_energy(v, rho):
+    """(Sigma_HF)_ij = sum_kl (2 v_iklj - v_ikjl) rho_lk (Sec. II)."""
+    return 2.0 * np.einsum("iklj,lk->ij", v, rho) - np.einsum("ikjl,lk->ij", v, rho)
+
+
+def expm_hermitian(H, dt):
+    """exp(-i dt H) for Hermitian H via its eigendecomposition."""
+    lam, V = np.linalg.eigh(H)
+    return (V * np.exp(-1j * dt * lam)[None, :]) @ V.conj().T
+
+
+# --------------------------------------------------------------------------
+# Time stepping of Eq. (equalt)
+# --------------------------------------------------------------------------
+
+
+class Propagation:
+    """Result of ``propagate``: rho[n], I[n] (k1's collision integral at t_n),
+    E_field[n], and per-step diagnostics."""
+
+    def __init__(self, rho, I, E, energy_total, energy_corr):
+        self.rho = rho
+        self.I = I
+        self.E = E
+        self.energy_total = energy_total
+        self.energy_corr = energy_corr
+
+
+def _rhs(h_hf, rho, I):
+    """d rho / dt from Eq. (equalt) with G^<(t,t) = i rho:
+    i d(i rho)/dt = [h_HF, i rho] + (I + I^dag)  =>
+    d rho/dt = -i [h_HF, rho] - (I + I^dag)."""
+    return -1j * (h_hf @ rho - rho @ h_hf) - (I + I.conj().T)
+
+
+def energy(h, d, E, v, rho, I):
+    """E(t) = Tr[(h + E d) rho] + 1/2 Tr[Sigma_HF rho] + 1/2 Im Tr I (per spin).
+    Returns (total, correlation part)."""
+    one = np.trace((h + E * d) @ rho).real
+    hf = 0.5 * np.trace(hf_self_energy(v, rho) @ rho).real
+    ec = 0.5 * np.trace(I).imag
+    return one + hf + ec, ec
+
+
+def propagate(h, v, d, rho0, dt, n_steps, E_samples, route="independent"):
+    """Heun stepping of Eq. (equalt) with the GKBA collision integral.
+
+    E_samples[n] = E(t_n), n = 0 .. n_steps.  Per step n -> n+1:
+      k1 = F(t_n, rho_n) over history t_0..t_n with T(t_n, .)
+      rho~ = rho_n + dt k1
+      U_n = exp(-i dt (h_HF(t_n, rho_n) + h_HF(t_{n+1}, rho~)) / 2)
+      T(t_{n+1}, t_k) = U_n T(t_n, t_k), T(t_{n+1}, t_{n+1}) = 1
+      k2 = F(t_{n+1}, rho~) over history t_0..t_n, t_{n+1} (rho~ in the last slot)
+      rho_{n+1} = rho_n + dt/2 (k1 + k2)
+    where F = -i[h_HF, rho] - (I + I^dag), h_HF(t, rho) = h + E(t) d + Sigma_HF(rho).
+    Returns a ``Propagation`` with rho[0..n_steps] and I[0..n_steps].
+    """
+    N = rho0.shape[0]
+    rho_hist = [rho0.copy()]
+    T_row = [np.eye(N, dtype=np.complex128)]
+    Is, energies, ecs = [], [], []
+
+    def coll(rhos, Ts):
+        L = len(rhos)
+        if L < 2:
+            return np.zeros((N, N), np.complex128)
+        return collision(v, np.array(rhos), np.array(Ts), trapezoid_weights(L, dt), route)
+
+    for n in range(n_steps + 1):
+        rho_n = rho_hist[n]
+        hhf_n = h + E_samples[n] * d + hf_self_energy(v, rho_n)
+        I_n = coll(rho_hist, T_row)
+        Is.append(I_n)
+        et, ec = energy(h, d, E_samples[n], v, rho_n, I_n)
+        energies.append(et)
+        ecs.append(ec)
+        if n == n_steps:
+            break
+        k1 = _rhs(hhf_n, rho_n, I_n)
+        rho_t = rho_n + dt * k1
+        hhf_t = h + E_samples[n + 1] * d + hf_self_energy(v, rho_t)
+        U = expm_hermitian(0.5 * (hhf_n + hhf_t), dt)
+        T_row = [U @ T for T in T_row] + [np.eye(N, dtype=np.complex128)]
+        I_t = coll(rho_hist + [rho_t], T_row)
+        k2 = _rhs(hhf_t, rho_t, I_t)
+        rho_hist.append(rho_n + 0.5 * dt * (k1 + k2))
+
+    return Propagation(np.array(rho_hist), np.array(Is), np.asarray(E_samples[: n_steps + 1]),
+                       np.array(energies), np.array(ecs))
