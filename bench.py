@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Benchmark: one GKBA second-Born Heun step at N = 96 with a 2000-point history.
+
+A step is one pass of the whole hot path through the C ABI (gkba_step): the
+mean field, two collision integrals (history of n+1 and n+2 points: GKBA
+reconstruction, the four-stage split-TF32 tensor-core contraction of
+Eq. (2bse), the FP64 weighted history sum), the propagator exp(-i dt h), the
+T(t,t_k) recursion and the Heun update.  Inputs are seeded and synthetic
+(random Hermitian rho_k with eigenvalues in [0,1], T(t,t_k) products of
+exp(-i H_j dt) with random Hermitian H_j, v from 64 Gaussian factors).
+
+Printed JSON line (rank 0):
+  value        algorithmic contraction TFLOP/s over the step (24 N^5 real flops
+               per (t_k, component) unit; 2 (2n+3) units per step)
+  e2e          the same metric for gkba_collision called with pinned host
+               buffers (history copied host->device inside the timed region)
+  roofline     the dominant stage kernel: its algorithmic flops per launch over
+               its CUDA-event launch time, against the TF32 tensor peak
+               (measured bf16 sustained peak x 1.1/2.25)
+  cpu_baseline the CPU oracle on one (t_k, component) unit of the same workload
+  fp64_path    the FP64 CUDA path timed on a 3-point history and extrapolated
+               (cost is linear in the number of units), with the split-TF32
+               error against it
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample per step: one (t_k, component) unit at N = 96.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates (GB300)
+METRIC = "GKBA-2B step time & contraction TFLOP/s (% peak), TC vs FP64 path at stated err"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=96)
+    ap.add_argument("--L", type=int, default=2000)
+    ap.add_argument("--nP", type=int, default=64)
+    ap.add_argument("--dt", type=float, default=0.02)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def unit_flops(N):
+    return 24.0 * float(N) ** 5
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(bf16_burst=d["bf16_tflops"], bf16_sustained=d["bf16_tflops_sustained"],
+                    hbm=d["hbm_gbs"], src="measured")
+    return dict(bf16_burst=1900.0, bf16_sustained=1700.0, hbm=6800.0, src="fallback")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_unit_sample(N, nP, seed=0):
+    """Time the CPU oracle on one (t_k, component) unit of the workload."""
+    import gkba_inputs as gi
+    import oracle as O
+    s = gi.system(N, nP, seed=seed)
+    rho, T = gi.history(N, 2, 0.02, seed=seed)
+    P = T[0] @ rho[0]
+    Q = T[0] - P
+    t0 = time.perf_counter()
+    O.sigma_independent(s["v"], P, Q.conj().T)
+    dt = time.perf_counter() - t0
+    return dt
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    N = a.N
+    import gkba_inputs  # noqa: F401  (warm imports outside the timed region)
+    times = []
+    for i in range(a.warmup + a.steps):
+        t = oracle_unit_sample(N, a.nP, seed=i)
+        if i >= a.warmup:
+            times.append(t)
+    ms = 1e3 * float(np.mean(times))
+    val = unit_flops(N) / (ms * 1e-3) / 1e12
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"gkba2b_heun_step_N{N}_L{a.L}", "N": N, "n_P": a.nP, "L": a.L,
+                   "dt": a.dt, "parallelism": "replicas"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one (t_k, component) unit of Eq. (2bse) at N={N} per step "
+                                   "(numpy FP64 N^5 route)"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+
+    import torch
+    import gkba_inputs as gi
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    N, L, dt = a.N, a.L, a.dt
+    s = gi.system(N, a.nP, seed=0)
+    rho_h, T_h = gi.history(N, L, dt, seed=1 + rank)
+    stream = torch.cuda.current_stream()
+    steps_total = a.warmup + a.steps
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=L - 1 + steps_total + 1,
+                    precision="tf32", stream=stream.cuda_stream, timing=True)
+    ctx.set_history(L - 1, rho_h, T_h)
+
+    for _ in range(a.warmup):
+        ctx.step(0.0, 0.0)
+    ctx.stats(reset=True)
+
+    clocks = Clocks(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = L - 1 + a.warmup
+    ev0.record(stream)
+    for _ in range(a.steps):
+        ctx.step(0.0, 0.0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    stats, launches = ctx.stats(reset=True)
+    units = sum(2 * (2 * (n0 + k) + 3) for k in range(a.steps))
+    flops = units * unit_flops(N)
+    value = world * flops / (ms_total * 1e-3) / 1e12
+    ms_step = ms_total / a.steps
+
+    # roofline: dominant stage kernel over the timed region
+    pk = peaks()
+    tf32_peak = pk["bf16_sustained"] * TF32_OVER_BF16
+    stage = {k: v for k, v in stats.items() if k.startswith("S") and v["launches"] > 0}
+    dom = max(stage, key=lambda k: stage[k]["ms"])
+    d = stage[dom]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": tf32_peak,
+            "unit": "TFLOP/s", "frac": achieved / tf32_peak,
+            "executed_frac": 3.0 * achieved / tf32_peak,
+            "peak_note": f"TF32 = bf16 sustained ({pk['src']}) x 1.1/2.25; executed_frac counts "
+                         "the 3 TF32 products per algorithmic product",
+            "traffic": None,
+            "ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"],
+            "share": d["ms"] / sum(v["ms"] for v in stage.values()),
+            "stages": {k: {"ms": v["ms"], "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9,
+                           "launches": v["launches"]} for k, v in stage.items()}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32x3+f64", "data": "synthetic",
+        "config": {"workload": f"gkba2b_heun_step_N{N}_L{L}", "N": N, "n_P": a.nP, "L": L,
+                   "dt": dt, "precision": "split_tf32", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (per-unit intermediates 680 MB each)",
+                   "units_per_step": units / a.steps},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk,
+    }
+
+    if rank == 0 and not a.no_e2e:
+        # e2e: gkba_collision with pinned host buffers, copies inside the timed region
+        Lh = L
+        rh = torch.from_numpy(rho_h).pin_memory()
+        th = torch.from_numpy(T_h).pin_memory()
+        Iout = torch.empty((N, N), dtype=torch.complex128).pin_memory()
+        e0 = time.perf_counter()
+        ctx.collision(rh.numpy(), th.numpy())
+        e_s = time.perf_counter() - e0
+        line["e2e"] = {"value": 2 * Lh * unit_flops(N) / e_s / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": int(rh.numel() * 16 + th.numel() * 16),
+                       "d2h_bytes_per_step": int(Iout.numel() * 16),
+                       "call": f"gkba_collision(L={Lh}) host buffers"}
+    ctx.close()
+
+    if rank == 0 and not a.no_fp64:
+        Ls = 3
+        c64 = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, precision="fp64",
+                        stream=stream.cuda_stream)
+        ctc = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, precision="tf32",
+                        stream=stream.cuda_stream)
+        r3, t3 = rho_h[:Ls].copy(), T_h[:Ls].copy()
+        I64 = c64.collision(r3, t3)  # warm
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        I64 = c64.collision(r3, t3)
+        t64 = time.perf_counter() - e0
+        Itc = ctc.collision(r3, t3)
+        err = float(np.linalg.norm(Itc - I64) / np.linalg.norm(I64))
+        per_unit = t64 / (2 * Ls)
+        ms64 = 1e3 * per_unit * units / a.steps
+        line["fp64_path"] = {"sample": f"collision over {Ls} history points ({2 * Ls} units) at N={N}",
+                             "ms_per_step_extrapolated": ms64,
+                             "tflops": unit_flops(N) / per_unit / 1e12,
+                             "speedup_split_tf32": ms64 / ms_step,
+                             "split_tf32_rel_err_I": err}
+        c64.close()
+        ctc.close()
+
+    if rank == 0 and not a.no_cpu:
+        t = oracle_unit_sample(N, a.nP)
+        line["cpu_baseline"] = {"value": unit_flops(N) / t / 1e12, "unit": "TFLOP/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"one (t_k, component) unit of Eq. (2bse) at N={N} "
+                                          f"({t:.1f} s, numpy FP64 N^5 route)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

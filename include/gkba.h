@@ -1,0 +1,200 @@
+/*
+ * gkba.h - C ABI of the GKBA second-Born collision-integral library (sm_103a).
+ *
+ * The library evaluates, on one GPU, the hot path of Tuovinen, Covito and
+ * Sentef, "Efficient computation of the second-Born self-energy using
+ * tensor-contraction operations" (arXiv:1905.01180):
+ *
+ *   Sec. III, Eq. (2bse)   second-Born self-energy
+ *        Sigma_ij = 2 sum v_irpn v_mqsj G_nm Gb_sr G_pq - sum v_irpn v_mqsj G_nq Gb_sr G_pm
+ *     computed as four chained N^5 contractions (one index each) with the
+ *     direct and exchange terms folded into w_mqsj = 2 v_mqsj - v_qmsj;
+ *   Sec. II, Eqs. (gkba), (prop)   G^<(t,t_k) = i T(t,t_k) rho_k,
+ *        G^>(t,t_k) = -i T(t,t_k)(1 - rho_k), with the Hartree-Fock propagator
+ *        T(t_n,t_k) = U_{n-1} ... U_k (lower limit of Eq. (prop) read as t');
+ *   Sec. II, Eq. (collint) first line, time integral as a weighted sum over
+ *        the history t_0 .. t_n:
+ *        I(t) = sum_k c_k [Sigma^>(t,t_k) G^<(t_k,t) - Sigma^<(t,t_k) G^>(t_k,t)]
+ *             = sum_k c_k [S(Q_k,P_k^+) P_k^+ - S(P_k,Q_k^+) Q_k^+],
+ *        P_k = T(t,t_k) rho_k, Q_k = T(t,t_k) - P_k;
+ *   Sec. II, Eq. (equalt)   d rho/dt = -i [h + E(t) d + Sigma_HF(rho), rho] - (I + I^+),
+ *        (Sigma_HF)_ij = sum_kl (2 v_iklj - v_ikjl) rho_lk, advanced by Heun's
+ *        method with U_n = exp(-i dt (h_HF(t_n) + h_HF(t_{n+1}))/2).
+ *
+ * Conventions shared by every call
+ *  - Complex matrices are N x N, row-major, interleaved (re, im) doubles
+ *    (the memory layout of C99 double complex / numpy complex128).
+ *  - v is N^4 real doubles, v[((i*N + j)*N + k)*N + l] = v_ijkl (Eq. coulomb).
+ *  - rho, I, Sigma are per spin (spin-restricted, Sec. II).
+ *  - The caller owns every buffer it passes; the library copies what it keeps.
+ *    "on_device" arguments say whether the caller's pointers are device
+ *    pointers (nonzero) or host pointers (zero, pinned or pageable).
+ *  - Calls are stream-ordered on the context's stream and synchronous at
+ *    return: host outputs are written when the call returns.
+ *  - Nothing aborts: every call returns a gkba_status, and gkba_last_error()
+ *    gives a message.  Device-side waits are bounded and report
+ *    GKBA_ETIMEOUT.  Calls on one context are not thread-safe.
+ */
+#ifndef GKBA_H
+#define GKBA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gkba_ctx gkba_ctx; /* opaque; created by gkba_init, freed by gkba_destroy */
+
+typedef enum {
+    GKBA_OK = 0,
+    GKBA_EINVAL = 1,      /* bad argument: size, NULL, non-Hermitian input, asymmetric v, non-finite data */
+    GKBA_ENOMEM = 2,      /* device or host allocation failed */
+    GKBA_ECUDA = 3,       /* a CUDA runtime/driver call failed (message has the CUDA error) */
+    GKBA_ESTATE = 4,      /* call not valid in the current state (e.g. history full) */
+    GKBA_ETIMEOUT = 5,    /* a device-side wait ran past its limit; results are invalid */
+    GKBA_ENUMERIC = 6,    /* non-finite values produced */
+    GKBA_EUNSUPPORTED = 7 /* valid request that this build does not implement */
+} gkba_status;
+
+typedef enum {
+    GKBA_FP64 = 0,       /* every contraction in FP64 on the CUDA cores */
+    GKBA_SPLIT_TF32 = 1  /* contractions on tcgen05 tensor cores: FP32 data,
+                            3 TF32 products (hi*hi + hi*lo + lo*hi), FP32
+                            accumulation inside a K-chunk, FP64 across chunks;
+                            P/Q, T recursion, I history sum and rho update stay FP64 */
+} gkba_precision;
+
+typedef struct {
+    int N;             /* basis size, 1 <= N <= 128 (GKBA_SPLIT_TF32: N <= 96) */
+    double dt;         /* time step delta (> 0) */
+    int max_steps;     /* history capacity: t_0 .. t_{max_steps} (>= 0) */
+    int precision;     /* gkba_precision */
+    void* cuda_stream; /* cudaStream_t to run on; NULL = the library creates one */
+    size_t workspace_bytes; /* cap on the contraction workspace (0 = default 16 GiB);
+                               the batch of (t_k, component) units is sized to fit */
+    int device;        /* CUDA device ordinal (-1 = current device) */
+    int timing;        /* nonzero: time every contraction kernel with CUDA events
+                          (see gkba_get_stats) */
+} gkba_config;
+
+/* Per-kernel-class counters (see gkba_get_stats). */
+typedef struct {
+    const char* name;       /* kernel class name */
+    long long launches;     /* launches since the last reset */
+    double ms;              /* summed CUDA-event time (only when cfg.timing) */
+    double flops;           /* summed algorithmic flops of those launches */
+    double bytes;           /* summed algorithmic (compulsory) DRAM bytes */
+} gkba_kernel_stat;
+
+/*
+ * gkba_init - create a context for the model of Sec. II, Eq. (hamiltonian).
+ *   h    N*N complex Hermitian one-body matrix h_ij (Eq. onebody), no field
+ *   v    N^4 real Coulomb integrals with the 8-fold symmetry of Eq. (symmetries)
+ *   d    N*N complex Hermitian dipole matrix; the field enters as h + E(t) d
+ *   rho0 N*N complex Hermitian initial density matrix rho(t_0) (per spin)
+ * Builds the contraction layouts of v and w = 2v - v_exch on the device, and
+ * the history store (rho_0 = rho0, T(t_0,t_0) = 1).  Returns GKBA_EINVAL for
+ * non-Hermitian h/d/rho0 or a v that breaks Eq. (symmetries) (tolerance
+ * 1e-10 relative), non-finite data or bad sizes; *out is NULL on failure.
+ */
+gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, const double* v,
+                      const double* d, const double* rho0, int inputs_on_device);
+
+/*
+ * gkba_sigma - second-Born self-energy S(G, Gb) of Eq. (2bse) for n_units
+ * independent pairs (G = G^{<>}(t,t'), Gb = G^{><}(t',t), Sec. III notation).
+ *   G, Gbar  n_units * N*N complex each
+ *   S_out    n_units * N*N complex: S_u = Eq. (2bse) evaluated on (G_u, Gbar_u)
+ * Runs on the context's precision path.
+ */
+gkba_status gkba_sigma(gkba_ctx* ctx, int n_units, const double* G, const double* Gbar,
+                       double* S_out, int on_device);
+
+/*
+ * gkba_collision - collision integral I(t) of Eq. (collint), first line, for
+ * an explicit history of L >= 1 points t_0 .. t_{L-1} = t:
+ *   rho_hist  L*N*N complex: rho(t_k)
+ *   T_hist    L*N*N complex: HF propagator T(t, t_k) of Eq. (prop)
+ *             (T_hist[L-1] is normally the identity)
+ *   weights   L doubles c_k, or NULL for the trapezoid rule with cfg.dt
+ *             (dt/2 at both ends, dt inside; L == 1 gives I = 0)
+ *   I_out     N*N complex: I(t) = sum_k c_k [S(Q_k,P_k^+) P_k^+ - S(P_k,Q_k^+) Q_k^+]
+ * All of P/Q reconstruction, the contractions, the products with P^+/Q^+ and
+ * the FP64 history sum run on the device.  The equation of motion uses
+ * I + I^+ (the second line of Eq. (collint) is the adjoint of the first).
+ */
+gkba_status gkba_collision(gkba_ctx* ctx, int L, const double* rho_hist, const double* T_hist,
+                           const double* weights, double* I_out, int on_device);
+
+/*
+ * gkba_step - one Heun step t_n -> t_{n+1} of Eq. (equalt) with the field
+ * samples E_n = E(t_n), E_np1 = E(t_{n+1}):
+ *   k1 = F(t_n, rho_n) over the history t_0..t_n, rho~ = rho_n + dt k1,
+ *   U_n = exp(-i dt (h_HF(t_n,rho_n) + h_HF(t_{n+1},rho~))/2),
+ *   T(t_{n+1},t_k) = U_n T(t_n,t_k), k2 = F(t_{n+1}, rho~) over t_0..t_{n+1},
+ *   rho_{n+1} = rho_n + dt/2 (k1 + k2),  F = -i[h_HF, rho] - (I + I^+).
+ * Outputs (host pointers, each may be NULL):
+ *   rho_out   N*N complex: rho_{n+1}
+ *   I_out     N*N complex: I(t_n) of k1
+ *   diag_out  4 doubles at t_n: {Tr rho_n, E_total, E_corr, Re Tr I_n} with
+ *             E_total = Tr[(h+E_n d) rho_n] + 1/2 Tr[Sigma_HF rho_n] + E_corr,
+ *             E_corr = 1/2 Im Tr I_n (per spin).
+ * GKBA_ESTATE when the history is full (n == cfg.max_steps).
+ */
+gkba_status gkba_step(gkba_ctx* ctx, double E_n, double E_np1, double* rho_out, double* I_out,
+                      double* diag_out);
+
+/*
+ * gkba_set_history - replace the stepper state (checkpoint restore): the
+ * history t_0 .. t_n with rho_hist[k] = rho(t_k) and T_hist[k] = T(t_n, t_k),
+ * k = 0..n (n + 1 points; T_hist[n] should be the identity).
+ * GKBA_EINVAL when n > cfg.max_steps.
+ */
+gkba_status gkba_set_history(gkba_ctx* ctx, int n, const double* rho_hist, const double* T_hist,
+                             int on_device);
+
+/*
+ * gkba_get_history - copy the stepper state out (checkpoint save): n and,
+ * when the pointers are non-NULL, rho_hist / T_hist with (n+1)*N*N complex
+ * each (host pointers).
+ */
+gkba_status gkba_get_history(const gkba_ctx* ctx, int* n, double* rho_hist, double* T_hist);
+
+/* gkba_get_state - current step index n and rho(t_n) (host, may be NULL). */
+gkba_status gkba_get_state(const gkba_ctx* ctx, int* n, double* rho);
+
+/*
+ * gkba_mean_field - (Sigma_HF)_ij = sum_kl (2 v_iklj - v_ikjl) rho_lk (Sec. II)
+ * for one N*N complex rho; output N*N complex.
+ */
+gkba_status gkba_mean_field(gkba_ctx* ctx, const double* rho, double* sigma_hf, int on_device);
+
+/*
+ * gkba_adjoint - reverse-mode gradient of L = Tr[d rho(t_T)] through the
+ * Heun stepper and the collision integral.  Not implemented in this build:
+ * returns GKBA_EUNSUPPORTED and writes nothing.
+ */
+gkba_status gkba_adjoint(gkba_ctx* ctx, const double* E_samples, int n_steps, int ckpt_every,
+                         const double* dL_drho_T, double* dL_dE, double* dL_dv);
+
+/*
+ * gkba_get_stats - kernel counters since the last reset: fills up to
+ * max_stats entries and returns their number in *n_stats; *total_launches is
+ * the number of library kernel launches.  reset != 0 clears the counters
+ * after reading.
+ */
+gkba_status gkba_get_stats(gkba_ctx* ctx, gkba_kernel_stat* stats, int max_stats, int* n_stats,
+                           long long* total_launches, int reset);
+
+/* Message for the last failing call on ctx (or the last failed gkba_init when ctx is NULL). */
+const char* gkba_last_error(const gkba_ctx* ctx);
+
+/* Free every device and host resource of ctx (NULL is a no-op). */
+void gkba_destroy(gkba_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKBA_H */

@@ -109,10 +109,11 @@ def sigma_paper(v, G, Gb):
     batched = G.ndim == 3
     if not batched:
         G, Gb = G[None], Gb[None]
-    T1 = np.einsum("mqsj,bnm->bnqsj", v, G)
-    T2 = np.einsum("irpn,bsr->bispn", v, Gb)
-    T3 = np.einsum("bpq,bispn->bisqn", G, T2)
-    S = 2.0 * np.einsum("bnqsj,bisqn->bij", T1, T3) - np.einsum("bqnjs,bisnq->bij", T1, T3)
+    T1 = np.einsum("mqsj,bnm->bnqsj", v, G, optimize=True)
+    T2 = np.einsum("irpn,bsr->bispn", v, Gb, optimize=True)
+    T3 = np.einsum("bpq,bispn->bisqn", G, T2, optimize=True)
+    S = (2.0 * np.einsum("bnqsj,bisqn->bij", T1, T3, optimize=True)
+         - np.einsum("bqnjs,bisnq->bij", T1, T3, optimize=True))
     return S if batched else S[0]
 
 
@@ -138,10 +139,10 @@ def sigma_independent(v, G, Gb):
     if not batched:
         G, Gb = G[None], Gb[None]
     w = exchange_folded(v)
-    W1 = np.einsum("mqsj,bsr->bmqrj", w, Gb)
-    W2 = np.einsum("bpq,bmqrj->bmprj", G, W1)
-    W3 = np.einsum("bnm,bmprj->bnprj", G, W2)
-    S = np.einsum("irpn,bnprj->bij", v, W3)
+    W1 = np.einsum("mqsj,bsr->bmqrj", w, Gb, optimize=True)
+    W2 = np.einsum("bpq,bmqrj->bmprj", G, W1, optimize=True)
+    W3 = np.einsum("bnm,bmprj->bnprj", G, W2, optimize=True)
+    S = np.einsum("irpn,bnprj->bij", v, W3, optimize=True)
     return S if batched else S[0]
 
 

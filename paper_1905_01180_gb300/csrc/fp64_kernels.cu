@@ -1,0 +1,685 @@
+// fp64_kernels.cu - FP64 kernels of the GKBA second-Born path:
+//  * the chained-contraction stage GEMM for the FP64 path (Eq. 2bse evaluated
+//    as four one-index contractions, see gkba_api.cu for the stage list),
+//  * GKBA reconstruction P_k = T(t,t_k) rho_k, Q_k = T(t,t_k) - P_k (Eq. gkba),
+//  * split-K reduction and the weighted history sum of Eq. (collint),
+//  * the time-local pieces of Eq. (equalt): Sigma_HF, h_HF, commutator,
+//    U_n = exp(-i dt h) by scaling and squaring with a Taylor polynomial,
+//    the propagator recursion T(t_{n+1},t_k) = U_n T(t_n,t_k), Heun updates.
+#include <cmath>
+
+#include "gkba_internal.cuh"
+
+namespace gkba {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// ---------------------------------------------------------------------------
+// Stage GEMM (FP64): D[row][col] = sum_k A[row*lda+k] * B[col*ldb+k]; the
+// result is scattered by the stage's index map.  64x64 output tile, 16-wide
+// K slices staged in shared memory, 4x4 outputs per thread.
+// ---------------------------------------------------------------------------
+constexpr int G64_BM = 64, G64_BN = 64, G64_BK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm64_stage(const double* __restrict__ A, long long lda,
+                                                      long long sAz, const double* __restrict__ B,
+                                                      long long ldb, long long sBz,
+                                                      double* __restrict__ out, long long sOz, int M,
+                                                      int Nc, long long Ktot, int splitk,
+                                                      long long Kc, StageMap map) {
+    const int z = blockIdx.z;
+    long long K = Ktot;
+    if (splitk) {
+        const long long k0 = (long long)z * Kc;
+        K = Ktot - k0 < Kc ? Ktot - k0 : Kc;
+        A += k0;
+        B += k0;
+        out += (long long)z * sOz;
+    } else {
+        A += (long long)z * sAz;
+        B += (long long)z * sBz;
+        out += (long long)z * sOz;
+    }
+    const long long m0 = (long long)blockIdx.y * G64_BM;
+    const int n0 = blockIdx.x * G64_BN;
+    __shared__ double As[G64_BK][G64_BM + 1];
+    __shared__ double Bs[G64_BK][G64_BN + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    for (long long kb = 0; kb < K; kb += G64_BK) {
+        for (int e = tid; e < G64_BM * G64_BK; e += 256) {
+            const int r = e / G64_BK, kk = e % G64_BK;
+            const long long gr = m0 + r, gk = kb + kk;
+            As[kk][r] = (gr < M && gk < K) ? A[gr * lda + gk] : 0.0;
+        }
+        for (int e = tid; e < G64_BN * G64_BK; e += 256) {
+            const int cidx = e / G64_BK, kk = e % G64_BK;
+            const long long gc = n0 + cidx, gk = kb + kk;
+            Bs[kk][cidx] = (gc < Nc && gk < K) ? B[gc * ldb + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < G64_BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long row = m0 + ty + 16 * i;
+        if (row >= M) continue;
+        const long long x = row % map.Dx;
+        const long long rb = row / map.Dx;
+        const long long b = rb % map.Db;
+        const long long a = rb / map.Db;
+        const long long roff = a * map.SA + b * map.SB + x * map.SX;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = n0 + tx + 16 * j;
+            if (col >= Nc) continue;
+            const int cc = col / map.Dy, y = col % map.Dy;
+            out[roff + cc * map.SC + (long long)y * map.SY] = acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Complex batched GEMM for N x N matrices (FP64):
+//   C = alpha op(A) op(B) + beta C (+ identity), op in {N, C = conj-transpose}.
+// When skip_ge != nullptr and idx >= *skip_ge the block copies op(A) into C
+// instead (used for the data-dependent number of squarings in expm).
+// ---------------------------------------------------------------------------
+constexpr int ZT = 16;
+
+__global__ void __launch_bounds__(256) k_zgemm(int n, int opA, int opB, double2 alpha,
+                                               const double2* __restrict__ A, long long sA,
+                                               const double2* __restrict__ B, long long sB,
+                                               double2 beta, double2* __restrict__ C, long long sC,
+                                               int add_identity, const int* skip_ge, int idx) {
+    const int b = blockIdx.z;
+    A += (long long)b * sA;
+    B += (long long)b * sB;
+    C += (long long)b * sC;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row = blockIdx.y * ZT + ty, col = blockIdx.x * ZT + tx;
+    if (skip_ge != nullptr && idx >= *skip_ge) {
+        if (row < n && col < n) {
+            double2 a = opA ? cconj(A[(long long)col * n + row]) : A[(long long)row * n + col];
+            C[(long long)row * n + col] = a;
+        }
+        return;
+    }
+    __shared__ double2 As[ZT][ZT + 1], Bs[ZT][ZT + 1];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int kb = 0; kb < n; kb += ZT) {
+        // As[ty][tx] = op(A)[row][kb+tx]
+        {
+            const int r = blockIdx.y * ZT + ty, k = kb + tx;
+            double2 v = make_double2(0.0, 0.0);
+            if (r < n && k < n) v = opA ? cconj(A[(long long)k * n + r]) : A[(long long)r * n + k];
+            As[ty][tx] = v;
+        }
+        // Bs[ty][tx] = op(B)[kb+ty][col]
+        {
+            const int k = kb + ty, cidx = blockIdx.x * ZT + tx;
+            double2 v = make_double2(0.0, 0.0);
+            if (k < n && cidx < n) v = opB ? cconj(B[(long long)cidx * n + k]) : B[(long long)k * n + cidx];
+            Bs[ty][tx] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < ZT; ++kk) acc = cadd(acc, cmul(As[ty][kk], Bs[kk][tx]));
+        __syncthreads();
+    }
+    if (row < n && col < n) {
+        double2 r = cmul(alpha, acc);
+        if (beta.x != 0.0 || beta.y != 0.0) r = cadd(r, cmul(beta, C[(long long)row * n + col]));
+        if (add_identity && row == col) r.x += 1.0;
+        C[(long long)row * n + col] = r;
+    }
+}
+
+// Sigma_HF(rho)_ij = sum_{l,k} hfK[(i,j),(l,k)] rho_lk, plus h + E d when add_h.
+// One warp per (i, j); lanes stride over (l, k).
+__global__ void k_mean_field(int N, const double* __restrict__ hfK, const double2* __restrict__ rho,
+                             const double2* __restrict__ h, const double2* __restrict__ d, double E,
+                             int add_h, double2* __restrict__ out) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int NN = N * N;
+    if (warp >= NN) return;
+    const double* row = hfK + (long long)warp * NN;
+    double re = 0.0, im = 0.0;
+    for (int e = lane; e < NN; e += 32) {
+        const double kv = row[e];
+        const double2 r = rho[e];
+        re = fma(kv, r.x, re);
+        im = fma(kv, r.y, im);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        if (add_h) {
+            re += h[warp].x + E * d[warp].x;
+            im += h[warp].y + E * d[warp].y;
+        }
+        out[warp] = make_double2(re, im);
+    }
+}
+
+// out = -i (HR - RH) - (I + I^+), where HR = H rho and RH = rho H.
+__global__ void k_rhs(int N, const double2* __restrict__ HR, const double2* __restrict__ RH,
+                      const double2* __restrict__ I, double2* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * N) return;
+    const int i = e / N, j = e % N;
+    const double2 c = make_double2(HR[e].x - RH[e].x, HR[e].y - RH[e].y);
+    const double2 a = I[e], bt = I[j * N + i];
+    // -i c = (c.y, -c.x); I + I^+ at (i,j) = I_ij + conj(I_ji)
+    out[e] = make_double2(c.y - (a.x + bt.x), -c.x - (a.y - bt.y));
+}
+
+// y = a x + b z (elementwise complex, real a and b).
+__global__ void k_lincomb(long long n, double2* __restrict__ y, const double2* __restrict__ x,
+                          const double2* __restrict__ z, double a, double b) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double2 xv = x[e];
+    const double2 zv = z ? z[e] : make_double2(0.0, 0.0);
+    y[e] = make_double2(a * xv.x + b * zv.x, a * xv.y + b * zv.y);
+}
+
+__global__ void k_set_identity(int N, int count, double2* __restrict__ A) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)N * N;
+    if (e >= NN * count) return;
+    const long long r = e % NN;
+    A[e] = make_double2((r / N) == (r % N) ? 1.0 : 0.0, 0.0);
+}
+
+// expm set-up: A = -i dt (hA + hB)/2; writes A into X, its 1-norm (max column
+// sum of |A_ij|) and the number of squarings s so that ||A||/2^s <= 1/2, then
+// scales X by 2^-s.  One block.
+__global__ void k_expm_setup(int N, double dt, const double2* __restrict__ hA,
+                             const double2* __restrict__ hB, double2* __restrict__ X,
+                             double* __restrict__ norm_out, int* __restrict__ s_out) {
+    __shared__ double colmax[1024];
+    const int tid = threadIdx.x;
+    double best = 0.0;
+    for (int j = tid; j < N; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const long long e = (long long)i * N + j;
+            const double hr = 0.5 * (hA[e].x + hB[e].x), hi = 0.5 * (hA[e].y + hB[e].y);
+            s += dt * sqrt(hr * hr + hi * hi);
+        }
+        best = fmax(best, s);
+    }
+    colmax[tid] = best;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) colmax[tid] = fmax(colmax[tid], colmax[tid + o]);
+        __syncthreads();
+    }
+    const double nrm = colmax[0];
+    int s = 0;
+    while (s < 30 && ldexp(nrm, -s) > 0.5) ++s;
+    const double scale = ldexp(1.0, -s);
+    for (int e = tid; e < N * N; e += blockDim.x) {
+        const double hr = 0.5 * (hA[e].x + hB[e].x), hi = 0.5 * (hA[e].y + hB[e].y);
+        // -i dt h = (dt*hi, -dt*hr)
+        X[e] = make_double2(scale * dt * hi, -scale * dt * hr);
+    }
+    if (tid == 0) {
+        *norm_out = nrm;
+        *s_out = s;
+    }
+}
+
+// Diagnostics at t_n: {Tr rho, E_total, E_corr, Re Tr I}.
+// E_total = 1/2 (Tr[(h+E d) rho] + Tr[h_HF rho]) + 1/2 Im Tr I.
+__global__ void k_diagnostics(int N, double E, const double2* __restrict__ h,
+                              const double2* __restrict__ d, const double2* __restrict__ hhf,
+                              const double2* __restrict__ rho, const double2* __restrict__ I,
+                              double* __restrict__ out) {
+    __shared__ double s0[256], s1[256], s2[256];
+    const int tid = threadIdx.x;
+    double t1 = 0.0, t2 = 0.0, tr = 0.0;
+    for (int e = tid; e < N * N; e += blockDim.x) {
+        const int i = e / N, j = e % N;
+        const double2 r = rho[j * N + i];
+        const double2 a = make_double2(h[e].x + E * d[e].x, h[e].y + E * d[e].y);
+        t1 += a.x * r.x - a.y * r.y;
+        t2 += hhf[e].x * r.x - hhf[e].y * r.y;
+        if (i == j) tr += rho[e].x;
+    }
+    s0[tid] = t1;
+    s1[tid] = t2;
+    s2[tid] = tr;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            s0[tid] += s0[tid + o];
+            s1[tid] += s1[tid + o];
+            s2[tid] += s2[tid + o];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double trI_re = 0.0, trI_im = 0.0;
+        for (int i = 0; i < N; ++i) {
+            trI_re += I[i * N + i].x;
+            trI_im += I[i * N + i].y;
+        }
+        const double ec = 0.5 * trI_im;
+        out[0] = s2[0];
+        out[1] = 0.5 * (s0[0] + s1[0]) + ec;
+        out[2] = ec;
+        out[3] = trI_re;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GKBA unit forms (FP64 path).  Unit u of a batch holds (G_u, Gb_u); the
+// stage-1 operand is B1[u][(c,r)][s] = Gb_c[s][r] (2N x N), the stage-2/3
+// operand is the real form of G: Gr[u][(c',p)][(c,q)] with blocks
+// [[Re G, -Im G], [Im G, Re G]] (2N x 2N).
+// ---------------------------------------------------------------------------
+__global__ void k_forms64(int N, int nb, const double2* __restrict__ G, const double2* __restrict__ Gb,
+                          double* __restrict__ B1, double* __restrict__ Gr) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)N * N;
+    if (e >= NN * nb) return;
+    const int u = (int)(e / NN);
+    const int rr = (int)(e % NN);
+    const int a = rr / N, b = rr % N;
+    // stage-1 operand: entry (s = a, r = b)
+    const double2 gb = Gb[u * NN + rr];  // Gb[s][r]
+    double* b1 = B1 + (long long)u * 2 * NN;
+    b1[(long long)(0 * N + b) * N + a] = gb.x;
+    b1[(long long)(1 * N + b) * N + a] = gb.y;
+    // stage-2/3 operand: entry (p = a, q = b)
+    const double2 g = G[u * NN + rr];
+    double* gr = Gr + (long long)u * 4 * NN;
+    const long long ld = 2 * N;
+    gr[(long long)(0 * N + a) * ld + 0 * N + b] = g.x;
+    gr[(long long)(0 * N + a) * ld + 1 * N + b] = -g.y;
+    gr[(long long)(1 * N + a) * ld + 0 * N + b] = g.y;
+    gr[(long long)(1 * N + a) * ld + 1 * N + b] = g.x;
+}
+
+// Units of history point k (batch-local kk = k - k0): u = 2 kk + comp,
+//   comp 0 (Sigma^<): G = P_k, Gb = Q_k^+, coefficient -c_k,
+//   comp 1 (Sigma^>): G = Q_k, Gb = P_k^+, coefficient +c_k,
+// so that I = sum_u coef_u S(G_u, Gb_u) Gb_u (first line of Eq. collint).
+// Writes G_u into Gout, Gb_u into Mb and the coefficients.
+__global__ void k_gkba_units(int N, int nk, int k0, int L, double dt, const double2* __restrict__ P,
+                             const double2* __restrict__ Q, const double* __restrict__ w,
+                             double2* __restrict__ Gout, double2* __restrict__ Mb,
+                             double* __restrict__ coef) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)N * N;
+    if (e >= NN * nk) return;
+    const int kk = (int)(e / NN);
+    const int rr = (int)(e % NN);
+    const int i = rr / N, j = rr % N;
+    const long long base = (long long)kk * NN;
+    const double2 p = P[base + rr], q = Q[base + rr];
+    const double2 pt = P[base + (long long)j * N + i], qt = Q[base + (long long)j * N + i];
+    Gout[(2 * kk + 0) * NN + rr] = p;
+    Gout[(2 * kk + 1) * NN + rr] = q;
+    Mb[(2 * kk + 0) * NN + rr] = make_double2(qt.x, -qt.y);  // (Q^+)_ij = conj(Q_ji)
+    Mb[(2 * kk + 1) * NN + rr] = make_double2(pt.x, -pt.y);
+    if (rr == 0) {
+        const int k = k0 + kk;
+        double c;
+        if (w != nullptr) c = w[k];
+        else if (L <= 1) c = 0.0;
+        else c = (k == 0 || k == L - 1) ? 0.5 * dt : dt;
+        coef[2 * kk + 0] = -c;
+        coef[2 * kk + 1] = c;
+    }
+}
+
+// S_u[i][j] = sum_z part[z][i][u*2N + j] + i part[z][i][u*2N + N + j]
+// (split-K partials of the last contraction, rows (u, c, j), FP64 sum in
+// fixed z order).  Partials are FP64 (FP64 path) or FP32 (tensor-core path).
+template <typename TP>
+__global__ void k_reduce_partials(int N, int Np, int nb, int nz, long long zstride, long long Rld,
+                                  const TP* __restrict__ part, double2* __restrict__ S) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)N * N;
+    if (e >= NN * nb) return;
+    const int u = (int)(e / NN);
+    const int rr = (int)(e % NN);
+    const int i = rr / N, j = rr % N;
+    const long long r_re = (long long)u * 2 * Np + j, r_im = r_re + Np;
+    double re = 0.0, im = 0.0;
+    for (int z = 0; z < nz; ++z) {
+        const TP* pz = part + (long long)z * zstride + (long long)i * Rld;
+        re += (double)pz[r_re];
+        im += (double)pz[r_im];
+    }
+    S[e] = make_double2(re, im);
+}
+
+// I_acc[e] += sum_u coef[u] * Y[u][e] (fixed unit order: deterministic).
+__global__ void k_weighted_sum(int NN, int nb, const double* __restrict__ coef,
+                               const double2* __restrict__ Y, double2* __restrict__ I_acc) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NN) return;
+    double re = 0.0, im = 0.0;
+    for (int u = 0; u < nb; ++u) {
+        const double c = coef[u];
+        const double2 y = Y[(long long)u * NN + e];
+        re = fma(c, y.x, re);
+        im = fma(c, y.y, im);
+    }
+    I_acc[e].x += re;
+    I_acc[e].y += im;
+}
+
+// hfK[(i*N + j)*N*N + l*N + k] = 2 v_iklj - v_ikjl  (Sigma_HF as a matrix-vector product)
+__global__ void k_build_hfK(int N, const double* __restrict__ v, double* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = N, N4 = n * n * n * n;
+    if (e >= N4) return;
+    const long long k = e % n, l = (e / n) % n, j = (e / n / n) % n, i = e / n / n / n;
+    out[e] = 2.0 * v[((i * n + k) * n + l) * n + j] - v[((i * n + k) * n + j) * n + l];
+}
+
+// wS[j][m][q][s] = w_mqsj = 2 v_mqsj - v_qmsj (the direct and exchange terms of
+// Eq. (2bse) after relabelling m <-> q in the exchange term).
+__global__ void k_build_wS64(int N, const double* __restrict__ v, double* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = N, N4 = n * n * n * n;
+    if (e >= N4) return;
+    const long long s = e % n, q = (e / n) % n, m = (e / n / n) % n, j = e / n / n / n;
+    out[e] = 2.0 * v[((m * n + q) * n + s) * n + j] - v[((q * n + m) * n + s) * n + j];
+}
+
+// vK[i][n][r][p] = v_irpn (K index (n, r, p) of the last contraction).
+__global__ void k_build_vK64(int N, const double* __restrict__ v, double* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = N, N4 = n * n * n * n;
+    if (e >= N4) return;
+    const long long p = e % n, r = (e / n) % n, nn = (e / n / n) % n, i = e / n / n / n;
+    out[e] = v[((i * n + r) * n + p) * n + nn];
+}
+
+inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host wrappers
+// ---------------------------------------------------------------------------
+
+gkba_status fp64_prepare_model(gkba_ctx* c) {
+    const long long n = c->N, N4 = n * n * n * n;
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_build_hfK<<<grid1(N4, 256), 256, 0, c->stream>>>(c->N, c->v, c->hfK);
+    GKBA_TRY(launch_end(c, t));
+    if (c->prec != GKBA_FP64) return GKBA_OK;
+    t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_build_wS64<<<grid1(N4, 256), 256, 0, c->stream>>>(c->N, c->v, c->wS64);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_build_vK64<<<grid1(N4, 256), 256, 0, c->stream>>>(c->N, c->v, c->vK64);
+    return launch_end(c, t);
+}
+
+gkba_status gemm64_stage(gkba_ctx* c, int cls, const double* A, long long lda, long long sAz,
+                         const double* B, long long ldb, long long sBz, double* out,
+                         long long sOz, int M, int Nc, long long Ktot, int nz, int splitk,
+                         long long Kc, StageMap map, double flops, double bytes) {
+    dim3 grid((Nc + G64_BN - 1) / G64_BN, (M + G64_BM - 1) / G64_BM, nz);
+    if (grid.y > 65535u) return fail(c, GKBA_EINVAL, "stage GEMM: M=%d too large", M);
+    auto t = launch_begin(c, cls, flops, bytes);
+    k_gemm64_stage<<<grid, 256, 0, c->stream>>>(A, lda, sAz, B, ldb, sBz, out, sOz, M, Nc, Ktot,
+                                                splitk, Kc, map);
+    return launch_end(c, t);
+}
+
+static gkba_status zgemm_impl(gkba_ctx* c, int cls, int n, char opA, char opB, double2 alpha,
+                              const double2* A, long long sA, const double2* B, long long sB,
+                              double2 beta, double2* C, long long sC, int batch, int add_identity,
+                              const int* skip_ge, int idx) {
+    if (batch <= 0) return GKBA_OK;
+    dim3 grid((n + ZT - 1) / ZT, (n + ZT - 1) / ZT, 1);
+    const double flops = 8.0 * n * (double)n * n;
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int nbat = batch - b0 < 65535 ? batch - b0 : 65535;
+        grid.z = nbat;
+        auto t = launch_begin(c, cls, flops * nbat, 0.0);
+        k_zgemm<<<grid, 256, 0, c->stream>>>(n, opA == 'C', opB == 'C', alpha, A + b0 * sA, sA,
+                                             B + b0 * sB, sB, beta, C + b0 * sC, sC, add_identity,
+                                             skip_ge, idx);
+        GKBA_TRY(launch_end(c, t));
+    }
+    return GKBA_OK;
+}
+
+gkba_status zgemm_batched(gkba_ctx* c, int cls, int n, char opA, char opB, double2 alpha,
+                          const double2* A, long long sA, const double2* B, long long sB,
+                          double2 beta, double2* C, long long sC, int batch, int add_identity) {
+    return zgemm_impl(c, cls, n, opA, opB, alpha, A, sA, B, sB, beta, C, sC, batch, add_identity,
+                      nullptr, 0);
+}
+
+gkba_status mean_field(gkba_ctx* c, const double2* rho, double2* out) {
+    const int NN = c->N * c->N;
+    auto t = launch_begin(c, K_STEP, 8.0 * NN * (double)NN, 8.0 * NN * (double)NN);
+    k_mean_field<<<grid1((long long)NN * 32, 256), 256, 0, c->stream>>>(c->N, c->hfK, rho, c->h,
+                                                                         c->d, 0.0, 0, out);
+    return launch_end(c, t);
+}
+
+gkba_status h_hf(gkba_ctx* c, double E, const double2* rho, double2* out) {
+    const int NN = c->N * c->N;
+    auto t = launch_begin(c, K_STEP, 8.0 * NN * (double)NN, 8.0 * NN * (double)NN);
+    k_mean_field<<<grid1((long long)NN * 32, 256), 256, 0, c->stream>>>(c->N, c->hfK, rho, c->h,
+                                                                         c->d, E, 1, out);
+    return launch_end(c, t);
+}
+
+gkba_status rhs(gkba_ctx* c, const double2* hhf, const double2* rho, const double2* I, double2* out) {
+    const int N = c->N;
+    const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+    GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', one, hhf, 0, rho, 0, zero, c->tmp0, 0, 1, 0));
+    GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', one, rho, 0, hhf, 0, zero, c->tmp1, 0, 1, 0));
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_rhs<<<grid1((long long)N * N, 256), 256, 0, c->stream>>>(N, c->tmp0, c->tmp1, I, out);
+    return launch_end(c, t);
+}
+
+gkba_status expm_step(gkba_ctx* c, const double2* hA, const double2* hB, double2* U) {
+    // Scaling and squaring with a degree-18 Taylor polynomial (Moler & Van Loan,
+    // "Nineteen dubious ways to compute the exponential of a matrix"): with
+    // ||A/2^s||_1 <= 1/2 the truncation error is below 0.5^19/19! ~ 1e-23.
+    const int N = c->N;
+    const long long NN = (long long)N * N;
+    double2* X = c->ex0;  // scaled argument B = A / 2^s
+    double2* Y = c->ex1;
+    double2* Z = c->ex2;
+    {
+        auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+        k_expm_setup<<<1, 256, 0, c->stream>>>(N, c->dt, hA, hB, X, c->dscal + 8, c->dint + 0);
+        GKBA_TRY(launch_end(c, t));
+    }
+    const int deg = 18;
+    // Y = I + X / deg
+    {
+        auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+        k_set_identity<<<grid1(NN, 256), 256, 0, c->stream>>>(N, 1, Y);
+        GKBA_TRY(launch_end(c, t));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', make_double2(1.0 / deg, 0.0), X, 0, Y, 0,
+                               make_double2(0.0, 0.0), Z, 0, 1, 1));
+        std::swap(Y, Z);
+    }
+    for (int k = deg - 1; k >= 1; --k) {
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', make_double2(1.0 / k, 0.0), X, 0, Y, 0,
+                               make_double2(0.0, 0.0), Z, 0, 1, 1));
+        std::swap(Y, Z);
+    }
+    // up to kMaxSq squarings; step i is a copy when i >= s (device-side count)
+    const int kMaxSq = 16;
+    for (int i = 0; i < kMaxSq; ++i) {
+        GKBA_TRY(zgemm_impl(c, K_STEP, N, 'N', 'N', make_double2(1.0, 0.0), Y, 0, Y, 0,
+                            make_double2(0.0, 0.0), Z, 0, 1, 0, c->dint + 0, i));
+        std::swap(Y, Z);
+    }
+    GKBA_CUDA(c, cudaMemcpyAsync(U, Y, NN * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    return GKBA_OK;
+}
+
+gkba_status axpy_c(gkba_ctx* c, double2* y, const double2* x, const double2* z, double a, double b,
+                   int n) {
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_lincomb<<<grid1(n, 256), 256, 0, c->stream>>>(n, y, x, z, a, b);
+    return launch_end(c, t);
+}
+
+gkba_status set_identity(gkba_ctx* c, double2* A, int count) {
+    const long long n = (long long)c->N * c->N * count;
+    if (n == 0) return GKBA_OK;
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_set_identity<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, count, A);
+    return launch_end(c, t);
+}
+
+gkba_status diagnostics(gkba_ctx* c, double E_n, const double2* rho, const double2* I, double* out4) {
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_diagnostics<<<1, 256, 0, c->stream>>>(c->N, E_n, c->h, c->d, c->hhf_n, rho, I, out4);
+    return launch_end(c, t);
+}
+
+// P_k = T_k rho_k, Q_k = T_k - P_k for k in [k0, k0+nk), then the unit list.
+// The G_u are staged in Su (free until the reduction of this batch).
+gkba_status build_forms_gkba(gkba_ctx* c, int k0, int nk, int L, const double2* rho,
+                             const double2* T, const double* w) {
+    const int N = c->N;
+    const long long NN = (long long)N * N;
+    double2* P = c->PQ;
+    double2* Q = c->PQ + (long long)nk * NN;
+    GKBA_TRY(zgemm_batched(c, K_PREP, N, 'N', 'N', make_double2(1.0, 0.0), T + k0 * NN, NN,
+                           rho + k0 * NN, NN, make_double2(0.0, 0.0), P, NN, nk, 0));
+    {
+        auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+        k_lincomb<<<grid1(nk * NN, 256), 256, 0, c->stream>>>(nk * NN, Q, T + k0 * NN, P, 1.0, -1.0);
+        GKBA_TRY(launch_end(c, t));
+    }
+    {
+        auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+        k_gkba_units<<<grid1(nk * NN, 256), 256, 0, c->stream>>>(N, nk, k0, L, c->dt, P, Q, w,
+                                                                  c->Su, c->Mb, c->coef);
+        GKBA_TRY(launch_end(c, t));
+    }
+    return build_forms(c, 2 * nk, c->Su, NN, c->Mb, NN, 0);
+}
+
+gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
+    const long long NN = (long long)c->N * c->N;
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_forms64<<<grid1(nb * NN, 256), 256, 0, c->stream>>>(c->N, nb, G, Gb, (double*)c->formsB1,
+                                                          (double*)c->formsG);
+    return launch_end(c, t);
+}
+
+gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
+                                   const void* part, bool fp32, double2* S) {
+    const long long NN = (long long)c->N * c->N;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    if (fp32)
+        k_reduce_partials<float><<<grid1(nb * NN, 256), 256, 0, c->stream>>>(
+            c->N, c->prec == GKBA_SPLIT_TF32 ? c->Np : c->N, nb, nz, zstride, Rld,
+            (const float*)part, S);
+    else
+        k_reduce_partials<double><<<grid1(nb * NN, 256), 256, 0, c->stream>>>(
+            c->N, c->N, nb, nz, zstride, Rld, (const double*)part, S);
+    return launch_end(c, t);
+}
+
+// Y_u = S_u Gb_u, I_acc += sum_u coef_u Y_u (fixed order).  When S_out is
+// non-null the S_u are copied out instead (gkba_sigma).
+gkba_status reduce_batch(gkba_ctx* c, int nb, double2* I_acc, double2* S_out) {
+    const int N = c->N;
+    const long long NN = (long long)N * N;
+    if (S_out != nullptr) {
+        GKBA_CUDA(c, cudaMemcpyAsync(S_out, c->Su, nb * NN * sizeof(double2),
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        return GKBA_OK;
+    }
+    GKBA_TRY(zgemm_batched(c, K_RED, N, 'N', 'N', make_double2(1.0, 0.0), c->Su, NN, c->Mb, NN,
+                           make_double2(0.0, 0.0), c->Yu, NN, nb, 0));
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_weighted_sum<<<grid1(NN, 256), 256, 0, c->stream>>>((int)NN, nb, c->coef, c->Yu, I_acc);
+    return launch_end(c, t);
+}
+
+// FP64 contraction of one batch (units 0..nb-1 with forms built):
+//   S1  X1[j][r][m][c][q] = sum_s wS[j][m][q][s] B1[(c,r)][s]
+//   S2  X2[j][r][p][c'][m] = sum_(c,q) X1[(j,r,m)][(c,q)] Gr[(c',p)][(c,q)]
+//   S3  X3[c'][j][n][r][p] = sum_(c,m) X2[(j,r,p)][(c,m)] Gr[(c',n)][(c,m)]
+//   S4  D[(u,c,j)][i] = sum_(n,r,p) X3[u][(c,j)][(n,r,p)] vK[i][(n,r,p)], split-K
+// i.e. W1 = w x_s Gb, W2 = G x_q W1, W3 = G x_m W2, Sigma = v . W3.
+gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
+    const int N = c->N;
+    const long long N2 = (long long)N * N, N3 = N2 * N, N4 = N3 * N;
+    double* X13 = (double*)c->X13;
+    double* X2 = (double*)c->X2;
+    const double fl_cr = 4.0 * (double)N4 * N;   // complex x real stage, per unit
+    const double fl_cc = 8.0 * (double)N4 * N;   // complex x complex stage, per unit
+    {
+        StageMap m{2 * N3, 2 * N, 1, N, 2 * N2, N, N, N};
+        GKBA_TRY(gemm64_stage(c, K_W1, c->wS64, N, 0, (const double*)c->formsB1, N, 2 * N2, X13,
+                              2 * N4, (int)N3, 2 * N, N, nb, 0, 0, m, fl_cr * nb,
+                              8.0 * (N4 + 2 * N4 * nb)));
+    }
+    {
+        StageMap m{2 * N3, 2 * N2, 1, N, 2 * N, N, N, N};
+        GKBA_TRY(gemm64_stage(c, K_W2, X13, 2 * N, 2 * N4, (const double*)c->formsG, 2 * N, 4 * N2,
+                              X2, 2 * N4, (int)N3, 2 * N, 2 * N, nb, 0, 0, m, fl_cc * nb,
+                              8.0 * 4 * N4 * nb));
+    }
+    {
+        StageMap m{N3, N, 1, N4, N2, N, N, N};
+        GKBA_TRY(gemm64_stage(c, K_W3, X2, 2 * N, 2 * N4, (const double*)c->formsG, 2 * N, 4 * N2,
+                              X13, 2 * N4, (int)N3, 2 * N, 2 * N, nb, 0, 0, m, fl_cc * nb,
+                              8.0 * 4 * N4 * nb));
+    }
+    const long long R = 2LL * N * nb;
+    const long long Kc = 8192;
+    const int nz = (int)((N3 + Kc - 1) / Kc);
+    {
+        StageMap m{0, 0, 1, 0, R, (int)R, 1, N};
+        GKBA_TRY(gemm64_stage(c, K_FIN, X13, N3, 0, c->vK64, N3, 0, (double*)c->part, N * R,
+                              (int)R, N, N3, nz, 1, Kc, m, fl_cr * nb,
+                              8.0 * (2 * N4 * nb + N4)));
+    }
+    return reduce_partials_launch(c, nb, nz, N * R, R, c->part, false, c->Su);
+}
+
+}  // namespace gkba

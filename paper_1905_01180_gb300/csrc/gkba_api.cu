@@ -1,0 +1,685 @@
+// gkba_api.cu - C ABI entry points of libgkba: context life cycle, input
+// validation, the history store, the contraction driver (collision integral
+// of Eq. (collint) over a batched list of (t_k, component) units) and the
+// Heun stepper of Eq. (equalt).  See include/gkba.h for the contract.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+
+#include "gkba_internal.cuh"
+
+namespace gkba {
+
+const char* kKernelClassNames[K_COUNT] = {"S1_w_x_Gbar", "S2_G_x_X1", "S3_G_x_X2", "S4_v_dot_X3",
+                                          "prep",        "reduce",    "stepper"};
+
+static std::mutex g_err_mu;
+static std::string g_last_init_error;
+
+gkba_status fail(gkba_ctx* c, gkba_status st, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_last_init_error = buf;
+    }
+    return st;
+}
+
+LaunchToken launch_begin(gkba_ctx* c, int cls, double flops, double bytes) {
+    LaunchToken t{cls, nullptr};
+    c->launches++;
+    c->cls_launches[cls]++;
+    c->cls_flops[cls] += flops;
+    c->cls_bytes[cls] += bytes;
+    if (c->timing && (cls == K_W1 || cls == K_W2 || cls == K_W3 || cls == K_FIN)) {
+        cudaEvent_t a;
+        if (!c->event_pool.empty()) {
+            a = c->event_pool.back();
+            c->event_pool.pop_back();
+        } else if (cudaEventCreate(&a) != cudaSuccess) {
+            return t;
+        }
+        cudaEventRecord(a, c->stream);
+        t.a = a;
+    }
+    return t;
+}
+
+gkba_status launch_end(gkba_ctx* c, LaunchToken t) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(c, GKBA_ECUDA, "kernel launch (%s) failed: %s", kKernelClassNames[t.cls],
+                    cudaGetErrorString(e));
+    if (t.a) {
+        cudaEvent_t b;
+        if (!c->event_pool.empty()) {
+            b = c->event_pool.back();
+            c->event_pool.pop_back();
+        } else if (cudaEventCreate(&b) != cudaSuccess) {
+            c->event_pool.push_back(t.a);
+            return GKBA_OK;
+        }
+        cudaEventRecord(b, c->stream);
+        c->pending.push_back(TimedLaunch{t.cls, t.a, b});
+    }
+    return GKBA_OK;
+}
+
+gkba_status harvest_timing(gkba_ctx* c) {
+    if (c->pending.empty()) return GKBA_OK;
+    GKBA_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->cls_ms[p.cls] += ms;
+        c->event_pool.push_back(p.a);
+        c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+    return GKBA_OK;
+}
+
+// Allocation helper: carve aligned sub-buffers out of one block.
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    }
+};
+
+gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
+    const long long N = c->N, NN = N * N;
+    want_units = std::max(2, want_units + (want_units & 1));
+    const bool tc = c->prec == GKBA_SPLIT_TF32;
+    const long long Np = c->Np;
+    const double x_bytes = tc ? 2.0 * Np * Np * Np * Np * 4 : 2.0 * NN * NN * 8;
+    const double form_bytes = tc ? 4.0 * 2 * Np * Np * 4 : (2.0 * NN + 4.0 * NN) * 8;
+    const double N3 = (double)NN * N;
+    const double part_per_unit = tc ? (std::ceil((double)Np * Np * Np / 4096.0) * Np * 2.0 * Np * 4)
+                                    : (std::ceil(N3 / 8192.0) * N * 2.0 * N * 8);
+    const double per_unit = 2 * x_bytes + form_bytes + part_per_unit + 4.0 * NN * 16 + 8;
+    size_t cap = c->ws_cap;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const size_t usable = (size_t)((double)(free_b + c->ws_bytes) * 0.85);
+        cap = std::min(cap, usable);
+    }
+    long long fit = (long long)((double)cap / per_unit);
+    fit -= fit & 1;
+    if (fit < 2)
+        return fail(c, GKBA_ENOMEM, "workspace cap %.3g GB holds fewer than 2 units (%.3g GB each)",
+                    cap / 1e9, per_unit / 1e9);
+    int ub = (int)std::min<long long>(fit, want_units);
+    if (c->ws && ub <= c->ub_cap) {
+        c->ub = ub;
+        return GKBA_OK;
+    }
+    if (c->ws) {
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    Carver cv;
+    const size_t oX13 = cv.take((size_t)(x_bytes * ub));
+    const size_t oX2 = cv.take((size_t)(x_bytes * ub));
+    size_t part_bytes;
+    if (tc) part_bytes = tf32_part_bytes((int)Np, ub);
+    else {
+        const long long nz = (long long)std::ceil(N3 / 8192.0);
+        part_bytes = (size_t)(nz * N * 2LL * N * ub * 8);
+    }
+    const size_t oPart = cv.take(part_bytes);
+    const size_t oB1 = cv.take(tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(2LL * NN * ub * 8));
+    const size_t oG = cv.take(tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(4LL * NN * ub * 8));
+    const size_t oPQ = cv.take((size_t)(ub * NN * 16));
+    const size_t oMb = cv.take((size_t)(ub * NN * 16));
+    const size_t oCoef = cv.take((size_t)ub * 8);
+    const size_t oSu = cv.take((size_t)(ub * NN * 16));
+    const size_t oYu = cv.take((size_t)(ub * NN * 16));
+    void* ws = nullptr;
+    if (cudaMalloc(&ws, cv.off) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GKBA_ENOMEM, "cudaMalloc(%zu) for the contraction workspace failed", cv.off);
+    }
+    char* b = (char*)ws;
+    c->ws = ws;
+    c->ws_bytes = cv.off;
+    c->ub = ub;
+    c->ub_cap = ub;
+    c->X13 = b + oX13;
+    c->X2 = b + oX2;
+    c->part = b + oPart;
+    c->part_bytes = part_bytes;
+    c->formsB1 = b + oB1;
+    c->formsG = b + oG;
+    c->PQ = (double2*)(b + oPQ);
+    c->Mb = (double2*)(b + oMb);
+    c->coef = (double*)(b + oCoef);
+    c->Su = (double2*)(b + oSu);
+    c->Yu = (double2*)(b + oYu);
+    return GKBA_OK;
+}
+
+gkba_status ensure_stage(gkba_ctx* c, size_t bytes) {
+    if (bytes <= c->stage_bytes) return GKBA_OK;
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    if (cudaMalloc(&c->stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GKBA_ENOMEM, "cudaMalloc(%zu) for staging failed", bytes);
+    }
+    c->stage_bytes = bytes;
+    return GKBA_OK;
+}
+
+static gkba_status contract(gkba_ctx* c, int nb) {
+    if (c->prec == GKBA_SPLIT_TF32) return contract_batch_tf32(c, nb);
+    return contract_batch_fp64(c, nb);
+}
+
+gkba_status collision_dev(gkba_ctx* c, int L, const double2* rho, const double2* T,
+                          const double* weights_dev, double2* I_out) {
+    const long long NN = (long long)c->N * c->N;
+    GKBA_CUDA(c, cudaMemsetAsync(I_out, 0, NN * sizeof(double2), c->stream));
+    if (L <= 1 && weights_dev == nullptr) return GKBA_OK;  // zero-length time interval
+    GKBA_TRY(ensure_workspace(c, 2 * L));
+    const int nk_per = c->ub / 2;
+    for (int k0 = 0; k0 < L; k0 += nk_per) {
+        const int nk = std::min(nk_per, L - k0);
+        GKBA_TRY(build_forms_gkba(c, k0, nk, L, rho, T, weights_dev));
+        GKBA_TRY(contract(c, 2 * nk));
+        GKBA_TRY(reduce_batch(c, 2 * nk, I_out, nullptr));
+    }
+    return GKBA_OK;
+}
+
+gkba_status sigma_dev(gkba_ctx* c, int n_units, const double2* G, const double2* Gb, double2* S_out) {
+    const long long NN = (long long)c->N * c->N;
+    GKBA_TRY(ensure_workspace(c, n_units));
+    for (int u0 = 0; u0 < n_units; u0 += c->ub) {
+        const int nb = std::min(c->ub, n_units - u0);
+        GKBA_TRY(build_forms(c, nb, G + u0 * NN, NN, Gb + u0 * NN, NN, 0));
+        GKBA_TRY(contract(c, nb));
+        GKBA_TRY(reduce_batch(c, nb, nullptr, S_out + u0 * NN));
+    }
+    return GKBA_OK;
+}
+
+// After a public call: wait for the stream, fold timings, check the device
+// error word written by bounded waits.
+static gkba_status finish(gkba_ctx* c) {
+    GKBA_CUDA(c, cudaStreamSynchronize(c->stream));
+    GKBA_TRY(harvest_timing(c));
+    int errw = 0;
+    GKBA_CUDA(c, cudaMemcpy(&errw, c->dint + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errw != 0) {
+        cudaMemset(c->dint + 1, 0, sizeof(int));
+        return fail(c, GKBA_ETIMEOUT, "device-side wait timed out (code %d); results invalid", errw);
+    }
+    return GKBA_OK;
+}
+
+}  // namespace gkba
+
+using namespace gkba;
+
+namespace {
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Max |A - A^+| relative to max |A| for an interleaved complex N x N matrix.
+bool hermitian(const double* a, int N, double tol) {
+    double mx = 0.0, dev = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            const double re = a[2 * (i * N + j)], im = a[2 * (i * N + j) + 1];
+            const double tre = a[2 * (j * N + i)], tim = a[2 * (j * N + i) + 1];
+            mx = std::max(mx, std::hypot(re, im));
+            dev = std::max(dev, std::hypot(re - tre, im + tim));
+        }
+    return dev <= tol * std::max(mx, 1e-300);
+}
+
+// Eq. (symmetries): v_ijkl = v_jilk = v_klij = v_lkji = v_ikjl = v_ljki = v_kilj = v_jlik.
+bool eightfold(const double* v, int N, double tol) {
+    const long long n = N;
+    double mx = 0.0;
+    for (long long e = 0; e < n * n * n * n; ++e) mx = std::max(mx, std::fabs(v[e]));
+    const double lim = tol * std::max(mx, 1e-300);
+    auto at = [&](long long i, long long j, long long k, long long l) { return v[((i * n + j) * n + k) * n + l]; };
+    for (long long i = 0; i < n; ++i)
+        for (long long j = 0; j < n; ++j)
+            for (long long k = 0; k < n; ++k)
+                for (long long l = 0; l < n; ++l) {
+                    const double x = at(i, j, k, l);
+                    if (std::fabs(x - at(j, i, l, k)) > lim || std::fabs(x - at(k, l, i, j)) > lim ||
+                        std::fabs(x - at(l, k, j, i)) > lim || std::fabs(x - at(i, k, j, l)) > lim ||
+                        std::fabs(x - at(l, j, k, i)) > lim || std::fabs(x - at(k, i, l, j)) > lim ||
+                        std::fabs(x - at(j, l, i, k)) > lim)
+                        return false;
+                }
+    return true;
+}
+
+gkba_status copy_in(gkba_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
+    GKBA_CUDA(c, cudaMemcpyAsync(dst, src, bytes,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 c->stream));
+    return GKBA_OK;
+}
+
+gkba_status alloc(gkba_ctx* c, void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, GKBA_ENOMEM, "cudaMalloc(%zu) failed", bytes);
+    }
+    return GKBA_OK;
+}
+
+void free_ctx(gkba_ctx* c) {
+    if (!c) return;
+    if (c->device >= 0) cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    void* ptrs[] = {c->h, c->d, c->v, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
+                    c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
+                    c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
+                    c->stage};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->hdiag) cudaFreeHost(c->hdiag);
+    for (auto& p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // namespace
+
+namespace gkba {
+gkba_status fp64_prepare_model(gkba_ctx* c);
+}
+
+extern "C" {
+
+gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, const double* v,
+                      const double* d, const double* rho0, int inputs_on_device) {
+    if (out) *out = nullptr;
+    if (!out || !cfg) return fail(nullptr, GKBA_EINVAL, "gkba_init: out and cfg must be non-NULL");
+    if (!h || !v || !d || !rho0) return fail(nullptr, GKBA_EINVAL, "gkba_init: NULL model input");
+    const int N = cfg->N;
+    if (N < 1 || N > 128) return fail(nullptr, GKBA_EINVAL, "gkba_init: N=%d outside [1, 128]", N);
+    if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt))
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: dt must be positive and finite");
+    if (cfg->max_steps < 0 || cfg->max_steps > 100000000)
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: max_steps=%d invalid", cfg->max_steps);
+    if (cfg->precision != GKBA_FP64 && cfg->precision != GKBA_SPLIT_TF32)
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown precision %d", cfg->precision);
+    const int Np = ((N + 15) / 16) * 16;
+    if (cfg->precision == GKBA_SPLIT_TF32 && Np > 96)
+        return fail(nullptr, GKBA_EINVAL,
+                    "gkba_init: the split-TF32 path supports N <= 96 (N=%d)", N);
+    const size_t NN = (size_t)N * N, N4 = NN * NN;
+
+    // Host copies for validation (device inputs are copied back first).
+    std::vector<double> hh(2 * NN), dh(2 * NN), rh(2 * NN), vh(N4);
+    if (inputs_on_device) {
+        if (cudaMemcpy(hh.data(), h, 2 * NN * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(dh.data(), d, 2 * NN * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(rh.data(), rho0, 2 * NN * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(vh.data(), v, N4 * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(nullptr, GKBA_EINVAL, "gkba_init: inputs_on_device but a pointer is not readable device memory");
+        }
+    } else {
+        memcpy(hh.data(), h, 2 * NN * 8);
+        memcpy(dh.data(), d, 2 * NN * 8);
+        memcpy(rh.data(), rho0, 2 * NN * 8);
+        memcpy(vh.data(), v, N4 * 8);
+    }
+    if (!finite_all(hh.data(), 2 * NN) || !finite_all(dh.data(), 2 * NN) ||
+        !finite_all(rh.data(), 2 * NN) || !finite_all(vh.data(), N4))
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: non-finite values in h, v, d or rho0");
+    if (!hermitian(hh.data(), N, 1e-10)) return fail(nullptr, GKBA_EINVAL, "gkba_init: h is not Hermitian");
+    if (!hermitian(dh.data(), N, 1e-10)) return fail(nullptr, GKBA_EINVAL, "gkba_init: d is not Hermitian");
+    if (!hermitian(rh.data(), N, 1e-10)) return fail(nullptr, GKBA_EINVAL, "gkba_init: rho0 is not Hermitian");
+    if (!eightfold(vh.data(), N, 1e-10))
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: v breaks the 8-fold permutation symmetry");
+
+    gkba_ctx* c = new gkba_ctx();
+    c->N = N;
+    c->Np = Np;
+    c->dt = cfg->dt;
+    c->max_steps = cfg->max_steps;
+    c->prec = cfg->precision;
+    c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)16 << 30);
+    c->timing = cfg->timing != 0;
+    c->device = -1;
+    auto bail = [&](gkba_status st) {
+        {
+            std::lock_guard<std::mutex> g(g_err_mu);
+            g_last_init_error = c->err;
+        }
+        free_ctx(c);
+        return st;
+    };
+    int dev = cfg->device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            fail(c, GKBA_ECUDA, "gkba_init: no CUDA device");
+            return bail(GKBA_ECUDA);
+        }
+    }
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        fail(c, GKBA_ECUDA, "gkba_init: cudaSetDevice(%d) failed", dev);
+        return bail(GKBA_ECUDA);
+    }
+    c->device = dev;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        fail(c, GKBA_ECUDA, "gkba_init: cudaGetDeviceProperties failed");
+        return bail(GKBA_ECUDA);
+    }
+    c->num_sms = prop.multiProcessorCount;
+    if (c->prec == GKBA_SPLIT_TF32 && !(prop.major == 10 && prop.minor == 3)) {
+        fail(c, GKBA_EUNSUPPORTED, "gkba_init: split-TF32 path needs an sm_103 GPU (found sm_%d%d)",
+             prop.major, prop.minor);
+        return bail(GKBA_EUNSUPPORTED);
+    }
+    if (cfg->cuda_stream) {
+        c->stream = (cudaStream_t)cfg->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(c, GKBA_ECUDA, "gkba_init: stream creation failed");
+            return bail(GKBA_ECUDA);
+        }
+        c->own_stream = true;
+    }
+    const size_t cap = (size_t)c->max_steps + 1;
+    gkba_status st = GKBA_OK;
+#define ALLOC(ptr, bytes)                                                  \
+    do {                                                                   \
+        void* p_ = nullptr;                                                \
+        st = alloc(c, &p_, (bytes));                                       \
+        if (st != GKBA_OK) return bail(st);                                \
+        ptr = (decltype(ptr))p_;                                           \
+    } while (0)
+    ALLOC(c->h, NN * 16);
+    ALLOC(c->d, NN * 16);
+    ALLOC(c->v, N4 * 8);
+    ALLOC(c->hfK, N4 * 8);
+    ALLOC(c->rho_hist, cap * NN * 16);
+    ALLOC(c->T_a, cap * NN * 16);
+    ALLOC(c->T_b, cap * NN * 16);
+    ALLOC(c->hhf_n, NN * 16);
+    ALLOC(c->hhf_t, NN * 16);
+    ALLOC(c->k1, NN * 16);
+    ALLOC(c->k2, NN * 16);
+    ALLOC(c->Ia, NN * 16);
+    ALLOC(c->Ib, NN * 16);
+    ALLOC(c->U, NN * 16);
+    ALLOC(c->ex0, NN * 16);
+    ALLOC(c->ex1, NN * 16);
+    ALLOC(c->ex2, NN * 16);
+    ALLOC(c->tmp0, NN * 16);
+    ALLOC(c->tmp1, NN * 16);
+    ALLOC(c->dscal, 16 * 8);
+    ALLOC(c->dint, 4 * 4);
+    if (c->prec == GKBA_FP64) {
+        ALLOC(c->wS64, N4 * 8);
+        ALLOC(c->vK64, N4 * 8);
+    } else {
+        const size_t Np4 = (size_t)Np * Np * Np * Np;
+        ALLOC(c->wS32, Np4 * 4);
+        ALLOC(c->vKhi, Np4 * 4);
+        ALLOC(c->vKlo, Np4 * 4);
+    }
+#undef ALLOC
+    if (cudaMallocHost((void**)&c->hdiag, 16 * 8) != cudaSuccess) {
+        fail(c, GKBA_ENOMEM, "cudaMallocHost failed");
+        return bail(GKBA_ENOMEM);
+    }
+    if ((st = copy_in(c, c->h, hh.data(), NN * 16, 0)) != GKBA_OK) return bail(st);
+    if ((st = copy_in(c, c->d, dh.data(), NN * 16, 0)) != GKBA_OK) return bail(st);
+    if ((st = copy_in(c, c->v, vh.data(), N4 * 8, 0)) != GKBA_OK) return bail(st);
+    if ((st = copy_in(c, c->rho_hist, rh.data(), NN * 16, 0)) != GKBA_OK) return bail(st);
+    if (cudaMemsetAsync(c->dint, 0, 16, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->dscal, 0, 128, c->stream) != cudaSuccess) {
+        fail(c, GKBA_ECUDA, "gkba_init: memset failed");
+        return bail(GKBA_ECUDA);
+    }
+    if ((st = set_identity(c, c->T_a, 1)) != GKBA_OK) return bail(st);
+    if ((st = fp64_prepare_model(c)) != GKBA_OK) return bail(st);
+    if (c->prec == GKBA_SPLIT_TF32 && (st = tf32_prepare_model(c)) != GKBA_OK) return bail(st);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        fail(c, GKBA_ECUDA, "gkba_init: %s", cudaGetErrorString(cudaGetLastError()));
+        return bail(GKBA_ECUDA);
+    }
+    c->n = 0;
+    *out = c;
+    return GKBA_OK;
+}
+
+gkba_status gkba_sigma(gkba_ctx* c, int n_units, const double* G, const double* Gbar, double* S_out,
+                       int on_device) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_sigma: NULL context");
+    if (n_units < 0 || (n_units > 0 && (!G || !Gbar || !S_out)))
+        return fail(c, GKBA_EINVAL, "gkba_sigma: bad arguments");
+    if (n_units == 0) return GKBA_OK;
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    const size_t NN = (size_t)c->N * c->N, bytes = NN * 16 * (size_t)n_units;
+    const double2 *dG, *dGb;
+    double2* dS;
+    if (on_device) {
+        dG = (const double2*)G;
+        dGb = (const double2*)Gbar;
+        dS = (double2*)S_out;
+    } else {
+        GKBA_TRY(ensure_stage(c, 3 * bytes));
+        dG = (double2*)c->stage;
+        dGb = (double2*)((char*)c->stage + bytes);
+        dS = (double2*)((char*)c->stage + 2 * bytes);
+        GKBA_TRY(copy_in(c, (void*)dG, G, bytes, 0));
+        GKBA_TRY(copy_in(c, (void*)dGb, Gbar, bytes, 0));
+    }
+    GKBA_TRY(sigma_dev(c, n_units, dG, dGb, dS));
+    if (!on_device)
+        GKBA_CUDA(c, cudaMemcpyAsync(S_out, dS, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return finish(c);
+}
+
+gkba_status gkba_collision(gkba_ctx* c, int L, const double* rho_hist, const double* T_hist,
+                           const double* weights, double* I_out, int on_device) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_collision: NULL context");
+    if (L < 1 || !rho_hist || !T_hist || !I_out)
+        return fail(c, GKBA_EINVAL, "gkba_collision: need L >= 1 and non-NULL history and output");
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    const size_t NN = (size_t)c->N * c->N, hb = NN * 16 * (size_t)L;
+    if (weights && !on_device) {
+        for (int k = 0; k < L; ++k)
+            if (!std::isfinite(weights[k])) return fail(c, GKBA_EINVAL, "gkba_collision: non-finite weight");
+    }
+    const double2 *dR, *dT;
+    const double* dW = nullptr;
+    double2* dI;
+    const size_t wb = ((size_t)L * 8 + 255) & ~(size_t)255;
+    if (on_device) {
+        dR = (const double2*)rho_hist;
+        dT = (const double2*)T_hist;
+        dW = weights;
+        dI = (double2*)I_out;
+    } else {
+        GKBA_TRY(ensure_stage(c, 2 * hb + wb + NN * 16));
+        char* s = (char*)c->stage;
+        dR = (double2*)s;
+        dT = (double2*)(s + hb);
+        double* w = (double*)(s + 2 * hb);
+        dI = (double2*)(s + 2 * hb + wb);
+        GKBA_TRY(copy_in(c, (void*)dR, rho_hist, hb, 0));
+        GKBA_TRY(copy_in(c, (void*)dT, T_hist, hb, 0));
+        if (weights) {
+            GKBA_TRY(copy_in(c, w, weights, (size_t)L * 8, 0));
+            dW = w;
+        }
+    }
+    GKBA_TRY(collision_dev(c, L, dR, dT, dW, dI));
+    if (!on_device)
+        GKBA_CUDA(c, cudaMemcpyAsync(I_out, dI, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+    return finish(c);
+}
+
+gkba_status gkba_mean_field(gkba_ctx* c, const double* rho, double* sigma_hf, int on_device) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_mean_field: NULL context");
+    if (!rho || !sigma_hf) return fail(c, GKBA_EINVAL, "gkba_mean_field: NULL argument");
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    const size_t NN = (size_t)c->N * c->N;
+    const double2* dR;
+    double2* dO;
+    if (on_device) {
+        dR = (const double2*)rho;
+        dO = (double2*)sigma_hf;
+    } else {
+        GKBA_TRY(ensure_stage(c, 2 * NN * 16));
+        dR = (double2*)c->stage;
+        dO = (double2*)((char*)c->stage + NN * 16);
+        GKBA_TRY(copy_in(c, (void*)dR, rho, NN * 16, 0));
+    }
+    GKBA_TRY(mean_field(c, dR, dO));
+    if (!on_device) GKBA_CUDA(c, cudaMemcpyAsync(sigma_hf, dO, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+    return finish(c);
+}
+
+gkba_status gkba_step(gkba_ctx* c, double E_n, double E_np1, double* rho_out, double* I_out,
+                      double* diag_out) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_step: NULL context");
+    if (!std::isfinite(E_n) || !std::isfinite(E_np1))
+        return fail(c, GKBA_EINVAL, "gkba_step: non-finite field sample");
+    if (c->n >= c->max_steps)
+        return fail(c, GKBA_ESTATE, "gkba_step: history full (n=%d, max_steps=%d)", c->n, c->max_steps);
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    const int n = c->n;
+    const long long NN = (long long)c->N * c->N;
+    double2* rho_n = c->rho_hist + n * NN;
+    double2* rho_t = c->rho_hist + (n + 1) * NN;
+    // predictor
+    GKBA_TRY(h_hf(c, E_n, rho_n, c->hhf_n));
+    GKBA_TRY(collision_dev(c, n + 1, c->rho_hist, c->T_a, nullptr, c->Ia));
+    GKBA_TRY(diagnostics(c, E_n, rho_n, c->Ia, c->dscal));
+    GKBA_TRY(rhs(c, c->hhf_n, rho_n, c->Ia, c->k1));
+    GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k1, 1.0, c->dt, (int)NN));
+    GKBA_TRY(h_hf(c, E_np1, rho_t, c->hhf_t));
+    // propagator recursion T(t_{n+1}, t_k) = U_n T(t_n, t_k); T(t_{n+1}, t_{n+1}) = 1
+    GKBA_TRY(expm_step(c, c->hhf_n, c->hhf_t, c->U));
+    GKBA_TRY(zgemm_batched(c, K_STEP, c->N, 'N', 'N', make_double2(1.0, 0.0), c->U, 0, c->T_a, NN,
+                           make_double2(0.0, 0.0), c->T_b, NN, n + 1, 0));
+    GKBA_TRY(set_identity(c, c->T_b + (n + 1) * NN, 1));
+    // corrector
+    GKBA_TRY(collision_dev(c, n + 2, c->rho_hist, c->T_b, nullptr, c->Ib));
+    GKBA_TRY(rhs(c, c->hhf_t, rho_t, c->Ib, c->k2));
+    GKBA_TRY(axpy_c(c, c->k2, c->k1, c->k2, 1.0, 1.0, (int)NN));
+    GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k2, 1.0, 0.5 * c->dt, (int)NN));
+    std::swap(c->T_a, c->T_b);
+    c->n = n + 1;
+    if (rho_out)
+        GKBA_CUDA(c, cudaMemcpyAsync(rho_out, rho_t, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+    if (I_out) GKBA_CUDA(c, cudaMemcpyAsync(I_out, c->Ia, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+    if (diag_out) GKBA_CUDA(c, cudaMemcpyAsync(c->hdiag, c->dscal, 4 * 8, cudaMemcpyDeviceToHost, c->stream));
+    GKBA_TRY(finish(c));
+    if (diag_out) memcpy(diag_out, c->hdiag, 4 * 8);
+    return GKBA_OK;
+}
+
+gkba_status gkba_set_history(gkba_ctx* c, int n, const double* rho_hist, const double* T_hist,
+                             int on_device) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_set_history: NULL context");
+    if (n < 0 || n > c->max_steps || !rho_hist || !T_hist)
+        return fail(c, GKBA_EINVAL, "gkba_set_history: n=%d outside [0, max_steps=%d] or NULL", n,
+                    c->max_steps);
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    const size_t bytes = (size_t)(n + 1) * c->N * c->N * 16;
+    GKBA_TRY(copy_in(c, c->rho_hist, rho_hist, bytes, on_device));
+    GKBA_TRY(copy_in(c, c->T_a, T_hist, bytes, on_device));
+    c->n = n;
+    return finish(c);
+}
+
+gkba_status gkba_get_history(const gkba_ctx* cc, int* n, double* rho_hist, double* T_hist) {
+    gkba_ctx* c = const_cast<gkba_ctx*>(cc);
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_get_history: NULL context");
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    if (n) *n = c->n;
+    const size_t bytes = (size_t)(c->n + 1) * c->N * c->N * 16;
+    if (rho_hist) GKBA_CUDA(c, cudaMemcpyAsync(rho_hist, c->rho_hist, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (T_hist) GKBA_CUDA(c, cudaMemcpyAsync(T_hist, c->T_a, bytes, cudaMemcpyDeviceToHost, c->stream));
+    GKBA_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GKBA_OK;
+}
+
+gkba_status gkba_get_state(const gkba_ctx* cc, int* n, double* rho) {
+    gkba_ctx* c = const_cast<gkba_ctx*>(cc);
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_get_state: NULL context");
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    if (n) *n = c->n;
+    if (rho) {
+        const size_t NN = (size_t)c->N * c->N;
+        GKBA_CUDA(c, cudaMemcpyAsync(rho, c->rho_hist + c->n * NN, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+        GKBA_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return GKBA_OK;
+}
+
+gkba_status gkba_adjoint(gkba_ctx* c, const double*, int, int, const double*, double*, double*) {
+    return fail(c, GKBA_EUNSUPPORTED, "gkba_adjoint is not implemented in this build");
+}
+
+gkba_status gkba_get_stats(gkba_ctx* c, gkba_kernel_stat* stats, int max_stats, int* n_stats,
+                           long long* total_launches, int reset) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_get_stats: NULL context");
+    GKBA_TRY(harvest_timing(c));
+    const int n = std::min(max_stats, (int)K_COUNT);
+    for (int i = 0; stats && i < n; ++i) {
+        stats[i].name = kKernelClassNames[i];
+        stats[i].launches = c->cls_launches[i];
+        stats[i].ms = c->cls_ms[i];
+        stats[i].flops = c->cls_flops[i];
+        stats[i].bytes = c->cls_bytes[i];
+    }
+    if (n_stats) *n_stats = stats ? n : 0;
+    if (total_launches) *total_launches = c->launches;
+    if (reset) {
+        c->launches = 0;
+        for (int i = 0; i < K_COUNT; ++i) {
+            c->cls_launches[i] = 0;
+            c->cls_ms[i] = c->cls_flops[i] = c->cls_bytes[i] = 0.0;
+        }
+    }
+    return GKBA_OK;
+}
+
+const char* gkba_last_error(const gkba_ctx* c) {
+    if (c) return c->err.c_str();
+    std::lock_guard<std::mutex> g(g_err_mu);
+    return g_last_init_error.c_str();
+}
+
+void gkba_destroy(gkba_ctx* c) { free_ctx(c); }
+
+}  // extern "C"

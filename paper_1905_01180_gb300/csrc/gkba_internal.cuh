@@ -1,0 +1,223 @@
+// gkba_internal.cuh - context, kernel classes and launch helpers shared by the
+// translation units of libgkba (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/gkba.h"
+
+namespace gkba {
+
+// Kernel classes counted by gkba_get_stats.  The algorithmic flops and bytes
+// of each launch are added at launch time (see the per-class comments in
+// gkba_api.cu).
+enum KernelClass : int {
+    K_W1 = 0,    // S1: X1 = w x_s Gbar          (real x complex, 4 N^5 / unit)
+    K_W2,        // S2: X2 = G x_q X1            (complex x complex, 8 N^5 / unit)
+    K_W3,        // S3: X3 = G x_m X2            (complex x complex, 8 N^5 / unit)
+    K_FIN,       // S4: S = v . X3 over (n,r,p)  (real x complex, 4 N^5 / unit, split-K)
+    K_PREP,      // P/Q reconstruction and per-unit operand forms
+    K_RED,       // split-K reduction, S.Gbar products, weighted history sum
+    K_STEP,      // mean field, commutators, expm, T recursion, Heun update
+    K_COUNT
+};
+
+extern const char* kKernelClassNames[K_COUNT];
+
+struct TimedLaunch {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+}  // namespace gkba
+
+struct gkba_ctx {
+    // configuration
+    int N = 0;          // basis size
+    int Np = 0;         // padded basis for the tensor-core path (multiple of 16)
+    double dt = 0.0;
+    int max_steps = 0;
+    int prec = GKBA_FP64;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t ws_cap = 0;
+    bool timing = false;
+    int num_sms = 0;
+
+    // model on the device
+    double2* h = nullptr;   // N*N
+    double2* d = nullptr;   // N*N
+    double* v = nullptr;    // N^4, v[i][j][k][l]
+    double* hfK = nullptr;  // N^4, hfK[(i*N+j)*N*N + l*N + k] = 2 v_iklj - v_ikjl
+
+    // FP64 contraction operands (natural N)
+    double* wS64 = nullptr;  // [j][m][q][s] = w_mqsj
+    double* vK64 = nullptr;  // [i][n][r][p] = v_irpn
+
+    // split-TF32 contraction operands (padded Np, zero padding)
+    float* wS32 = nullptr;    // raw FP32 [j][m][q][s]
+    float* vKhi = nullptr;    // TF32-rounded [i][(n,r,p)]
+    float* vKlo = nullptr;    // TF32-rounded remainder
+
+    // history store: slot k holds rho(t_k) and T(t_n, t_k)
+    int n = 0;
+    double2* rho_hist = nullptr;  // (max_steps + 2) * N*N
+    double2* T_a = nullptr;       // current T row
+    double2* T_b = nullptr;       // next T row (double buffer)
+
+    // stepper scratch (N*N complex each unless noted)
+    double2* hhf_n = nullptr;
+    double2* hhf_t = nullptr;
+    double2* k1 = nullptr;
+    double2* k2 = nullptr;
+    double2* Ia = nullptr;       // I(t_n)
+    double2* Ib = nullptr;       // I(t_{n+1}) of the corrector
+    double2* U = nullptr;
+    double2* ex0 = nullptr;      // expm work
+    double2* ex1 = nullptr;
+    double2* ex2 = nullptr;
+    double2* tmp0 = nullptr;
+    double2* tmp1 = nullptr;
+    double* dscal = nullptr;     // device scalars: [0..7] diagnostics, [8] expm norm
+    int* dint = nullptr;         // device ints: [0] expm squarings, [1] error word
+    double* hdiag = nullptr;     // pinned host copy of diagnostics
+
+    // contraction workspace (lazily sized)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int ub = 0;                  // units per batch
+    int ub_cap = 0;              // units the workspace was sized for
+    // sub-buffers inside ws
+    void* X13 = nullptr;
+    void* X2 = nullptr;
+    void* part = nullptr;
+    size_t part_bytes = 0;
+    double2* PQ = nullptr;       // P and Q for ub/2 history points: 2 * (ub/2) * N*N
+    void* formsB1 = nullptr;     // per-unit B operand of S1
+    void* formsG = nullptr;      // per-unit B operand of S2/S3
+    double2* Mb = nullptr;       // per-unit Gbar (= the right factor of S.Gbar), ub * N*N
+    double* coef = nullptr;      // per-unit weight (+-c_k), ub
+    double2* Su = nullptr;       // per-unit S, ub * N*N
+    double2* Yu = nullptr;       // per-unit coef * S . Gbar, ub * N*N
+
+    // caller-buffer staging for host-pointer calls
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+
+    // statistics
+    long long launches = 0;
+    long long cls_launches[gkba::K_COUNT] = {};
+    double cls_ms[gkba::K_COUNT] = {};
+    double cls_flops[gkba::K_COUNT] = {};
+    double cls_bytes[gkba::K_COUNT] = {};
+    std::vector<gkba::TimedLaunch> pending;
+    std::vector<cudaEvent_t> event_pool;
+
+    std::string err;
+};
+
+namespace gkba {
+
+// Record an error message on the context and return the status.
+gkba_status fail(gkba_ctx* c, gkba_status st, const char* fmt, ...);
+
+// Check a CUDA runtime call; on failure record it and return GKBA_ECUDA.
+#define GKBA_CUDA(ctx, call)                                                              \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return ::gkba::fail((ctx), GKBA_ECUDA, "%s failed: %s (%s:%d)", #call,        \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);              \
+    } while (0)
+
+#define GKBA_TRY(expr)                 \
+    do {                               \
+        gkba_status s_ = (expr);       \
+        if (s_ != GKBA_OK) return s_;  \
+    } while (0)
+
+// Launch bookkeeping: count a launch of class cls with its algorithmic flops and
+// bytes, and (when timing) bracket it with events.  Usage:
+//   auto t = launch_begin(ctx, K_W2, flops, bytes); kernel<<<...>>>(...); launch_end(ctx, t);
+struct LaunchToken {
+    int cls;
+    cudaEvent_t a;
+};
+LaunchToken launch_begin(gkba_ctx* c, int cls, double flops, double bytes);
+gkba_status launch_end(gkba_ctx* c, LaunchToken t);
+// Fold finished event pairs into the per-class times (synchronises the stream).
+gkba_status harvest_timing(gkba_ctx* c);
+
+// ---- FP64 kernels (fp64_kernels.cu) ---------------------------------------
+
+// Output scatter of a stage GEMM: row = (a*Db + b)*Dx + x, col = c*Dy + y,
+// offset = a*SA + b*SB + x*SX + c*SC + y*SY.
+struct StageMap {
+    long long SA, SB, SX, SC, SY;
+    int Dx, Db, Dy;
+};
+
+// D[z][row][col] = sum_k A[z][row*lda + k] * B[z][col*ldb + k] (FP64, K-major).
+// Mode 0: z indexes units (per-z strides sAz, sBz, sOz; K = Ktot).
+// Mode 1: z indexes K-chunks of length Kc (split-K; out += z*sOz).
+gkba_status gemm64_stage(gkba_ctx* c, int cls, const double* A, long long lda, long long sAz,
+                         const double* B, long long ldb, long long sBz, double* out,
+                         long long sOz, int M, int Nc, long long Ktot, int nz, int splitk,
+                         long long Kc, StageMap map, double flops, double bytes);
+
+// Complex batched GEMM: C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] (+ I if add_identity),
+// op = 'N' or 'C' (conjugate transpose); square n x n matrices, per-batch strides in elements.
+gkba_status zgemm_batched(gkba_ctx* c, int cls, int n, char opA, char opB, double2 alpha,
+                          const double2* A, long long sA, const double2* B, long long sB,
+                          double2 beta, double2* C, long long sC, int batch, int add_identity);
+
+// Stepper helpers.
+gkba_status mean_field(gkba_ctx* c, const double2* rho, double2* out);
+gkba_status h_hf(gkba_ctx* c, double E, const double2* rho, double2* out);  // h + E d + Sigma_HF
+gkba_status rhs(gkba_ctx* c, const double2* hhf, const double2* rho, const double2* I,
+                double2* out);  // -i[hhf, rho] - (I + I^+)
+gkba_status expm_step(gkba_ctx* c, const double2* hA, const double2* hB,
+                      double2* U);  // U = exp(-i dt (hA + hB)/2)
+gkba_status axpy_c(gkba_ctx* c, double2* y, const double2* x, const double2* z, double a,
+                   double b, int n);  // y = a*x + b*z (elementwise, n complex)
+gkba_status set_identity(gkba_ctx* c, double2* A, int count);  // count N*N identities
+gkba_status diagnostics(gkba_ctx* c, double E_n, const double2* rho, const double2* I,
+                        double* out4);  // device out4 = {Tr rho, E_tot, E_c, ReTrI}
+
+// Contraction driver: I_out (device, N*N) = collision over L history points.
+gkba_status collision_dev(gkba_ctx* c, int L, const double2* rho, const double2* T,
+                          const double* weights_dev, double2* I_out);
+// S_out (device) for n_units (G, Gbar) pairs (device).
+gkba_status sigma_dev(gkba_ctx* c, int n_units, const double2* G, const double2* Gb,
+                      double2* S_out);
+
+// Contraction backends (one batch of units whose forms are already built).
+gkba_status contract_batch_fp64(gkba_ctx* c, int nb);
+gkba_status contract_batch_tf32(gkba_ctx* c, int nb);
+gkba_status tf32_prepare_model(gkba_ctx* c);  // build wS32, vKhi, vKlo
+gkba_status fp64_prepare_model(gkba_ctx* c);  // build wS64, vK64, hfK
+
+// Per-unit operand forms for a batch: units u = 0..nb-1 given (G_u, Gb_u) pointers
+// laid out as G = base_G + u*N*N etc.  Writes formsB1/formsG (precision-specific),
+// Mb (= Gb) and coef.
+gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG,
+                        const double2* Gb, long long sGb, int gb_conj_of_other);
+gkba_status build_forms_gkba(gkba_ctx* c, int k0, int nk, int L, const double2* rho,
+                             const double2* T, const double* w);
+gkba_status reduce_batch(gkba_ctx* c, int nb, double2* I_acc, double2* S_out);
+gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
+gkba_status build_forms_tf32(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
+gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
+                                   const void* part, bool fp32, double2* S);
+size_t tf32_part_bytes(int Np, int ub);
+
+// Workspace sizing: make sure the workspace holds ub units (returns actual ub).
+gkba_status ensure_workspace(gkba_ctx* c, int want_units);
+gkba_status ensure_stage(gkba_ctx* c, size_t bytes);
+
+}  // namespace gkba

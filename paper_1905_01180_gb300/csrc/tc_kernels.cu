@@ -1,0 +1,972 @@
+// tc_kernels.cu - split-TF32 contraction of the second-Born self-energy on
+// the sm_103a tensor cores (tcgen05 + TMA + TMEM).
+//
+// Eq. (2bse) of arXiv:1905.01180 is evaluated as four one-index contractions
+// (Sec. III, "general basis"; the ordering contracts w's s index first):
+//   S1  X1[j][r][m][c][q]  = sum_s  w_mqsj Gb_c[s][r]                 (w real)
+//   S2  X2[j][r][p][c'][m] = sum_q  G[p][q] X1[..][q]                 (complex)
+//   S3  X3[c'][j][n][r][p] = sum_m  G[n][m] X2[..][m]                 (complex)
+//   S4  Sigma[i][j]        = sum_(n,r,p) v_irpn X3[j][n][r][p]         (v real)
+// with w_mqsj = 2 v_mqsj - v_qmsj (direct minus exchange).  Each stage is a
+// real GEMM D[M][Nc] = sum_K A[M][K] B[Nc][K]:
+//   * A (the large, streamed operand) is FP32 in HBM; TMA stages 128 x 32
+//     tiles (128-byte swizzle) in shared memory, a converter warpgroup splits
+//     every element into TF32 hi = rna(x) and lo = rna(x - hi) and writes both
+//     into tensor memory (tcgen05.st), where the MMA reads A;
+//   * B (the small per-unit matrix, or v for S4) is stored pre-split hi/lo;
+//   * each K-step issues hi*hi + hi*lo + lo*hi (3xTF32) into an FP32 TMEM
+//     accumulator; S4 is split over K in chunks of 4096 whose FP32 partial
+//     sums are added in FP64 by the reduction kernel.
+// Complex data is planar: S2/S3 read the (re, im) planes of A as separate
+// K-chunks; the im plane multiplies the [Im G; Re G] halves of B with the
+// instruction descriptor's negate-B bit for -Im A Im G.
+//
+// Every mbarrier wait is bounded (globaltimer); on timeout the kernel raises
+// an abort flag, records an error word, drains its in-flight TMA loads and
+// MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+
+#include "gkba_internal.cuh"
+
+namespace gkba {
+
+namespace {
+
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per wait
+constexpr int kBM = 128;                                   // rows per tile (TMEM lanes)
+constexpr int kKC = 32;                                    // K floats per chunk (128 B rows)
+constexpr int kTileBytes = kBM * kKC * 4;                  // 16 KiB
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase with the given parity.  Returns false when the
+// CTA's abort flag is up or the limit ran out (then it raises the flag and
+// records `code` in the error word).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                          int code) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63u) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > kWaitLimitNs) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* m) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)m) : "memory");
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];" ::"r"(dst),
+        "l"((unsigned long long)m), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int x, int y,
+                                       int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4, %5}], [%2];" ::"r"(dst),
+        "l"((unsigned long long)m), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int x, int y,
+                                       int z, int w) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4, %5, %6}], [%2];" ::"r"(dst),
+        "l"((unsigned long long)m), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[tmem] * B[smem desc], kind::tf32, M = 128.
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, unsigned long long bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+#define R8(a, o) "r"(a[o + 0]), "r"(a[o + 1]), "r"(a[o + 2]), "r"(a[o + 3]), "r"(a[o + 4]), "r"(a[o + 5]), "r"(a[o + 6]), "r"(a[o + 7])
+#define W8(a, o) "=r"(a[o + 0]), "=r"(a[o + 1]), "=r"(a[o + 2]), "=r"(a[o + 3]), "=r"(a[o + 4]), "=r"(a[o + 5]), "=r"(a[o + 6]), "=r"(a[o + 7])
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+        "%29, %30, %31, %32};" ::"r"(taddr),
+        R8(v, 0), R8(v, 8), R8(v, 16), R8(v, 24)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : W8(v, 0), W8(v, 8), W8(v, 16), W8(v, 24)
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : W8(v, 0), W8(v, 8)
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes grouped by 8 (stride-byte-offset 1024), sm_100-family version bit.
+__device__ __forceinline__ unsigned long long desc_sw128(uint32_t saddr) {
+    unsigned long long d = (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+    d |= 1ull << 16;                              // leading byte offset (unused when swizzled)
+    d |= (unsigned long long)(1024 >> 4) << 32;   // stride byte offset
+    d |= 1ull << 46;                              // descriptor version
+    d |= 2ull << 61;                              // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32, K-major,
+// M = 128, N = n, optional negation of B.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n, int negB) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negB << 14) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+// Split row r (0..127) of a 128 x 32 FP32 tile written by TMA with the 128-byte
+// swizzle into TF32 hi / lo and store them in TMEM columns [col, col+32) and
+// [col+32, col+64) of this warp's lanes.
+__device__ __forceinline__ void split_row_to_tmem(const uint8_t* tile, int r, uint32_t taddr) {
+    uint32_t hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 v = *reinterpret_cast<const float4*>(tile + r * 128 + ((j ^ (r & 7)) << 4));
+        const float xs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t h = tf32_rna(xs[e]);
+            hi[4 * j + e] = h;
+            lo[4 * j + e] = tf32_rna(xs[e] - __uint_as_float(h));
+        }
+    }
+    tmem_st32(taddr, hi);
+    tmem_st32(taddr + 32, lo);
+}
+
+// ---------------------------------------------------------------------------
+// Stages S1-S3: resident per-unit B operand, persistent CTAs over (unit, tile).
+// ---------------------------------------------------------------------------
+struct StageParams {
+    int Np;
+    int planes;        // 1 for S1 (real A), 2 for S2/S3 (planar complex A)
+    int kch;           // K-chunks per plane: ceil(Np / 32)
+    int mtiles;        // Np^3 / 128
+    long long M;       // rows = Np^3
+    int units;         // units in the batch
+    int a_unit;        // A has a unit coordinate (S2/S3) or is shared (S1)
+    float* out;
+    long long out_unit;
+    StageMap map;
+    int* err;
+};
+
+constexpr int kStageAStages = 4;
+constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-11 epilogue
+
+__global__ void __launch_bounds__(kStageThreads, 1)
+    k_tc_stage(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+               const __grid_constant__ CUtensorMap tmBlo, const StageParams p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int Np = p.Np;
+    const uint32_t chunkB = (uint32_t)(2 * Np * 128);  // one K-chunk of the 2Np-row B operand
+    uint8_t* sBhi = smem;
+    uint8_t* sBlo = sBhi + p.kch * chunkB;
+    uint8_t* sA = sBlo + p.kch * chunkB;
+    uint64_t* bars = (uint64_t*)(sA + kStageAStages * kTileBytes);
+    // barrier indices
+    const int BFULL = 0, BEMPTY = 1, AFULL = 2, AEMPTY = 6, TFULL = 10, TEMPTY = 12, ACCF = 14,
+              ACCE = 16, DRAIN = 18;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 20);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    auto bar = [&](int i) { return smem_u32(bars + i); };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(bar(BFULL), 1);
+        mbar_init(bar(BEMPTY), 1);
+        for (int s = 0; s < kStageAStages; ++s) {
+            mbar_init(bar(AFULL + s), 1);
+            mbar_init(bar(AEMPTY + s), 4);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(bar(TFULL + s), 4);
+            mbar_init(bar(TEMPTY + s), 1);
+            mbar_init(bar(ACCF + s), 1);
+            mbar_init(bar(ACCE + s), 4);
+        }
+        mbar_init(bar(DRAIN), 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmBhi);
+        prefetch_tmap(&tmBlo);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const long long total = (long long)p.units * p.mtiles;
+    const long long t0 = total * blockIdx.x / gridDim.x;
+    const long long t1 = total * (blockIdx.x + 1) / gridDim.x;
+    const int chunks_per_tile = p.planes * p.kch;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int cur_u = -1;
+            uint32_t bph = 0;
+            long long it = 0;
+            bool ok = true;
+            bool loaded_b = false;
+            for (long long t = t0; t < t1 && ok; ++t) {
+                const int u = (int)(t / p.mtiles), mt = (int)(t % p.mtiles);
+                if (u != cur_u) {
+                    if (cur_u >= 0) {
+                        if (!mbar_wait(bar(BEMPTY), bph, abort_flag, p.err, 1)) { ok = false; break; }
+                        bph ^= 1;
+                    }
+                    mbar_expect_tx(bar(BFULL), 2u * p.kch * chunkB);
+                    for (int kc = 0; kc < p.kch; ++kc) {
+                        tma_3d(smem_u32(sBhi + kc * chunkB), &tmBhi, bar(BFULL), kc * kKC, 0, u);
+                        tma_3d(smem_u32(sBlo + kc * chunkB), &tmBlo, bar(BFULL), kc * kKC, 0, u);
+                    }
+                    loaded_b = true;
+                    cur_u = u;
+                }
+                for (int c = 0; c < chunks_per_tile && ok; ++c, ++it) {
+                    const int pl = c / p.kch, kc = c % p.kch;
+                    const int s = (int)(it % kStageAStages);
+                    const uint32_t ph = (uint32_t)((it / kStageAStages) & 1);
+                    if (!mbar_wait(bar(AEMPTY + s), ph ^ 1, abort_flag, p.err, 2)) { ok = false; break; }
+                    mbar_expect_tx(bar(AFULL + s), kTileBytes);
+                    const uint32_t dst = smem_u32(sA + s * kTileBytes);
+                    if (p.a_unit) tma_4d(dst, &tmA, bar(AFULL + s), kc * kKC, pl, mt * kBM, u);
+                    else tma_2d(dst, &tmA, bar(AFULL + s), kc * kKC, mt * kBM);
+                }
+            }
+            if (*abort_flag) {
+                // drain: wait for the last load issued into every stage and for B
+                for (int s = 0; s < kStageAStages; ++s) {
+                    if (it > s) {
+                        const long long last = it - 1 - ((it - 1 - s) % kStageAStages);
+                        const uint32_t ph = (uint32_t)((last / kStageAStages) & 1);
+                        const unsigned long long g0 = gtimer();
+                        while (!mbar_try(bar(AFULL + s), ph) && gtimer() - g0 < kWaitLimitNs) {}
+                    }
+                }
+                if (loaded_b) {
+                    const unsigned long long g0 = gtimer();
+                    while (!mbar_try(bar(BFULL), bph) && gtimer() - g0 < kWaitLimitNs) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t id_full = idesc_tf32(2 * Np, 0);
+            const uint32_t id_half = idesc_tf32(Np, 0);
+            const uint32_t id_half_neg = idesc_tf32(Np, 1);
+            int cur_u = -1;
+            uint32_t bfph = 0;
+            long long it = 0, tile_i = 0;
+            bool ok = true;
+            for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
+                const int u = (int)(t / p.mtiles);
+                if (u != cur_u) {
+                    if (!mbar_wait(bar(BFULL), bfph, abort_flag, p.err, 3)) { ok = false; break; }
+                    bfph ^= 1;
+                    cur_u = u;
+                    tc_fence_after();
+                }
+                const int ab = (int)(tile_i & 1);
+                const uint32_t abph = (uint32_t)((tile_i >> 1) & 1);
+                if (!mbar_wait(bar(ACCE + ab), abph ^ 1, abort_flag, p.err, 4)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t dacc = tmem + (uint32_t)(ab * 256);
+                for (int c = 0; c < chunks_per_tile; ++c, ++it) {
+                    const int pl = c / p.kch, kc = c % p.kch;
+                    const int slot = (int)(it & 1);
+                    const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                    if (!mbar_wait(bar(TFULL + slot), sph, abort_flag, p.err, 5)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ahi = tmem + (slot ? 448u : 192u), alo = ahi + 32;
+                    const uint32_t bhi = smem_u32(sBhi) + kc * chunkB, blo = smem_u32(sBlo) + kc * chunkB;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t first = (c == 0 && kk == 0) ? 1u : 0u;
+                        const uint32_t ah = ahi + kk * 8, al = alo + kk * 8;
+                        if (pl == 0) {
+                            const unsigned long long dh = desc_sw128(bhi + kk * 32), dl = desc_sw128(blo + kk * 32);
+                            mma_tf32(dacc, ah, dh, id_full, first ? 0u : 1u);
+                            mma_tf32(dacc, ah, dl, id_full, 1u);
+                            mma_tf32(dacc, al, dh, id_full, 1u);
+                        } else {
+                            // D[:, 0:Np] += A_im * (-Im G);  D[:, Np:2Np] += A_im * Re G
+                            const uint32_t off_im = (uint32_t)(Np * 128);
+                            const unsigned long long dih = desc_sw128(bhi + off_im + kk * 32);
+                            const unsigned long long dil = desc_sw128(blo + off_im + kk * 32);
+                            const unsigned long long drh = desc_sw128(bhi + kk * 32);
+                            const unsigned long long drl = desc_sw128(blo + kk * 32);
+                            mma_tf32(dacc, ah, dih, id_half_neg, 1u);
+                            mma_tf32(dacc, ah, dil, id_half_neg, 1u);
+                            mma_tf32(dacc, al, dih, id_half_neg, 1u);
+                            mma_tf32(dacc + Np, ah, drh, id_half, 1u);
+                            mma_tf32(dacc + Np, ah, drl, id_half, 1u);
+                            mma_tf32(dacc + Np, al, drh, id_half, 1u);
+                        }
+                    }
+                    mma_commit(bar(TEMPTY + slot));
+                }
+                if (!ok) break;
+                mma_commit(bar(ACCF + ab));
+                if (t + 1 < t1 && (int)((t + 1) / p.mtiles) != u) mma_commit(bar(BEMPTY));
+            }
+            if (*abort_flag) {
+                mma_commit(bar(DRAIN));
+                const unsigned long long g0 = gtimer();
+                while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---------------- converter: FP32 A tile -> TF32 hi/lo in TMEM ----------------
+        const int wq = warp & 3;
+        const int r = wq * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+        long long it = 0;
+        bool ok = true;
+        for (long long t = t0; t < t1 && ok; ++t) {
+            for (int c = 0; c < chunks_per_tile; ++c, ++it) {
+                const int s = (int)(it % kStageAStages);
+                const uint32_t ph = (uint32_t)((it / kStageAStages) & 1);
+                if (!mbar_wait(bar(AFULL + s), ph, abort_flag, p.err, 6)) { ok = false; break; }
+                const int slot = (int)(it & 1);
+                const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 7)) { ok = false; break; }
+                tc_fence_after();
+                split_row_to_tmem(sA + s * kTileBytes, r, lane_base + (slot ? 448u : 192u));
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(AEMPTY + s));
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(TFULL + slot));
+            }
+        }
+    } else if (warp >= 8) {
+        // ---------------- epilogue: TMEM -> registers -> HBM (scattered layout) ----------------
+        const int wq = warp & 3;
+        const int rloc = wq * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+        const int ncc = (2 * Np) / 32;
+        long long tile_i = 0;
+        bool ok = true;
+        for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
+            const int u = (int)(t / p.mtiles), mt = (int)(t % p.mtiles);
+            const int ab = (int)(tile_i & 1);
+            const uint32_t abph = (uint32_t)((tile_i >> 1) & 1);
+            if (!mbar_wait(bar(ACCF + ab), abph, abort_flag, p.err, 8)) { ok = false; break; }
+            tc_fence_after();
+            const long long row = (long long)mt * kBM + rloc;
+            const bool valid = row < p.M;
+            const long long x = row % p.map.Dx;
+            const long long rb = row / p.map.Dx;
+            float* o = p.out + (long long)u * p.out_unit + (rb / p.map.Db) * p.map.SA +
+                       (rb % p.map.Db) * p.map.SB + x * p.map.SX;
+            for (int cc = 0; cc < ncc; ++cc) {
+                uint32_t v[32];
+                tmem_ld32(lane_base + (uint32_t)(ab * 256 + cc * 32), v);
+                tmem_wait_ld();
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = cc * 32 + j;
+                        const int hc = col >= Np ? 1 : 0;
+                        const int y = col - hc * Np;
+                        o[hc * p.map.SC + (long long)y * p.map.SY] = __uint_as_float(v[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(ACCE + ab));
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage S4: D[(u,c,j)][i] = sum_K X3[(u,c,j)][K] vK[i][K], K = Np^3, split-K.
+// Work item = (group of two 128-row tiles, K range of kKW); B is streamed.
+// ---------------------------------------------------------------------------
+struct FinalParams {
+    int Np;
+    long long K;
+    int KW;
+    int nks;
+    long long rows;
+    int ngroups;
+    float* part;   // [ks][i][Rld]
+    long long Rld;
+    int* err;
+};
+
+constexpr int kFinStages = 3;
+constexpr int kFinThreads = 384;
+
+__global__ void __launch_bounds__(kFinThreads, 1)
+    k_tc_final(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+               const __grid_constant__ CUtensorMap tmBlo, const FinalParams p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int Np = p.Np;
+    const uint32_t bbytes = (uint32_t)(Np * 128);
+    const uint32_t stage_bytes = 2 * kTileBytes + 2 * bbytes;
+    uint64_t* bars = (uint64_t*)(smem + kFinStages * stage_bytes);
+    const int FULL = 0, EMPTY = 3, TFULL = 6, TEMPTY = 8, ACCF = 10, ACCE = 11, DRAIN = 12;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 14);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    auto bar = [&](int i) { return smem_u32(bars + i); };
+    auto stA = [&](int s, int t) { return smem + s * stage_bytes + t * kTileBytes; };
+    auto stBhi = [&](int s) { return smem + s * stage_bytes + 2 * kTileBytes; };
+    auto stBlo = [&](int s) { return smem + s * stage_bytes + 2 * kTileBytes + bbytes; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kFinStages; ++s) {
+            mbar_init(bar(FULL + s), 1);
+            mbar_init(bar(EMPTY + s), 5);  // 4 converter warps + 1 MMA commit
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(bar(TFULL + s), 4);
+            mbar_init(bar(TEMPTY + s), 1);
+        }
+        mbar_init(bar(ACCF), 1);
+        mbar_init(bar(ACCE), 4);
+        mbar_init(bar(DRAIN), 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmBhi);
+        prefetch_tmap(&tmBlo);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const long long items = (long long)p.ngroups * p.nks;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long it = 0;
+            bool ok = true;
+            for (long long item = blockIdx.x; item < items && ok; item += gridDim.x) {
+                const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
+                const long long k0 = (long long)ks * p.KW;
+                const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
+                for (long long k = k0; k < k1; k += kKC, ++it) {
+                    const int s = (int)(it % kFinStages);
+                    const uint32_t ph = (uint32_t)((it / kFinStages) & 1);
+                    if (!mbar_wait(bar(EMPTY + s), ph ^ 1, abort_flag, p.err, 11)) { ok = false; break; }
+                    mbar_expect_tx(bar(FULL + s), stage_bytes);
+                    tma_2d(smem_u32(stA(s, 0)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM);
+                    tma_2d(smem_u32(stA(s, 1)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM + kBM);
+                    tma_2d(smem_u32(stBhi(s)), &tmBhi, bar(FULL + s), (int)k, 0);
+                    tma_2d(smem_u32(stBlo(s)), &tmBlo, bar(FULL + s), (int)k, 0);
+                }
+            }
+            if (*abort_flag) {
+                for (int s = 0; s < kFinStages; ++s) {
+                    if (it > s) {
+                        const long long last = it - 1 - ((it - 1 - s) % kFinStages);
+                        const uint32_t ph = (uint32_t)((last / kFinStages) & 1);
+                        const unsigned long long g0 = gtimer();
+                        while (!mbar_try(bar(FULL + s), ph) && gtimer() - g0 < kWaitLimitNs) {}
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id = idesc_tf32(Np, 0);
+            long long it = 0, item_i = 0;
+            bool ok = true;
+            for (long long item = blockIdx.x; item < items && ok; item += gridDim.x, ++item_i) {
+                const int ks = (int)(item / p.ngroups);
+                const long long k0 = (long long)ks * p.KW;
+                const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
+                if (!mbar_wait(bar(ACCE), (uint32_t)((item_i & 1) ^ 1), abort_flag, p.err, 12)) { ok = false; break; }
+                tc_fence_after();
+                bool first_chunk = true;
+                for (long long k = k0; k < k1; k += kKC, ++it) {
+                    const int s = (int)(it % kFinStages);
+                    const int slot = (int)(it & 1);
+                    const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                    if (!mbar_wait(bar(TFULL + slot), sph, abort_flag, p.err, 13)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t bhi = smem_u32(stBhi(s)), blo = smem_u32(stBlo(s));
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const uint32_t dacc = tmem + (uint32_t)(t * 128);
+                        const uint32_t ahi = tmem + 256u + (uint32_t)(slot * 128 + t * 64), alo = ahi + 32;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const unsigned long long dh = desc_sw128(bhi + kk * 32), dl = desc_sw128(blo + kk * 32);
+                            mma_tf32(dacc, ahi + kk * 8, dh, id, (first_chunk && kk == 0) ? 0u : 1u);
+                            mma_tf32(dacc, ahi + kk * 8, dl, id, 1u);
+                            mma_tf32(dacc, alo + kk * 8, dh, id, 1u);
+                        }
+                    }
+                    first_chunk = false;
+                    mma_commit(bar(TEMPTY + slot));
+                    mma_commit(bar(EMPTY + s));
+                }
+                if (!ok) break;
+                mma_commit(bar(ACCF));
+            }
+            if (*abort_flag) {
+                mma_commit(bar(DRAIN));
+                const unsigned long long g0 = gtimer();
+                while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        const int wq = warp & 3;
+        const int r = wq * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+        long long it = 0;
+        bool ok = true;
+        for (long long item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const int ks = (int)(item / p.ngroups);
+            const long long k0 = (long long)ks * p.KW;
+            const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
+            for (long long k = k0; k < k1; k += kKC, ++it) {
+                const int s = (int)(it % kFinStages);
+                const uint32_t ph = (uint32_t)((it / kFinStages) & 1);
+                if (!mbar_wait(bar(FULL + s), ph, abort_flag, p.err, 14)) { ok = false; break; }
+                const int slot = (int)(it & 1);
+                const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 15)) { ok = false; break; }
+                tc_fence_after();
+                split_row_to_tmem(stA(s, 0), r, lane_base + 256u + (uint32_t)(slot * 128));
+                split_row_to_tmem(stA(s, 1), r, lane_base + 256u + (uint32_t)(slot * 128 + 64));
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(EMPTY + s));
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(TFULL + slot));
+            }
+        }
+    } else if (warp >= 8) {
+        const int wq = warp & 3;
+        const int rloc = wq * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+        long long item_i = 0;
+        bool ok = true;
+        for (long long item = blockIdx.x; item < items && ok; item += gridDim.x, ++item_i) {
+            const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
+            if (!mbar_wait(bar(ACCF), (uint32_t)(item_i & 1), abort_flag, p.err, 16)) { ok = false; break; }
+            tc_fence_after();
+            float* base = p.part + (long long)ks * Np * p.Rld;
+            for (int t = 0; t < 2; ++t) {
+                const long long row = (long long)g * 2 * kBM + t * kBM + rloc;
+                for (int cc = 0; cc < Np / 16; ++cc) {
+                    uint32_t v[16];
+                    tmem_ld16(lane_base + (uint32_t)(t * 128 + cc * 16), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) base[(long long)(cc * 16 + j) * p.Rld + row] = __uint_as_float(v[j]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(ACCE));
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+    const uint32_t h = tf32_rna((float)x);
+    hi = __uint_as_float(h);
+    lo = __uint_as_float(tf32_rna((float)(x - (double)hi)));
+}
+
+// wS32[j][m][q][s] = w_mqsj = 2 v_mqsj - v_qmsj (zero in the padding).
+__global__ void k_build_wS32(int N, int Np, const double* __restrict__ v, float* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long Np4 = (long long)Np * Np * Np * Np;
+    if (e >= Np4) return;
+    const int s = (int)(e % Np), q = (int)((e / Np) % Np), m = (int)((e / Np / Np) % Np),
+              j = (int)(e / Np / Np / Np);
+    float w = 0.0f;
+    if (s < N && q < N && m < N && j < N) {
+        const long long NN = N;
+        const double a = v[((m * NN + q) * NN + s) * NN + j];
+        const double b = v[((q * NN + m) * NN + s) * NN + j];
+        w = (float)(2.0 * a - b);
+    }
+    out[e] = w;
+}
+
+// vK[i][n][r][p] = v_irpn split into TF32 hi / lo (zero in the padding).
+__global__ void k_build_vK32(int N, int Np, const double* __restrict__ v, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long Np4 = (long long)Np * Np * Np * Np;
+    if (e >= Np4) return;
+    const int pp = (int)(e % Np), r = (int)((e / Np) % Np), n = (int)((e / Np / Np) % Np),
+              i = (int)(e / Np / Np / Np);
+    float h = 0.0f, l = 0.0f;
+    if (pp < N && r < N && n < N && i < N) {
+        const long long NN = N;
+        split_f64(v[((i * NN + r) * NN + pp) * NN + n], h, l);
+    }
+    hi[e] = h;
+    lo[e] = l;
+}
+
+// Per-unit B operands of the tensor-core path (padded to Np, zero padding):
+//   B1[u][(c,r)][s] = Gb_c[s][r]   (S1)      Gs[u][(c,p)][q] = G_c[p][q]   (S2, S3)
+// each stored as TF32 hi then lo blocks of ub units.
+__global__ void k_forms_tf32(int N, int Np, int nb, int ub, const double2* __restrict__ G,
+                             const double2* __restrict__ Gb, float* __restrict__ B1,
+                             float* __restrict__ Gs) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per = 2LL * Np * Np;
+    if (e >= per * nb) return;
+    const int u = (int)(e / per);
+    const int rr = (int)(e % per);
+    const int row = rr / Np, k = rr % Np;  // row = (c, idx), k = K index
+    const int comp = row / Np, idx = row % Np;
+    const long long NN = (long long)N * N;
+    float bh = 0.f, bl = 0.f, gh = 0.f, gl = 0.f;
+    if (idx < N && k < N) {
+        const double2 gb = Gb[u * NN + (long long)k * N + idx];  // Gb[s = k][r = idx]
+        split_f64(comp ? gb.y : gb.x, bh, bl);
+        const double2 g = G[u * NN + (long long)idx * N + k];    // G[p = idx][q = k]
+        split_f64(comp ? g.y : g.x, gh, gl);
+    }
+    const long long lo_off = per * ub;
+    B1[e] = bh;
+    B1[lo_off + e] = bl;
+    Gs[e] = gh;
+    Gs[lo_off + e] = gl;
+}
+
+inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode(gkba_ctx* c, gkba_status* st) {
+    static EncodeTiledFn fn = nullptr;
+    if (fn) return fn;
+    cudaDriverEntryPointQueryResult q;
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || ptr == nullptr) {
+        *st = fail(c, GKBA_ECUDA, "cuTensorMapEncodeTiled not available (%s)", cudaGetErrorString(e));
+        return nullptr;
+    }
+    fn = (EncodeTiledFn)ptr;
+    return fn;
+}
+
+gkba_status make_map(gkba_ctx* c, CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims,
+                     const cuuint64_t* strides_bytes, const cuuint32_t* box) {
+    gkba_status st = GKBA_OK;
+    EncodeTiledFn enc = get_encode(c, &st);
+    if (!enc) return st;
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base),
+                     dims, strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(c, GKBA_ECUDA, "cuTensorMapEncodeTiled failed (%d), rank %d", (int)r, rank);
+    return GKBA_OK;
+}
+
+size_t stage_smem_bytes(int Np) {
+    const int kch = (Np + kKC - 1) / kKC;
+    return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 256;
+}
+size_t final_smem_bytes(int Np) {
+    return 1024 + (size_t)kFinStages * (2 * kTileBytes + 2 * Np * 128) + 256;
+}
+
+}  // namespace
+
+// Model operands of the tensor-core path (once per context).
+gkba_status tf32_prepare_model(gkba_ctx* c) {
+    const long long Np4 = (long long)c->Np * c->Np * c->Np * c->Np;
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_build_wS32<<<grid1(Np4, 256), 256, 0, c->stream>>>(c->N, c->Np, c->v, c->wS32);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_build_vK32<<<grid1(Np4, 256), 256, 0, c->stream>>>(c->N, c->Np, c->v, c->vKhi, c->vKlo);
+    GKBA_TRY(launch_end(c, t));
+    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)stage_smem_bytes(c->Np)));
+    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)final_smem_bytes(c->Np)));
+    return GKBA_OK;
+}
+
+gkba_status build_forms_tf32(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
+    const long long per = 2LL * c->Np * c->Np;
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_forms_tf32<<<grid1(per * nb, 256), 256, 0, c->stream>>>(c->N, c->Np, nb, c->ub_cap, G, Gb,
+                                                              (float*)c->formsB1, (float*)c->formsG);
+    return launch_end(c, t);
+}
+
+gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG, const double2* Gb,
+                        long long sGb, int) {
+    (void)sG;
+    (void)sGb;
+    if (c->prec == GKBA_SPLIT_TF32) return build_forms_tf32(c, nb, G, Gb);
+    return build_forms_fp64(c, nb, G, Gb);
+}
+
+// Tensor-core contraction of one batch (forms built): S_u -> c->Su.
+gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
+    const int Np = c->Np;
+    const long long N2 = (long long)Np * Np, N3 = N2 * Np, N4 = N3 * Np;
+    const int kch = (Np + kKC - 1) / kKC;
+    const int mtiles = (int)(N3 / kBM);
+    float* X13 = (float*)c->X13;
+    float* X2 = (float*)c->X2;
+    const long long per = 2LL * Np * Np;
+    float* B1hi = (float*)c->formsB1;
+    float* B1lo = B1hi + per * c->ub_cap;
+    float* Gshi = (float*)c->formsG;
+    float* Gslo = Gshi + per * c->ub_cap;
+    int* err = c->dint + 1;
+    // Flops below are the algorithmic counts of the N-basis problem (padding excluded).
+    const double Nr = c->N;
+    const double fl_cr = 4.0 * Nr * Nr * Nr * Nr * Nr, fl_cc = 2.0 * fl_cr;
+    const double N4r = Nr * Nr * Nr * Nr;
+
+    CUtensorMap mA1, mA23_in1, mA23_in2, mB1h, mB1l, mGh, mGl, mAf, mVh, mVl;
+    {
+        cuuint64_t d[2] = {(cuuint64_t)Np, (cuuint64_t)N3};
+        cuuint64_t s[1] = {(cuuint64_t)Np * 4};
+        cuuint32_t b[2] = {kKC, kBM};
+        GKBA_TRY(make_map(c, &mA1, c->wS32, 2, d, s, b));
+    }
+    {
+        cuuint64_t d[4] = {(cuuint64_t)Np, 2, (cuuint64_t)N3, (cuuint64_t)nb};
+        cuuint64_t s[3] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * Np * 4, (cuuint64_t)(2 * N4 * 4)};
+        cuuint32_t b[4] = {kKC, 1, kBM, 1};
+        GKBA_TRY(make_map(c, &mA23_in1, X13, 4, d, s, b));
+        GKBA_TRY(make_map(c, &mA23_in2, X2, 4, d, s, b));
+    }
+    {
+        cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)2 * Np, (cuuint64_t)nb};
+        cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)per * 4};
+        cuuint32_t b[3] = {kKC, (cuuint32_t)(2 * Np), 1};
+        GKBA_TRY(make_map(c, &mB1h, B1hi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &mB1l, B1lo, 3, d, s, b));
+        GKBA_TRY(make_map(c, &mGh, Gshi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &mGl, Gslo, 3, d, s, b));
+    }
+    const long long rows = 2LL * Np * nb;
+    {
+        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)rows};
+        cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
+        cuuint32_t b[2] = {kKC, kBM};
+        GKBA_TRY(make_map(c, &mAf, X13, 2, d, s, b));
+    }
+    {
+        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)Np};
+        cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
+        cuuint32_t b[2] = {kKC, (cuuint32_t)Np};
+        GKBA_TRY(make_map(c, &mVh, c->vKhi, 2, d, s, b));
+        GKBA_TRY(make_map(c, &mVl, c->vKlo, 2, d, s, b));
+    }
+
+    const size_t ssm = stage_smem_bytes(Np);
+    const long long total = (long long)nb * mtiles;
+    const int grid = (int)(total < c->num_sms ? total : c->num_sms);
+    StageParams sp{};
+    sp.Np = Np;
+    sp.kch = kch;
+    sp.mtiles = mtiles;
+    sp.M = N3;
+    sp.units = nb;
+    sp.out_unit = 2 * N4;
+    sp.err = err;
+    // S1: rows (j,m,q), cols (c,r) -> X1[j][r][m][c][q]
+    sp.planes = 1;
+    sp.a_unit = 0;
+    sp.out = X13;
+    sp.map = StageMap{2 * N3, 2 * Np, 1, Np, 2 * N2, Np, Np, Np};
+    {
+        auto t = launch_begin(c, K_W1, fl_cr * nb, 4.0 * (N4r + 2 * N4r * nb));
+        k_tc_stage<<<grid, kStageThreads, ssm, c->stream>>>(mA1, mB1h, mB1l, sp);
+        GKBA_TRY(launch_end(c, t));
+    }
+    // S2: rows (j,r,m), K (c,q), cols (c',p) -> X2[j][r][p][c'][m]
+    sp.planes = 2;
+    sp.a_unit = 1;
+    sp.out = X2;
+    sp.map = StageMap{2 * N3, 2 * N2, 1, Np, 2 * Np, Np, Np, Np};
+    {
+        auto t = launch_begin(c, K_W2, fl_cc * nb, 4.0 * 4 * N4r * nb);
+        k_tc_stage<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in1, mGh, mGl, sp);
+        GKBA_TRY(launch_end(c, t));
+    }
+    // S3: rows (j,r,p), K (c,m), cols (c',n) -> X3[c'][j][n][r][p]
+    sp.out = X13;
+    sp.map = StageMap{N3, Np, 1, N4, N2, Np, Np, Np};
+    {
+        auto t = launch_begin(c, K_W3, fl_cc * nb, 4.0 * 4 * N4r * nb);
+        k_tc_stage<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in2, mGh, mGl, sp);
+        GKBA_TRY(launch_end(c, t));
+    }
+    // S4: split-K over (n,r,p)
+    FinalParams fp{};
+    fp.Np = Np;
+    fp.K = N3;
+    fp.KW = 4096;
+    fp.nks = (int)((N3 + fp.KW - 1) / fp.KW);
+    fp.rows = rows;
+    fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
+    fp.Rld = (long long)fp.ngroups * 2 * kBM;
+    fp.part = (float*)c->part;
+    fp.err = err;
+    if ((size_t)fp.nks * Np * fp.Rld * 4 > c->part_bytes)
+        return fail(c, GKBA_ESTATE, "partial buffer too small");
+    {
+        const long long items = (long long)fp.ngroups * fp.nks;
+        const int g = (int)(items < c->num_sms ? items : c->num_sms);
+        auto t = launch_begin(c, K_FIN, fl_cr * nb, 4.0 * (2 * N4r * nb + 2 * N4r));
+        k_tc_final<<<g, kFinThreads, final_smem_bytes(Np), c->stream>>>(mAf, mVh, mVl, fp);
+        GKBA_TRY(launch_end(c, t));
+    }
+    return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
+}
+
+size_t tf32_part_bytes(int Np, int ub) {
+    const long long N3 = (long long)Np * Np * Np;
+    const long long nks = (N3 + 4095) / 4096;
+    const long long rows = 2LL * Np * ub;
+    const long long Rld = ((rows + 255) / 256) * 256;
+    return (size_t)(nks * Np * Rld * 4);
+}
+
+}  // namespace gkba

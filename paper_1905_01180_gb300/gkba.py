@@ -1,0 +1,242 @@
+"""Thin Python binding of libgkba (include/gkba.h): argument marshalling only.
+
+Every step of the GKBA second-Born path runs in the library's CUDA kernels;
+this module converts numpy arrays (host buffers) or torch CUDA tensors
+(device buffers) into the C ABI's pointers and sizes.  It fails loudly when
+the shared library is missing: there is no CPU fallback.
+
+Complex arrays are complex128 (interleaved re, im), N x N row-major; v is
+float64 with shape (N, N, N, N).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgkba.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC, EUNSUPPORTED = range(8)
+FP64, SPLIT_TF32 = 0, 1
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT",
+           6: "ENUMERIC", 7: "EUNSUPPORTED"}
+
+EXPORTED = ["gkba_init", "gkba_sigma", "gkba_collision", "gkba_step", "gkba_set_history",
+            "gkba_get_history", "gkba_get_state", "gkba_mean_field", "gkba_adjoint",
+            "gkba_get_stats", "gkba_last_error", "gkba_destroy"]
+
+
+class GKBAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("dt", ctypes.c_double), ("max_steps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
+                ("timing", ctypes.c_int)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libgkba.so (built by ``paper_1905_01180_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.gkba_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Config), P, P, P, P, I]
+    L.gkba_sigma.argtypes = [P, I, P, P, P, I]
+    L.gkba_collision.argtypes = [P, I, P, P, P, P, I]
+    L.gkba_step.argtypes = [P, D, D, P, P, P]
+    L.gkba_set_history.argtypes = [P, I, P, P, I]
+    L.gkba_get_history.argtypes = [P, ctypes.POINTER(I), P, P]
+    L.gkba_get_state.argtypes = [P, ctypes.POINTER(I), P]
+    L.gkba_mean_field.argtypes = [P, P, P, I]
+    L.gkba_adjoint.argtypes = [P, P, I, I, P, P, P]
+    L.gkba_get_stats.argtypes = [P, ctypes.POINTER(KernelStat), I, ctypes.POINTER(I),
+                                 ctypes.POINTER(ctypes.c_longlong), I]
+    L.gkba_last_error.argtypes = [P]
+    L.gkba_last_error.restype = ctypes.c_char_p
+    L.gkba_destroy.argtypes = [P]
+    L.gkba_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("gkba_last_error", "gkba_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _host(x, dtype):
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def _dev(x, dtype_name):
+    import torch
+    want = {"c16": torch.complex128, "f64": torch.float64}[dtype_name]
+    if not x.is_cuda:
+        raise ValueError("torch tensors passed to libgkba must live on a CUDA device")
+    t = x.contiguous()
+    if t.dtype != want:
+        t = t.to(want)
+    return t, t.data_ptr()
+
+
+class Context:
+    """One GKBA system on one GPU (wraps a gkba_ctx)."""
+
+    def __init__(self, h, v, d, rho0, dt, max_steps=0, precision="fp64", stream=None,
+                 workspace_bytes=0, device=-1, timing=False):
+        L = load()
+        on_dev = _is_torch(h)
+        N = int(h.shape[0])
+        keep = []
+        if on_dev:
+            ph = _dev(h, "c16"); pv = _dev(v, "f64"); pd = _dev(d, "c16"); pr = _dev(rho0, "c16")
+        else:
+            ph = _host(h, np.complex128); pv = _host(v, np.float64)
+            pd = _host(d, np.complex128); pr = _host(rho0, np.complex128)
+        keep += [ph, pv, pd, pr]
+        prec = {"fp64": FP64, "tf32": SPLIT_TF32, FP64: FP64, SPLIT_TF32: SPLIT_TF32}[precision]
+        cfg = Config(N=N, dt=float(dt), max_steps=int(max_steps), precision=prec,
+                     cuda_stream=stream, workspace_bytes=int(workspace_bytes), device=int(device),
+                     timing=1 if timing else 0)
+        handle = ctypes.c_void_p()
+        st = L.gkba_init(ctypes.byref(handle), ctypes.byref(cfg), ph[1], pv[1], pd[1], pr[1],
+                         1 if on_dev else 0)
+        if st != OK:
+            raise GKBAError(st, L.gkba_last_error(None).decode())
+        self._h = handle
+        self.N = N
+        self.dt = float(dt)
+        self.max_steps = int(max_steps)
+        self.precision = prec
+
+    # -- helpers -------------------------------------------------------
+    def _check(self, st):
+        if st != OK:
+            raise GKBAError(st, load().gkba_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gkba_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls ---------------------------------------------------------
+    def sigma(self, G, Gbar):
+        """Eq. (2bse) for a batch (U, N, N) or a single (N, N) pair."""
+        single = G.ndim == 2
+        n = 1 if single else int(G.shape[0])
+        if _is_torch(G):
+            import torch
+            g, gp = _dev(G, "c16"); gb, gbp = _dev(Gbar, "c16")
+            out = torch.empty_like(g)
+            self._check(load().gkba_sigma(self._h, n, gp, gbp, out.data_ptr(), 1))
+            return out
+        g, gp = _host(G, np.complex128); gb, gbp = _host(Gbar, np.complex128)
+        out = np.empty_like(g)
+        self._check(load().gkba_sigma(self._h, n, gp, gbp, out.ctypes.data, 0))
+        return out
+
+    def collision(self, rho_hist, T_hist, weights=None):
+        """First line of Eq. (collint) over the L points of the history."""
+        Lh = int(rho_hist.shape[0])
+        if _is_torch(rho_hist):
+            import torch
+            r, rp = _dev(rho_hist, "c16"); t, tp = _dev(T_hist, "c16")
+            wp = None
+            if weights is not None:
+                w, wp = _dev(weights, "f64")
+            out = torch.empty((self.N, self.N), dtype=torch.complex128, device=r.device)
+            self._check(load().gkba_collision(self._h, Lh, rp, tp, wp, out.data_ptr(), 1))
+            return out
+        r, rp = _host(rho_hist, np.complex128); t, tp = _host(T_hist, np.complex128)
+        wp = None
+        if weights is not None:
+            w, wp = _host(weights, np.float64)
+        out = np.empty((self.N, self.N), np.complex128)
+        self._check(load().gkba_collision(self._h, Lh, rp, tp, wp, out.ctypes.data, 0))
+        return out
+
+    def step(self, E_n, E_np1):
+        """One Heun step; returns (rho_{n+1}, I(t_n), diag(t_n))."""
+        rho = np.empty((self.N, self.N), np.complex128)
+        I = np.empty((self.N, self.N), np.complex128)
+        diag = np.empty(4, np.float64)
+        self._check(load().gkba_step(self._h, float(E_n), float(E_np1), rho.ctypes.data,
+                                     I.ctypes.data, diag.ctypes.data))
+        return rho, I, diag
+
+    def mean_field(self, rho):
+        r, rp = _host(rho, np.complex128)
+        out = np.empty_like(r)
+        self._check(load().gkba_mean_field(self._h, rp, out.ctypes.data, 0))
+        return out
+
+    def set_history(self, n, rho_hist, T_hist):
+        if _is_torch(rho_hist):
+            r, rp = _dev(rho_hist, "c16"); t, tp = _dev(T_hist, "c16")
+            self._check(load().gkba_set_history(self._h, int(n), rp, tp, 1))
+        else:
+            r, rp = _host(rho_hist, np.complex128); t, tp = _host(T_hist, np.complex128)
+            self._check(load().gkba_set_history(self._h, int(n), rp, tp, 0))
+
+    def get_history(self):
+        n = ctypes.c_int()
+        self._check(load().gkba_get_history(self._h, ctypes.byref(n), None, None))
+        rho = np.empty((n.value + 1, self.N, self.N), np.complex128)
+        T = np.empty_like(rho)
+        self._check(load().gkba_get_history(self._h, ctypes.byref(n), rho.ctypes.data, T.ctypes.data))
+        return n.value, rho, T
+
+    def get_state(self):
+        n = ctypes.c_int()
+        rho = np.empty((self.N, self.N), np.complex128)
+        self._check(load().gkba_get_state(self._h, ctypes.byref(n), rho.ctypes.data))
+        return n.value, rho
+
+    def stats(self, reset=False):
+        arr = (KernelStat * 16)()
+        n = ctypes.c_int()
+        tot = ctypes.c_longlong()
+        self._check(load().gkba_get_stats(self._h, arr, 16, ctypes.byref(n), ctypes.byref(tot),
+                                          1 if reset else 0))
+        out = {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms,
+                                          flops=arr[i].flops, bytes=arr[i].bytes)
+               for i in range(n.value)}
+        return out, tot.value
+
+    def adjoint(self, *a, **k):
+        st = load().gkba_adjoint(self._h, None, 0, 0, None, None, None)
+        self._check(st)

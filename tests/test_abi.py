@@ -1,0 +1,93 @@
+"""C-ABI checks that need no GPU: the library builds and loads, it exports
+every function include/gkba.h declares, and invalid arguments are rejected
+by host-side validation before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gkba_inputs as gi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    from paper_1905_01180_gb300 import gkba
+    return gkba.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gkba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gkba_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "gkba_init" in names and "gkba_collision" in names and "gkba_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1905_01180_gb300 import gkba
+    assert sorted(gkba.EXPORTED) == names
+
+
+def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None):
+    from paper_1905_01180_gb300 import gkba
+    s = gi.system(4, 4, seed=0)
+    h = s["h"] if h is None else h
+    v = s["v"] if v is None else v
+    d = s["d"] if d is None else d
+    rho = s["rho0"] if rho is None else rho
+    cfg = gkba.Config(N=N, dt=dt, max_steps=1, precision=prec, cuda_stream=None,
+                      workspace_bytes=0, device=-1, timing=0)
+    out = ctypes.c_void_p()
+    arrs = [np.ascontiguousarray(x) for x in (h, v, d, rho)]
+    st = lib.gkba_init(ctypes.byref(out), ctypes.byref(cfg), *[a.ctypes.data for a in arrs], 0)
+    return st, out, lib.gkba_last_error(None).decode()
+
+
+def test_init_rejects_bad_sizes_and_inputs(lib):
+    from paper_1905_01180_gb300 import gkba
+    st, out, msg = _init(lib, N=0)
+    assert st == gkba.EINVAL and out.value is None and "N=0" in msg
+    st, _, _ = _init(lib, N=129)
+    assert st == gkba.EINVAL
+    st, _, msg = _init(lib, dt=-1.0)
+    assert st == gkba.EINVAL and "dt" in msg
+    st, _, _ = _init(lib, prec=7)
+    assert st == gkba.EINVAL
+    s = gi.system(4, 4, seed=0)
+    h = s["h"].copy()
+    h[0, 1] += 0.3
+    st, _, msg = _init(lib, h=h)
+    assert st == gkba.EINVAL and "Hermitian" in msg
+    v = s["v"].copy()
+    v[0, 1, 2, 3] += 1.0
+    st, _, msg = _init(lib, v=v)
+    assert st == gkba.EINVAL and "symmetry" in msg
+    rho = s["rho0"].copy()
+    rho[1, 1] = np.nan
+    st, _, msg = _init(lib, rho=rho)
+    assert st == gkba.EINVAL and "non-finite" in msg
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    from paper_1905_01180_gb300 import gkba
+    assert lib.gkba_collision(None, 1, None, None, None, None, 0) == gkba.EINVAL
+    assert lib.gkba_step(None, 0.0, 0.0, None, None, None) == gkba.EINVAL
+    assert lib.gkba_sigma(None, 1, None, None, None, 0) == gkba.EINVAL
+    lib.gkba_destroy(None)
+
+
+def test_product_path_does_not_import_oracle():
+    import subprocess
+    import sys
+    code = ("import sys; import paper_1905_01180_gb300 as p; p.load(); "
+            "assert 'oracle' not in sys.modules, 'oracle imported'")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

@@ -1,0 +1,287 @@
+"""GPU parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (relative Frobenius norm, per output matrix):
+  * FP64 path: 1e-10 (every step runs in FP64; what remains is summation order).
+  * split-TF32 path: each product is hi*hi + hi*lo + lo*hi with hi = rna_tf32(x),
+    lo = rna_tf32(x - hi), so a product carries a relative error of about
+    2^-22 (the dropped lo*lo term and the rounding of lo); the four stages store
+    their intermediates in FP32 (2^-24) and accumulate in FP32 inside K-chunks
+    of at most 4096 terms.  Sigma and I are sums with cancellation (direct minus
+    exchange, Sigma^> G^< minus Sigma^< G^>), so the gate is 2e-5 on Sigma and
+    I, and 1e-5 on rho(t) over a propagation (the FP64 Heun update and history
+    sum damp the contraction error by dt).
+"""
+import numpy as np
+import pytest
+
+import gkba_inputs as gi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL_TC = 2e-5
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as p
+    return p
+
+
+def ctx_for(P, N, n_P=8, seed=0, precision="fp64", dt=0.05, max_steps=0, v=None):
+    s = gi.system(N, n_P, seed=seed)
+    if v is not None:
+        s["v"] = v
+    return s, P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=max_steps,
+                        precision=precision)
+
+
+# ---------------------------------------------------------------- a4: Sigma
+@pytest.mark.parametrize("N", [1, 4, 7, 13])
+def test_sigma_fp64(P, N):
+    s, ctx = ctx_for(P, N, seed=N)
+    G = np.stack([gi.random_pair(N, seed=10 * N + u)[0] for u in range(3)])
+    Gb = np.stack([gi.random_pair(N, seed=10 * N + u)[1] for u in range(3)])
+    S = ctx.sigma(G, Gb)
+    ref = O.sigma_independent(s["v"], G, Gb)
+    if N <= 4:
+        assert rel(ref, O.sigma_bruteforce(s["v"], G, Gb)) < 1e-12
+    for u in range(3):
+        assert rel(S[u], ref[u]) < TOL64
+    ctx.close()
+
+
+@pytest.mark.parametrize("N", [4, 13, 16, 24, 33, 48])
+def test_sigma_tf32(P, N):
+    s, ctx = ctx_for(P, N, seed=N, precision="tf32")
+    U = 3
+    G = np.stack([gi.random_pair(N, seed=7 * N + u)[0] for u in range(U)])
+    Gb = np.stack([gi.random_pair(N, seed=7 * N + u)[1] for u in range(U)])
+    S = ctx.sigma(G, Gb)
+    ref = O.sigma_paper(s["v"], G, Gb)
+    errs = [rel(S[u], ref[u]) for u in range(U)]
+    print(f"N={N} split-TF32 Sigma rel errors {errs}")
+    assert max(errs) < TOL_TC
+    ctx.close()
+
+
+def test_sigma_hubbard_and_ohno_closed_forms_fp64(P):
+    # the CUDA path reproduces Eqs. (2b-diag) and (2b-symm) directly
+    N = 6
+    U = np.linspace(0.5, 1.5, N)
+    vh = np.zeros((N,) * 4)
+    for i in range(N):
+        vh[i, i, i, i] = U[i]
+    s, ctx = ctx_for(P, N, v=vh)
+    G, Gb = gi.random_pair(N, seed=3)
+    assert rel(ctx.sigma(G, Gb), O.sigma_hubbard(U, G, Gb)) < TOL64
+    ctx.close()
+    idx = np.arange(N)
+    V = 1.0 / np.sqrt(1.0 + (idx[:, None] - idx[None, :]) ** 2)
+    vo = np.zeros((N,) * 4)
+    for i in range(N):
+        for j in range(N):
+            vo[i, j, j, i] = V[i, j]
+    s, ctx = ctx_for(P, N, v=vo)
+    assert rel(ctx.sigma(G, Gb), O.sigma_symmetric(V, G, Gb)) < TOL64
+    ctx.close()
+
+
+def test_sigma_zero_and_scaling(P):
+    N = 8
+    s, ctx = ctx_for(P, N)
+    G, Gb = gi.random_pair(N, seed=1)
+    S = ctx.sigma(G, Gb)
+    a, b = 0.5 - 0.25j, 1.5 + 0.5j
+    assert rel(ctx.sigma(a * G, b * Gb), a * a * b * S) < TOL64
+    ctx.close()
+    s, ctx = ctx_for(P, N, v=np.zeros((N,) * 4))
+    assert np.abs(ctx.sigma(G, Gb)).max() == 0.0
+    ctx.close()
+
+
+# ------------------------------------------------------- a2-a5: collision I
+@pytest.mark.parametrize("N,L", [(4, 1), (4, 2), (5, 7), (9, 4)])
+def test_collision_fp64(P, N, L):
+    s, ctx = ctx_for(P, N, seed=N + L)
+    rho, T = gi.history(N, L, 0.05, seed=L)
+    I = ctx.collision(rho, T)
+    ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.05))
+    if L == 1:
+        assert np.abs(I).max() == 0.0
+    else:
+        assert rel(I, ref) < TOL64
+        assert abs(np.trace(I).real) < 1e-12 * np.abs(I).max() * N
+    # explicit weights
+    w = np.linspace(0.2, 1.0, L)
+    assert rel(ctx.collision(rho, T, w), O.collision(s["v"], rho, T, w)) < TOL64
+    ctx.close()
+
+
+@pytest.mark.parametrize("N,L", [(16, 6), (24, 5), (13, 9)])
+def test_collision_tf32(P, N, L):
+    s, ctx = ctx_for(P, N, seed=N + L, precision="tf32")
+    rho, T = gi.history(N, L, 0.05, seed=L)
+    I = ctx.collision(rho, T)
+    ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.05))
+    e = rel(I, ref)
+    print(f"N={N} L={L} split-TF32 collision rel err {e:.3e}")
+    assert e < TOL_TC
+    ctx.close()
+
+
+def test_collision_batches_larger_than_workspace(P):
+    # a workspace cap that fits only two units forces many batches; the result
+    # must not depend on the batching (fixed-order FP64 history sum)
+    N, L = 6, 9
+    s = gi.system(N, 8, seed=3)
+    rho, T = gi.history(N, L, 0.05, seed=4)
+    ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.05))
+    small = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.05, workspace_bytes=200_000)
+    big = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.05)
+    a, b = small.collision(rho, T), big.collision(rho, T)
+    assert rel(a, ref) < TOL64 and rel(b, ref) < TOL64
+    small.close()
+    big.close()
+
+
+def test_collision_device_buffers(P):
+    import torch
+    N, L = 8, 5
+    s, ctx = ctx_for(P, N)
+    rho, T = gi.history(N, L, 0.05, seed=5)
+    I_host = ctx.collision(rho, T)
+    I_dev = ctx.collision(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+    assert np.array_equal(I_dev.cpu().numpy(), I_host)
+    ctx.close()
+
+
+# ------------------------------------------------------------ a6: stepper
+def test_mean_field(P):
+    N = 10
+    s, ctx = ctx_for(P, N)
+    rho, _ = gi.history(N, 1, 0.05, seed=1)
+    assert rel(ctx.mean_field(rho[0]), O.hf_self_energy(s["v"], rho[0])) < 1e-13
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def config0_ref():
+    s = gi.system(4, 8, seed=0)
+    dt, n = 0.05, 200
+    E = gi.field(dt * np.arange(n + 1))
+    return s, dt, n, E, O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, E)
+
+
+def test_config0_full_run_fp64(P, config0_ref):
+    # N=4, 8 factors, dt=0.05, 200 Heun steps with the pulse, vs the oracle
+    s, dt, n, E, ref = config0_ref
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
+    worst_rho = worst_I = 0.0
+    for k in range(n):
+        rho, I, diag = ctx.step(E[k], E[k + 1])
+        worst_rho = max(worst_rho, rel(rho, ref.rho[k + 1]))
+        if k > 0:
+            worst_I = max(worst_I, rel(I, ref.I[k]))
+        assert abs(diag[2] - ref.energy_corr[k]) < 1e-10
+        assert abs(diag[1] - ref.energy_total[k]) < 1e-10
+        assert abs(diag[0] - 1.0) < 1e-12
+    assert worst_rho < TOL64, worst_rho
+    assert worst_I < TOL64, worst_I
+    with pytest.raises(P.GKBAError) as ei:
+        ctx.step(0.0, 0.0)  # history full
+    assert ei.value.status == 4
+    ctx.close()
+
+
+def test_config1_first_steps_fp64_and_tf32(P):
+    # N=24, 32 factors, dt=0.02: FP64 path vs the oracle, and split-TF32 vs FP64
+    s = gi.system(24, 32, seed=0)
+    dt, n = 0.02, 12
+    E = gi.field(dt * np.arange(n + 1))
+    ref = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, E)
+    c64 = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
+    ctc = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision="tf32")
+    w64 = wtc = 0.0
+    for k in range(n):
+        r64, _, _ = c64.step(E[k], E[k + 1])
+        rtc, _, _ = ctc.step(E[k], E[k + 1])
+        w64 = max(w64, rel(r64, ref.rho[k + 1]))
+        wtc = max(wtc, rel(rtc, r64))
+    print(f"config1 {n} steps: FP64 vs oracle {w64:.2e}, split-TF32 vs FP64 {wtc:.2e}")
+    assert w64 < TOL64
+    assert wtc < 1e-5
+    c64.close()
+    ctc.close()
+
+
+def test_checkpoint_resume_bitwise(P):
+    s = gi.system(6, 8, seed=2)
+    dt, n, cut = 0.05, 12, 5
+    E = gi.field(dt * np.arange(n + 1))
+    a = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
+    for k in range(n):
+        ra, _, _ = a.step(E[k], E[k + 1])
+    b = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
+    for k in range(cut):
+        b.step(E[k], E[k + 1])
+    m, rh, Th = b.get_history()
+    assert m == cut
+    c = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
+    c.set_history(m, rh, Th)
+    for k in range(cut, n):
+        rc, _, _ = c.step(E[k], E[k + 1])
+    assert np.array_equal(rc, ra)
+    for x in (a, b, c):
+        x.close()
+
+
+def test_tf32_rejects_large_basis(P):
+    s = gi.system(4, 4, seed=0)
+    N = 100
+    with pytest.raises(P.GKBAError) as ei:
+        P.Context(np.eye(N, dtype=complex), np.zeros((N,) * 4), np.eye(N, dtype=complex),
+                  np.eye(N, dtype=complex), 0.05, precision="tf32")
+    assert ei.value.status == 1
+
+
+# ------------------------------------------------ full size (N = 96)
+@pytest.mark.slow
+def test_full_size_n96_sigma_tf32(P):
+    # the bench's basis: N = 96 with 64 factors; one GKBA unit (G = P_k,
+    # Gbar = Q_k^+ of a synthetic history point) checked against the oracle
+    N = 96
+    s = gi.system(N, 64, seed=0)
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.02, precision="tf32")
+    rho, T = gi.history(N, 2, 0.02, seed=0)
+    Pk = T[0] @ rho[0]
+    Qk = T[0] - Pk
+    G, Gb = Pk, Qk.conj().T
+    S = ctx.sigma(G[None], Gb[None])[0]
+    ref = O.sigma_independent(s["v"], G, Gb)
+    e = rel(S, ref)
+    print(f"N=96 split-TF32 Sigma rel err {e:.3e}")
+    assert e < TOL_TC
+    ctx.close()
+
+
+def test_collision_n48_tf32(P):
+    N, L = 48, 3
+    s, ctx = ctx_for(P, N, n_P=16, seed=1, precision="tf32")
+    rho, T = gi.history(N, L, 0.02, seed=2)
+    I = ctx.collision(rho, T)
+    ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.02), chunk=2)
+    e = rel(I, ref)
+    print(f"N=48 L=3 split-TF32 collision rel err {e:.3e}")
+    assert e < TOL_TC
+    ctx.close()
