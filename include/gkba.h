@@ -76,6 +76,11 @@ typedef struct {
     int device;        /* CUDA device ordinal (-1 = current device) */
     int timing;        /* nonzero: time every contraction kernel with CUDA events
                           (see gkba_get_stats) */
+    int s4_kchunk;     /* GKBA_SPLIT_TF32: length of the FP32 partial sums of the
+                          last contraction (K = N^3) before they are added in
+                          FP64; a multiple of 32, 0 = default 512.  Shorter chunks
+                          bound the tensor-core accumulation error, longer ones
+                          write fewer partials. */
 } gkba_config;
 
 /* Per-kernel-class counters (see gkba_get_stats). */

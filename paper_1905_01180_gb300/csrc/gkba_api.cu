@@ -103,7 +103,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const double x_bytes = tc ? 2.0 * Np * Np * Np * Np * 4 : 2.0 * NN * NN * 8;
     const double form_bytes = tc ? 4.0 * 2 * Np * Np * 4 : (2.0 * NN + 4.0 * NN) * 8;
     const double N3 = (double)NN * N;
-    const double part_per_unit = tc ? (std::ceil((double)Np * Np * Np / 4096.0) * Np * 2.0 * Np * 4)
+    const double part_per_unit = tc ? (std::ceil((double)Np * Np * Np / c->s4_kchunk) * Np * 2.0 * Np * 4)
                                     : (std::ceil(N3 / 8192.0) * N * 2.0 * N * 8);
     const double per_unit = 2 * x_bytes + form_bytes + part_per_unit + 4.0 * NN * 16 + 8;
     size_t cap = c->ws_cap;
@@ -131,7 +131,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const size_t oX13 = cv.take((size_t)(x_bytes * ub));
     const size_t oX2 = cv.take((size_t)(x_bytes * ub));
     size_t part_bytes;
-    if (tc) part_bytes = tf32_part_bytes((int)Np, ub);
+    if (tc) part_bytes = tf32_part_bytes((int)Np, ub, c->s4_kchunk);
     else {
         const long long nz = (long long)std::ceil(N3 / 8192.0);
         part_bytes = (size_t)(nz * N * 2LL * N * ub * 8);
@@ -329,6 +329,9 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         return fail(nullptr, GKBA_EINVAL, "gkba_init: dt must be positive and finite");
     if (cfg->max_steps < 0 || cfg->max_steps > 100000000)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: max_steps=%d invalid", cfg->max_steps);
+    if (cfg->s4_kchunk < 0 || cfg->s4_kchunk % 32 != 0)
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: s4_kchunk=%d must be a non-negative multiple of 32",
+                    cfg->s4_kchunk);
     if (cfg->precision != GKBA_FP64 && cfg->precision != GKBA_SPLIT_TF32)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown precision %d", cfg->precision);
     const int Np = ((N + 15) / 16) * 16;
@@ -370,6 +373,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     c->prec = cfg->precision;
     c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)16 << 30);
     c->timing = cfg->timing != 0;
+    c->s4_kchunk = cfg->s4_kchunk > 0 ? cfg->s4_kchunk : 512;
     c->device = -1;
     auto bail = [&](gkba_status st) {
         {

@@ -48,6 +48,7 @@ struct gkba_ctx {
     size_t ws_cap = 0;
     bool timing = false;
     int num_sms = 0;
+    int s4_kchunk = 512;
 
     // model on the device
     double2* h = nullptr;   // N*N
@@ -214,7 +215,7 @@ gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double
 gkba_status build_forms_tf32(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
                                    const void* part, bool fp32, double2* S);
-size_t tf32_part_bytes(int Np, int ub);
+size_t tf32_part_bytes(int Np, int ub, int kchunk);
 
 // Workspace sizing: make sure the workspace holds ub units (returns actual ub).
 gkba_status ensure_workspace(gkba_ctx* c, int want_units);

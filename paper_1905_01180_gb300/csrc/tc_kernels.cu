@@ -15,7 +15,7 @@
 //     into tensor memory (tcgen05.st), where the MMA reads A;
 //   * B (the small per-unit matrix, or v for S4) is stored pre-split hi/lo;
 //   * each K-step issues hi*hi + hi*lo + lo*hi (3xTF32) into an FP32 TMEM
-//     accumulator; S4 is split over K in chunks of 4096 whose FP32 partial
+//     accumulator; S4 is split over K in chunks (default 512) whose FP32 partial
 //     sums are added in FP64 by the reduction kernel.
 // Complex data is planar: S2/S3 read the (re, im) planes of A as separate
 // K-chunks; the im plane multiplies the [Im G; Re G] halves of B with the
@@ -942,7 +942,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     FinalParams fp{};
     fp.Np = Np;
     fp.K = N3;
-    fp.KW = 4096;
+    fp.KW = c->s4_kchunk;
     fp.nks = (int)((N3 + fp.KW - 1) / fp.KW);
     fp.rows = rows;
     fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
@@ -961,9 +961,9 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
 }
 
-size_t tf32_part_bytes(int Np, int ub) {
+size_t tf32_part_bytes(int Np, int ub, int kchunk) {
     const long long N3 = (long long)Np * Np * Np;
-    const long long nks = (N3 + 4095) / 4096;
+    const long long nks = (N3 + kchunk - 1) / kchunk;
     const long long rows = 2LL * Np * ub;
     const long long Rld = ((rows + 255) / 256) * 256;
     return (size_t)(nks * Np * Rld * 4);

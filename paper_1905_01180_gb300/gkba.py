@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dt", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("s4_kchunk", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -105,7 +105,7 @@ class Context:
     """One GKBA system on one GPU (wraps a gkba_ctx)."""
 
     def __init__(self, h, v, d, rho0, dt, max_steps=0, precision="fp64", stream=None,
-                 workspace_bytes=0, device=-1, timing=False):
+                 workspace_bytes=0, device=-1, timing=False, s4_kchunk=0):
         L = load()
         on_dev = _is_torch(h)
         N = int(h.shape[0])
@@ -119,7 +119,7 @@ class Context:
         prec = {"fp64": FP64, "tf32": SPLIT_TF32, FP64: FP64, SPLIT_TF32: SPLIT_TF32}[precision]
         cfg = Config(N=N, dt=float(dt), max_steps=int(max_steps), precision=prec,
                      cuda_stream=stream, workspace_bytes=int(workspace_bytes), device=int(device),
-                     timing=1 if timing else 0)
+                     timing=1 if timing else 0, s4_kchunk=int(s4_kchunk))
         handle = ctypes.c_void_p()
         st = L.gkba_init(ctypes.byref(handle), ctypes.byref(cfg), ph[1], pv[1], pd[1], pr[1],
                          1 if on_dev else 0)

@@ -44,7 +44,7 @@ def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None):
     d = s["d"] if d is None else d
     rho = s["rho0"] if rho is None else rho
     cfg = gkba.Config(N=N, dt=dt, max_steps=1, precision=prec, cuda_stream=None,
-                      workspace_bytes=0, device=-1, timing=0)
+                      workspace_bytes=0, device=-1, timing=0, s4_kchunk=0)
     out = ctypes.c_void_p()
     arrs = [np.ascontiguousarray(x) for x in (h, v, d, rho)]
     st = lib.gkba_init(ctypes.byref(out), ctypes.byref(cfg), *[a.ctypes.data for a in arrs], 0)

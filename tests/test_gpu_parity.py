@@ -277,7 +277,7 @@ def test_full_size_n96_sigma_tf32(P):
 
 def test_collision_n48_tf32(P):
     N, L = 48, 3
-    s, ctx = ctx_for(P, N, n_P=16, seed=1, precision="tf32")
+    s, ctx = ctx_for(P, N, n_P=16, seed=1, precision="tf32", dt=0.02)
     rho, T = gi.history(N, L, 0.02, seed=2)
     I = ctx.collision(rho, T)
     ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.02), chunk=2)
