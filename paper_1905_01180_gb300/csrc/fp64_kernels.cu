@@ -364,23 +364,52 @@ __global__ void k_gkba_units(int N, int nk, int k0, int L, double dt, const doub
 }
 
 // S_u[i][j] = sum_z part[z][i][u*2N + j] + i part[z][i][u*2N + N + j]
-// (split-K partials of the last contraction, rows (u, c, j), FP64 sum in
-// fixed z order).  Partials are FP64 (FP64 path) or FP32 (tensor-core path).
+// (split-K partials of the last contraction, rows (u, c, j)).  Two passes with
+// a fixed summation order (deterministic): pass 1 sums z-range zc of each
+// element into tmp[zc], pass 2 adds the z-ranges in order.  Partials are FP64
+// (FP64 path) or FP32 (tensor-core path); all sums are FP64.
 template <typename TP>
-__global__ void k_reduce_partials(int N, int Np, int nb, int nz, long long zstride, long long Rld,
-                                  const TP* __restrict__ part, double2* __restrict__ S) {
+__global__ void k_reduce_partials_p1(int N, int Np, int nb, int nz, int zper, long long zstride,
+                                     long long Rld, const TP* __restrict__ part,
+                                     double2* __restrict__ tmp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long NN = (long long)N * N;
     if (e >= NN * nb) return;
+    const int zc = blockIdx.y;
     const int u = (int)(e / NN);
     const int rr = (int)(e % NN);
     const int i = rr / N, j = rr % N;
     const long long r_re = (long long)u * 2 * Np + j, r_im = r_re + Np;
+    const int z0 = zc * zper, z1 = min(nz, z0 + zper);
+    double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
+    const TP* base = part + (long long)i * Rld;
+    int z = z0;
+    for (; z + 4 <= z1; z += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const TP* pz = base + (long long)(z + q) * zstride;
+            re[q] += (double)pz[r_re];
+            im[q] += (double)pz[r_im];
+        }
+    }
+    for (; z < z1; ++z) {
+        const TP* pz = base + (long long)z * zstride;
+        re[0] += (double)pz[r_re];
+        im[0] += (double)pz[r_im];
+    }
+    tmp[(long long)zc * NN * nb + e] =
+        make_double2((re[0] + re[1]) + (re[2] + re[3]), (im[0] + im[1]) + (im[2] + im[3]));
+}
+
+__global__ void k_reduce_partials_p2(long long n, int nzc, const double2* __restrict__ tmp,
+                                     double2* __restrict__ S) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
     double re = 0.0, im = 0.0;
-    for (int z = 0; z < nz; ++z) {
-        const TP* pz = part + (long long)z * zstride + (long long)i * Rld;
-        re += (double)pz[r_re];
-        im += (double)pz[r_im];
+    for (int zc = 0; zc < nzc; ++zc) {
+        const double2 t = tmp[(long long)zc * n + e];
+        re += t.x;
+        im += t.y;
     }
     S[e] = make_double2(re, im);
 }
@@ -611,14 +640,20 @@ gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
                                    const void* part, bool fp32, double2* S) {
     const long long NN = (long long)c->N * c->N;
+    const int nzc = nz < kReduceSplit ? nz : kReduceSplit;
+    const int zper = (nz + nzc - 1) / nzc;
+    const int Np = c->prec == GKBA_SPLIT_TF32 ? c->Np : c->N;
+    dim3 g1(grid1(nb * NN, 256), nzc);
     auto t = launch_begin(c, K_RED, 0.0, 0.0);
     if (fp32)
-        k_reduce_partials<float><<<grid1(nb * NN, 256), 256, 0, c->stream>>>(
-            c->N, c->prec == GKBA_SPLIT_TF32 ? c->Np : c->N, nb, nz, zstride, Rld,
-            (const float*)part, S);
+        k_reduce_partials_p1<float><<<g1, 256, 0, c->stream>>>(c->N, Np, nb, nz, zper, zstride, Rld,
+                                                               (const float*)part, c->red_tmp);
     else
-        k_reduce_partials<double><<<grid1(nb * NN, 256), 256, 0, c->stream>>>(
-            c->N, c->N, nb, nz, zstride, Rld, (const double*)part, S);
+        k_reduce_partials_p1<double><<<g1, 256, 0, c->stream>>>(c->N, Np, nb, nz, zper, zstride,
+                                                                Rld, (const double*)part, c->red_tmp);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_reduce_partials_p2<<<grid1(nb * NN, 256), 256, 0, c->stream>>>(nb * NN, nzc, c->red_tmp, S);
     return launch_end(c, t);
 }
 

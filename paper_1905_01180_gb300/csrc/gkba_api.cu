@@ -105,7 +105,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const double N3 = (double)NN * N;
     const double part_per_unit = tc ? (std::ceil((double)Np * Np * Np / c->s4_kchunk) * Np * 2.0 * Np * 4)
                                     : (std::ceil(N3 / 8192.0) * N * 2.0 * N * 8);
-    const double per_unit = 2 * x_bytes + form_bytes + part_per_unit + 4.0 * NN * 16 + 8;
+    const double per_unit = 2 * x_bytes + form_bytes + part_per_unit + (4.0 + kReduceSplit) * NN * 16 + 8;
     size_t cap = c->ws_cap;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
@@ -144,6 +144,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const size_t oCoef = cv.take((size_t)ub * 8);
     const size_t oSu = cv.take((size_t)(ub * NN * 16));
     const size_t oYu = cv.take((size_t)(ub * NN * 16));
+    const size_t oRed = cv.take((size_t)(kReduceSplit * ub * NN * 16));
     void* ws = nullptr;
     if (cudaMalloc(&ws, cv.off) != cudaSuccess) {
         cudaGetLastError();
@@ -165,6 +166,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     c->coef = (double*)(b + oCoef);
     c->Su = (double2*)(b + oSu);
     c->Yu = (double2*)(b + oYu);
+    c->red_tmp = (double2*)(b + oRed);
     return GKBA_OK;
 }
 

@@ -8,9 +8,12 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gkba.h"
+#include "gkba.h"
 
 namespace gkba {
+
+// z-ranges of the two-pass split-K reduction of the last contraction
+constexpr int kReduceSplit = 16;
 
 // Kernel classes counted by gkba_get_stats.  The algorithmic flops and bytes
 // of each launch are added at launch time (see the per-class comments in
@@ -105,6 +108,7 @@ struct gkba_ctx {
     double* coef = nullptr;      // per-unit weight (+-c_k), ub
     double2* Su = nullptr;       // per-unit S, ub * N*N
     double2* Yu = nullptr;       // per-unit coef * S . Gbar, ub * N*N
+    double2* red_tmp = nullptr;  // split-K reduction scratch: kReduceSplit * ub * N*N
 
     // caller-buffer staging for host-pointer calls
     void* stage = nullptr;

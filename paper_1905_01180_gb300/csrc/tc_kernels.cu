@@ -11,8 +11,8 @@
 // real GEMM D[M][Nc] = sum_K A[M][K] B[Nc][K]:
 //   * A (the large, streamed operand) is FP32 in HBM; TMA stages 128 x 32
 //     tiles (128-byte swizzle) in shared memory, a converter warpgroup splits
-//     every element into TF32 hi = rna(x) and lo = rna(x - hi) and writes both
-//     into tensor memory (tcgen05.st), where the MMA reads A;
+//     every element into TF32 hi and lo (x = hi + lo, see split_tf32) and
+//     writes both into tensor memory (tcgen05.st), where the MMA reads A;
 //   * B (the small per-unit matrix, or v for S4) is stored pre-split hi/lo;
 //   * each K-step issues hi*hi + hi*lo + lo*hi (3xTF32) into an FP32 TMEM
 //     accumulator; S4 is split over K in chunks (default 512) whose FP32 partial
@@ -87,6 +87,14 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
             }
         }
     }
+}
+// Warp-uniform bounded wait: every lane waits, and the warp leaves a loop
+// together when any lane's wait gives up (no lane is left at a later
+// __syncwarp or warp-collective tcgen05 instruction).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err, int code) {
+    const bool r = mbar_wait(bar, parity, abort_flag, err, code);
+    return __all_sync(0xffffffffu, r);
 }
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -206,24 +214,41 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n, int negB) {
            ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
-// Split row r (0..127) of a 128 x 32 FP32 tile written by TMA with the 128-byte
-// swizzle into TF32 hi / lo and store them in TMEM columns [col, col+32) and
-// [col+32, col+64) of this warp's lanes.
-__device__ __forceinline__ void split_row_to_tmem(const uint8_t* tile, int r, uint32_t taddr) {
-    uint32_t hi[32], lo[32];
+// TF32 split of the streamed A operand, selected at compile time:
+//   0: hi = rna(x), lo = rna(x - hi)           (|error| <= 2^-23 |x| per element)
+//   1: hi = x truncated to TF32, lo = rna(x - hi)
+//   2: hi = x truncated to TF32, lo = x - hi    (the MMA keeps lo's leading
+//      11 bits: |error| <= 2^-21 |x|), two full-rate integer/FP ops per element
+#ifndef GKBA_SPLIT_MODE
+#define GKBA_SPLIT_MODE 2
+#endif
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+#if GKBA_SPLIT_MODE == 0
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+#elif GKBA_SPLIT_MODE == 1
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = tf32_rna(x - __uint_as_float(hi));
+#else
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+#endif
+}
+
+// Load row r (0..127) of a 128 x 32 FP32 tile written by TMA with the 128-byte
+// swizzle (16-byte chunk j of row r sits at chunk j ^ (r & 7)) and split it
+// into TF32 hi / lo registers.
+__device__ __forceinline__ void load_split_row(const uint8_t* tile, int r, uint32_t (&hi)[32],
+                                               uint32_t (&lo)[32]) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float4 v = *reinterpret_cast<const float4*>(tile + r * 128 + ((j ^ (r & 7)) << 4));
-        const float xs[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint32_t h = tf32_rna(xs[e]);
-            hi[4 * j + e] = h;
-            lo[4 * j + e] = tf32_rna(xs[e] - __uint_as_float(h));
-        }
+        split_tf32(v.x, hi[4 * j + 0], lo[4 * j + 0]);
+        split_tf32(v.y, hi[4 * j + 1], lo[4 * j + 1]);
+        split_tf32(v.z, hi[4 * j + 2], lo[4 * j + 2]);
+        split_tf32(v.w, hi[4 * j + 3], lo[4 * j + 3]);
     }
-    tmem_st32(taddr, hi);
-    tmem_st32(taddr + 32, lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -258,9 +283,10 @@ __global__ void __launch_bounds__(kStageThreads, 1)
     uint8_t* sA = sBlo + p.kch * chunkB;
     uint64_t* bars = (uint64_t*)(sA + kStageAStages * kTileBytes);
     // barrier indices
-    const int BFULL = 0, BEMPTY = 1, AFULL = 2, AEMPTY = 6, TFULL = 10, TEMPTY = 12, ACCF = 14,
-              ACCE = 16, DRAIN = 18;
-    uint32_t* tmem_slot = (uint32_t*)(bars + 20);
+    constexpr int BFULL = 0, BEMPTY = 1, AFULL = 2, AEMPTY = AFULL + kStageAStages,
+                  TFULL = AEMPTY + kStageAStages, TEMPTY = TFULL + 2, ACCF = TEMPTY + 2,
+                  ACCE = ACCF + 2, DRAIN = ACCE + 2, NBARS = DRAIN + 1;
+    uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     auto bar = [&](int i) { return smem_u32(bars + i); };
 
@@ -428,14 +454,18 @@ __global__ void __launch_bounds__(kStageThreads, 1)
             for (int c = 0; c < chunks_per_tile; ++c, ++it) {
                 const int s = (int)(it % kStageAStages);
                 const uint32_t ph = (uint32_t)((it / kStageAStages) & 1);
-                if (!mbar_wait(bar(AFULL + s), ph, abort_flag, p.err, 6)) { ok = false; break; }
-                const int slot = (int)(it & 1);
-                const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                if (!mbar_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 7)) { ok = false; break; }
-                tc_fence_after();
-                split_row_to_tmem(sA + s * kTileBytes, r, lane_base + (slot ? 448u : 192u));
+                if (!warp_wait(bar(AFULL + s), ph, abort_flag, p.err, 6)) { ok = false; break; }
+                uint32_t hi[32], lo[32];
+                load_split_row(sA + s * kTileBytes, r, hi, lo);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(AEMPTY + s));
+                const int slot = (int)(it & 1);
+                const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                if (!warp_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 7)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t ta = lane_base + (slot ? 448u : 192u);
+                tmem_st32(ta, hi);
+                tmem_st32(ta + 32, lo);
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
@@ -454,7 +484,7 @@ __global__ void __launch_bounds__(kStageThreads, 1)
             const int u = (int)(t / p.mtiles), mt = (int)(t % p.mtiles);
             const int ab = (int)(tile_i & 1);
             const uint32_t abph = (uint32_t)((tile_i >> 1) & 1);
-            if (!mbar_wait(bar(ACCF + ab), abph, abort_flag, p.err, 8)) { ok = false; break; }
+            if (!warp_wait(bar(ACCF + ab), abph, abort_flag, p.err, 8)) { ok = false; break; }
             tc_fence_after();
             const long long row = (long long)mt * kBM + rloc;
             const bool valid = row < p.M;
@@ -516,8 +546,10 @@ __global__ void __launch_bounds__(kFinThreads, 1)
     const uint32_t bbytes = (uint32_t)(Np * 128);
     const uint32_t stage_bytes = 2 * kTileBytes + 2 * bbytes;
     uint64_t* bars = (uint64_t*)(smem + kFinStages * stage_bytes);
-    const int FULL = 0, EMPTY = 3, TFULL = 6, TEMPTY = 8, ACCF = 10, ACCE = 11, DRAIN = 12;
-    uint32_t* tmem_slot = (uint32_t*)(bars + 14);
+    constexpr int FULL = 0, EMPTY = FULL + kFinStages, TFULL = EMPTY + kFinStages,
+                  TEMPTY = TFULL + 2, ACCF = TEMPTY + 2, ACCE = ACCF + 1, DRAIN = ACCE + 1,
+                  NBARS = DRAIN + 1;
+    uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     auto bar = [&](int i) { return smem_u32(bars + i); };
     auto stA = [&](int s, int t) { return smem + s * stage_bytes + t * kTileBytes; };
@@ -641,15 +673,21 @@ __global__ void __launch_bounds__(kFinThreads, 1)
             for (long long k = k0; k < k1; k += kKC, ++it) {
                 const int s = (int)(it % kFinStages);
                 const uint32_t ph = (uint32_t)((it / kFinStages) & 1);
-                if (!mbar_wait(bar(FULL + s), ph, abort_flag, p.err, 14)) { ok = false; break; }
-                const int slot = (int)(it & 1);
-                const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                if (!mbar_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 15)) { ok = false; break; }
-                tc_fence_after();
-                split_row_to_tmem(stA(s, 0), r, lane_base + 256u + (uint32_t)(slot * 128));
-                split_row_to_tmem(stA(s, 1), r, lane_base + 256u + (uint32_t)(slot * 128 + 64));
+                if (!warp_wait(bar(FULL + s), ph, abort_flag, p.err, 14)) { ok = false; break; }
+                uint32_t hi0[32], lo0[32], hi1[32], lo1[32];
+                load_split_row(stA(s, 0), r, hi0, lo0);
+                load_split_row(stA(s, 1), r, hi1, lo1);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(EMPTY + s));
+                const int slot = (int)(it & 1);
+                const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                if (!warp_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 15)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t ta = lane_base + 256u + (uint32_t)(slot * 128);
+                tmem_st32(ta, hi0);
+                tmem_st32(ta + 32, lo0);
+                tmem_st32(ta + 64, hi1);
+                tmem_st32(ta + 96, lo1);
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
@@ -664,7 +702,7 @@ __global__ void __launch_bounds__(kFinThreads, 1)
         bool ok = true;
         for (long long item = blockIdx.x; item < items && ok; item += gridDim.x, ++item_i) {
             const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
-            if (!mbar_wait(bar(ACCF), (uint32_t)(item_i & 1), abort_flag, p.err, 16)) { ok = false; break; }
+            if (!warp_wait(bar(ACCF), (uint32_t)(item_i & 1), abort_flag, p.err, 16)) { ok = false; break; }
             tc_fence_after();
             float* base = p.part + (long long)ks * Np * p.Rld;
             for (int t = 0; t < 2; ++t) {
@@ -802,10 +840,10 @@ gkba_status make_map(gkba_ctx* c, CUtensorMap* m, const void* base, int rank, co
 
 size_t stage_smem_bytes(int Np) {
     const int kch = (Np + kKC - 1) / kKC;
-    return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 256;
+    return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 512;
 }
 size_t final_smem_bytes(int Np) {
-    return 1024 + (size_t)kFinStages * (2 * kTileBytes + 2 * Np * 128) + 256;
+    return 1024 + (size_t)kFinStages * (2 * kTileBytes + 2 * Np * 128) + 512;
 }
 
 }  // namespace
