@@ -192,6 +192,34 @@ gkba_status gkba_adjoint(gkba_ctx* ctx, const double* E_samples, int n_steps, in
 gkba_status gkba_get_stats(gkba_ctx* ctx, gkba_kernel_stat* stats, int max_stats, int* n_stats,
                            long long* total_launches, int reset);
 
+/*
+ * gkba_sigma_noalloc - the FP64 self-energy of gkba_sigma (Eq. (2bse) for
+ * n_units pairs G, Gbar) without a context and without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory, such as code that runs while a CUDA graph is
+ * being captured, a host framework that owns every allocation on the device,
+ * or a service that runs under a fixed memory budget.
+ *   N        basis size, 1 <= N <= 24 (larger N is rejected with GKBA_EINVAL)
+ *   v        device pointer, N^4 real doubles v_ijkl (Eq. coulomb layout)
+ *   G, Gbar  device pointers, n_units * N*N complex each
+ *   S_out    device pointer, n_units * N*N complex
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = the legacy default stream)
+ *   err, err_len optional caller buffer for a message on failure
+ * Scratch is a 32 MiB file-scope __device__ array that every GPU which loads
+ * the library holds until the process exits; no cudaMalloc, cudaFree or other
+ * allocating routine is called.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device current);
+ * make that first call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (other streams, other threads)
+ * race with each other: serialise them.  Every scratch element a call reads
+ * is written earlier in the same call, so nothing left by a previous call
+ * leaks into the result.  The call only enqueues work: S_out is valid after
+ * the stream is synchronised; launch errors return GKBA_ECUDA.
+ */
+gkba_status gkba_sigma_noalloc(int N, int n_units, const double* v, const double* G,
+                               const double* Gbar, double* S_out, void* cuda_stream, char* err,
+                               size_t err_len);
+
 /* Message for the last failing call on ctx (or the last failed gkba_init when ctx is NULL). */
 const char* gkba_last_error(const gkba_ctx* ctx);
 

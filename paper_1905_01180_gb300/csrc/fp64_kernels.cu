@@ -6,7 +6,10 @@
 //  * the time-local pieces of Eq. (equalt): Sigma_HF, h_HF, commutator,
 //    U_n = exp(-i dt h) by scaling and squaring with a Taylor polynomial,
 //    the propagator recursion T(t_{n+1},t_k) = U_n T(t_n,t_k), Heun updates.
+#include <algorithm>
 #include <cmath>
+#include <cstdarg>
+#include <mutex>
 
 #include "gkba_internal.cuh"
 
@@ -718,3 +721,158 @@ gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
 }
 
 }  // namespace gkba
+
+namespace gkba {
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 self-energy (gkba_sigma_noalloc, include/gkba.h).
+//
+// For callers that cannot allocate device memory (code that runs while a
+// CUDA graph is being captured, inside a host framework that owns every
+// allocation, or under a fixed memory budget), this entry point evaluates the
+// same FP64 contraction as gkba_sigma without a context and without any
+// allocation: its scratch is the file-scope array below, which every GPU that
+// loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB per device
+constexpr int kNoAllocMaxN = 24;
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device ordinal (null until set up).
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+gkba_status noalloc_fail(char* err, size_t err_len, gkba_status st, const char* fmt, ...) {
+    if (err != nullptr && err_len > 0) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, err_len, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+}  // namespace gkba
+
+extern "C" gkba_status gkba_sigma_noalloc(int N, int n_units, const double* v, const double* G,
+                                          const double* Gbar, double* S_out, void* cuda_stream,
+                                          char* err, size_t err_len) {
+    using namespace gkba;
+    if (err != nullptr && err_len > 0) err[0] = '\0';
+    if (N < 1 || N > kNoAllocMaxN)
+        return noalloc_fail(err, err_len, GKBA_EINVAL,
+                            "gkba_sigma_noalloc: N=%d outside [1, %d] (static scratch of %zu bytes)", N,
+                            kNoAllocMaxN, kNoAllocScratchBytes);
+    if (n_units < 0) return noalloc_fail(err, err_len, GKBA_EINVAL, "gkba_sigma_noalloc: n_units < 0");
+    if (n_units == 0) return GKBA_OK;
+    if (!v || !G || !Gbar || !S_out)
+        return noalloc_fail(err, err_len, GKBA_EINVAL, "gkba_sigma_noalloc: NULL pointer argument");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess)
+        return noalloc_fail(err, err_len, GKBA_ECUDA, "gkba_sigma_noalloc: cudaGetDevice: %s",
+                            cudaGetErrorString(ce));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return noalloc_fail(err, err_len, GKBA_EUNSUPPORTED, "gkba_sigma_noalloc: device %d", dev);
+    void* base = nullptr;
+    {
+        // Set-up once per device (with that device current): the host-side
+        // symbol is a stand-in, so the kernels get the device address.
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (g_noalloc_addr[dev] == nullptr) {
+            void* p = nullptr;
+            ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (ce != cudaSuccess || p == nullptr)
+                return noalloc_fail(err, err_len, GKBA_ECUDA,
+                                    "gkba_sigma_noalloc: cudaGetSymbolAddress: %s",
+                                    cudaGetErrorString(ce));
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    const long long n = N, NN = n * n, N3 = NN * n, N4 = N3 * n;
+    const long long Kc = 8192;
+    const int nz = (int)((N3 + Kc - 1) / Kc);
+    // scratch layout: wS | vK | per-batch: B1 | Gr | X13 | X2 | part | red
+    const size_t model_b = 2 * round256((size_t)N4 * 8);
+    const size_t unit_b = round256((size_t)2 * NN * 8) + round256((size_t)4 * NN * 8) +
+                          2 * round256((size_t)2 * N4 * 8) + round256((size_t)nz * n * 2 * n * 8) +
+                          round256((size_t)kReduceSplit * NN * 16);
+    if (model_b + unit_b > kNoAllocScratchBytes)
+        return noalloc_fail(err, err_len, GKBA_EINVAL, "gkba_sigma_noalloc: N=%d does not fit", N);
+    const int ub = (int)std::min<size_t>((kNoAllocScratchBytes - model_b) / unit_b, (size_t)n_units);
+    char* s = (char*)base;
+    double* wS = (double*)s;
+    double* vK = (double*)(s + round256((size_t)N4 * 8));
+    char* q = s + model_b;
+    double* B1 = (double*)q;
+    q += round256((size_t)2 * NN * 8 * ub);
+    double* Gr = (double*)q;
+    q += round256((size_t)4 * NN * 8 * ub);
+    double* X13 = (double*)q;
+    q += round256((size_t)2 * N4 * 8 * ub);
+    double* X2 = (double*)q;
+    q += round256((size_t)2 * N4 * 8 * ub);
+    double* part = (double*)q;
+    q += round256((size_t)nz * n * 2 * n * 8 * ub);
+    double2* red = (double2*)q;
+    q += round256((size_t)kReduceSplit * NN * 16 * ub);
+    if ((size_t)(q - s) > kNoAllocScratchBytes)
+        return noalloc_fail(err, err_len, GKBA_EINVAL, "gkba_sigma_noalloc: scratch layout overflow");
+
+    // model operands (rebuilt on every call; every element is written)
+    k_build_wS64<<<grid1(N4, 256), 256, 0, stream>>>(N, v, wS);
+    k_build_vK64<<<grid1(N4, 256), 256, 0, stream>>>(N, v, vK);
+    const double2* Gd = (const double2*)G;
+    const double2* Gbd = (const double2*)Gbar;
+    double2* Sd = (double2*)S_out;
+    for (int u0 = 0; u0 < n_units; u0 += ub) {
+        const int nb = std::min(ub, n_units - u0);
+        k_forms64<<<grid1(nb * NN, 256), 256, 0, stream>>>(N, nb, Gd + u0 * NN, Gbd + u0 * NN, B1, Gr);
+        {
+            StageMap m{2 * N3, 2 * n, 1, n, 2 * NN, N, N, N};
+            dim3 g((2 * N + G64_BN - 1) / G64_BN, (unsigned)((N3 + G64_BM - 1) / G64_BM), nb);
+            k_gemm64_stage<<<g, 256, 0, stream>>>(wS, n, 0, B1, n, 2 * NN, X13, 2 * N4, (int)N3,
+                                                  2 * N, n, 0, 0, m);
+        }
+        {
+            StageMap m{2 * N3, 2 * NN, 1, n, 2 * n, N, N, N};
+            dim3 g((2 * N + G64_BN - 1) / G64_BN, (unsigned)((N3 + G64_BM - 1) / G64_BM), nb);
+            k_gemm64_stage<<<g, 256, 0, stream>>>(X13, 2 * n, 2 * N4, Gr, 2 * n, 4 * NN, X2, 2 * N4,
+                                                  (int)N3, 2 * N, 2 * n, 0, 0, m);
+        }
+        {
+            StageMap m{N3, n, 1, N4, NN, N, N, N};
+            dim3 g((2 * N + G64_BN - 1) / G64_BN, (unsigned)((N3 + G64_BM - 1) / G64_BM), nb);
+            k_gemm64_stage<<<g, 256, 0, stream>>>(X2, 2 * n, 2 * N4, Gr, 2 * n, 4 * NN, X13, 2 * N4,
+                                                  (int)N3, 2 * N, 2 * n, 0, 0, m);
+        }
+        const long long R = 2LL * n * nb;
+        {
+            StageMap m{0, 0, 1, 0, R, (int)R, 1, N};
+            dim3 g((N + G64_BN - 1) / G64_BN, (unsigned)((R + G64_BM - 1) / G64_BM), nz);
+            k_gemm64_stage<<<g, 256, 0, stream>>>(X13, N3, 0, vK, N3, 0, part, n * R, (int)R, N, N3,
+                                                  1, Kc, m);
+        }
+        const int nzc = nz < kReduceSplit ? nz : kReduceSplit;
+        const int zper = (nz + nzc - 1) / nzc;
+        dim3 g1(grid1(nb * NN, 256), nzc);
+        k_reduce_partials_p1<double><<<g1, 256, 0, stream>>>(N, N, nb, nz, zper, n * R, R, part, red);
+        k_reduce_partials_p2<<<grid1(nb * NN, 256), 256, 0, stream>>>(nb * NN, nzc, red, Sd + u0 * NN);
+    }
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess)
+        return noalloc_fail(err, err_len, GKBA_ECUDA, "gkba_sigma_noalloc: launch failed: %s",
+                            cudaGetErrorString(ce));
+    return GKBA_OK;
+}
+

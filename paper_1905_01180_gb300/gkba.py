@@ -25,7 +25,7 @@ _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIME
 
 EXPORTED = ["gkba_init", "gkba_sigma", "gkba_collision", "gkba_step", "gkba_set_history",
             "gkba_get_history", "gkba_get_state", "gkba_mean_field", "gkba_adjoint",
-            "gkba_get_stats", "gkba_last_error", "gkba_destroy"]
+            "gkba_get_stats", "gkba_last_error", "gkba_destroy", "gkba_sigma_noalloc"]
 
 
 class GKBAError(RuntimeError):
@@ -74,6 +74,7 @@ def load():
     L.gkba_last_error.restype = ctypes.c_char_p
     L.gkba_destroy.argtypes = [P]
     L.gkba_destroy.restype = None
+    L.gkba_sigma_noalloc.argtypes = [I, I, P, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTED:
         if name not in ("gkba_last_error", "gkba_destroy"):
             getattr(L, name).restype = ctypes.c_int
