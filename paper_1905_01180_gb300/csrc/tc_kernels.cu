@@ -382,6 +382,8 @@ __global__ void __launch_bounds__(kStageThreads, 1)
             const uint32_t id_full = idesc_tf32(2 * Np, 0);
             const uint32_t id_half = idesc_tf32(Np, 0);
             const uint32_t id_half_neg = idesc_tf32(Np, 1);
+            const unsigned long long dBhi0 = desc_sw128(smem_u32(sBhi));
+            const unsigned long long dBlo0 = desc_sw128(smem_u32(sBlo));
             int cur_u = -1;
             uint32_t bfph = 0;
             long long it = 0, tile_i = 0;
@@ -405,30 +407,35 @@ __global__ void __launch_bounds__(kStageThreads, 1)
                     const uint32_t sph = (uint32_t)((it >> 1) & 1);
                     if (!mbar_wait(bar(TFULL + slot), sph, abort_flag, p.err, 5)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t ahi = tmem + (slot ? 448u : 192u), alo = ahi + 32;
-                    const uint32_t bhi = smem_u32(sBhi) + kc * chunkB, blo = smem_u32(sBlo) + kc * chunkB;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t first = (c == 0 && kk == 0) ? 1u : 0u;
-                        const uint32_t ah = ahi + kk * 8, al = alo + kk * 8;
-                        if (pl == 0) {
-                            const unsigned long long dh = desc_sw128(bhi + kk * 32), dl = desc_sw128(blo + kk * 32);
-                            mma_tf32(dacc, ah, dh, id_full, first ? 0u : 1u);
-                            mma_tf32(dacc, ah, dl, id_full, 1u);
-                            mma_tf32(dacc, al, dh, id_full, 1u);
-                        } else {
-                            // D[:, 0:Np] += A_im * (-Im G);  D[:, Np:2Np] += A_im * Re G
-                            const uint32_t off_im = (uint32_t)(Np * 128);
-                            const unsigned long long dih = desc_sw128(bhi + off_im + kk * 32);
-                            const unsigned long long dil = desc_sw128(blo + off_im + kk * 32);
-                            const unsigned long long drh = desc_sw128(bhi + kk * 32);
-                            const unsigned long long drl = desc_sw128(blo + kk * 32);
-                            mma_tf32(dacc, ah, dih, id_half_neg, 1u);
-                            mma_tf32(dacc, ah, dil, id_half_neg, 1u);
-                            mma_tf32(dacc, al, dih, id_half_neg, 1u);
-                            mma_tf32(dacc + Np, ah, drh, id_half, 1u);
-                            mma_tf32(dacc + Np, ah, drl, id_half, 1u);
-                            mma_tf32(dacc + Np, al, drh, id_half, 1u);
+                    // Compact issue loop (a long unrolled body stalls this single
+                    // issuing thread on instruction fetch).  The start-address
+                    // field of a descriptor is addr >> 4, so a 32-byte K-step
+                    // adds 2 and the Im-half of B adds Np*128 >> 4.
+                    const uint32_t ahi = tmem + (slot ? 448u : 192u);
+                    const unsigned long long dh = dBhi0 + ((unsigned long long)(kc * chunkB) >> 4);
+                    const unsigned long long dl = dBlo0 + ((unsigned long long)(kc * chunkB) >> 4);
+                    if (pl == 0) {
+#pragma unroll 1
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t ah = ahi + kk * 8, al = ah + 32;
+                            const unsigned long long o = 2ull * kk;
+                            mma_tf32(dacc, ah, dh + o, id_full, (c | kk) ? 1u : 0u);
+                            mma_tf32(dacc, ah, dl + o, id_full, 1u);
+                            mma_tf32(dacc, al, dh + o, id_full, 1u);
+                        }
+                    } else {
+                        // D[:, 0:Np] += A_im * (-Im G);  D[:, Np:2Np] += A_im * Re G
+                        const unsigned long long im = (unsigned long long)(Np * 128) >> 4;
+#pragma unroll 1
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t ah = ahi + kk * 8, al = ah + 32;
+                            const unsigned long long o = 2ull * kk;
+                            mma_tf32(dacc, ah, dh + im + o, id_half_neg, 1u);
+                            mma_tf32(dacc, ah, dl + im + o, id_half_neg, 1u);
+                            mma_tf32(dacc, al, dh + im + o, id_half_neg, 1u);
+                            mma_tf32(dacc + Np, ah, dh + o, id_half, 1u);
+                            mma_tf32(dacc + Np, ah, dl + o, id_half, 1u);
+                            mma_tf32(dacc + Np, al, dh + o, id_half, 1u);
                         }
                     }
                     mma_commit(bar(TEMPTY + slot));
@@ -634,18 +641,17 @@ __global__ void __launch_bounds__(kFinThreads, 1)
                     const uint32_t sph = (uint32_t)((it >> 1) & 1);
                     if (!mbar_wait(bar(TFULL + slot), sph, abort_flag, p.err, 13)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t bhi = smem_u32(stBhi(s)), blo = smem_u32(stBlo(s));
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
+                    const unsigned long long dh = desc_sw128(smem_u32(stBhi(s)));
+                    const unsigned long long dl = desc_sw128(smem_u32(stBlo(s)));
+#pragma unroll 1
+                    for (int q = 0; q < 8; ++q) {  // q = (tile t, K-step kk), compact issue loop
+                        const int t = q >> 2, kk = q & 3;
                         const uint32_t dacc = tmem + (uint32_t)(t * 128);
-                        const uint32_t ahi = tmem + 256u + (uint32_t)(slot * 128 + t * 64), alo = ahi + 32;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const unsigned long long dh = desc_sw128(bhi + kk * 32), dl = desc_sw128(blo + kk * 32);
-                            mma_tf32(dacc, ahi + kk * 8, dh, id, (first_chunk && kk == 0) ? 0u : 1u);
-                            mma_tf32(dacc, ahi + kk * 8, dl, id, 1u);
-                            mma_tf32(dacc, alo + kk * 8, dh, id, 1u);
-                        }
+                        const uint32_t ah = tmem + 256u + (uint32_t)(slot * 128 + t * 64) + kk * 8;
+                        const unsigned long long o = 2ull * kk;
+                        mma_tf32(dacc, ah, dh + o, id, (first_chunk && kk == 0) ? 0u : 1u);
+                        mma_tf32(dacc, ah, dl + o, id, 1u);
+                        mma_tf32(dacc, ah + 32, dh + o, id, 1u);
                     }
                     first_chunk = false;
                     mma_commit(bar(TEMPTY + slot));
