@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one split-TF32 collision over one history point at N "
+                         "with a two-unit workspace (the small case for ncu captures) and exit")
     return ap.parse_args()
 
 
@@ -142,6 +145,38 @@ def oracle_unit_sample(N, nP, seed=0):
     return dt
 
 
+def profile_case(a):
+    """One split-TF32 collision over one history point (two units) at N: each
+    stage kernel launches once on a batch of two units."""
+    import gkba_inputs as gi
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as P
+    N = a.N
+    s = gi.system(N, a.nP, seed=0)
+    rho, T = gi.history(N, 2, a.dt, seed=0)
+    per_unit = 2 * 2 * (((N + 15) // 16) * 16) ** 4 * 4
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], a.dt, precision="tf32",
+                    workspace_bytes=int(2.4 * per_unit) + (64 << 20))
+    I = ctx.collision(rho[:1], T[:1], np.array([a.dt]))
+    ctx.close()
+    print(json.dumps({"profile_case": f"N={N}, 2 units", "max_abs_I": float(np.abs(I).max())}))
+
+
+def captured_traffic(kernel, units_per_launch):
+    """DRAM bytes per launch of the kernel class `kernel`, scaled by units from
+    a committed ncu summary line 'dram_bytes_per_unit[<class>]: <bytes>' under
+    profiles/ (kernels whose traffic is proportional to the units), or None."""
+    import glob
+    import re
+    pat = re.compile(r"dram_bytes_per_unit\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+]+)")
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        m = pat.search(open(f).read())
+        if m:
+            return float(m.group(1)) * units_per_launch, os.path.basename(f)
+    return None, None
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -177,6 +212,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.profile_case:
+        profile_case(a)
         return
 
     import torch
@@ -237,12 +275,16 @@ def main():
     dom = max(stage, key=lambda k: stage[k]["ms"])
     d = stage[dom]
     achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    units_per_launch = units / d["launches"]  # (t_k, component) units per launch of dom
+    traffic, traffic_src = captured_traffic(dom, units_per_launch)
     roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": tf32_peak,
             "unit": "TFLOP/s", "frac": achieved / tf32_peak,
             "executed_frac": 3.0 * achieved / tf32_peak,
             "peak_note": f"TF32 = bf16 sustained ({pk['src']}) x 1.1/2.25; executed_frac counts "
                          "the 3 TF32 products per algorithmic product",
-            "traffic": None,
+            "traffic": traffic, "traffic_unit": "bytes per launch",
+            "traffic_source": traffic_src,
+            "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
             "ms_per_launch": d["ms"] / d["launches"], "launches": d["launches"],
             "share": d["ms"] / sum(v["ms"] for v in stage.values()),
             "stages": {k: {"ms": v["ms"], "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9,

@@ -371,6 +371,20 @@ __global__ void k_gkba_units(int N, int nk, int k0, int L, double dt, const doub
 // a fixed summation order (deterministic): pass 1 sums z-range zc of each
 // element into tmp[zc], pass 2 adds the z-ranges in order.  Partials are FP64
 // (FP64 path) or FP32 (tensor-core path); all sums are FP64.
+// Compensated (Kahan) running sum in the partials' own precision: the error
+// stays at a few ulps of the sum whatever the number of terms, and FP32 adds
+// run at full rate (GB300's FP64 rate is low).
+template <typename TP>
+struct KahanSum {
+    TP s = 0, c = 0;
+    __device__ __forceinline__ void add(TP x) {
+        const TP y = x - c;
+        const TP t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
 template <typename TP>
 __global__ void k_reduce_partials_p1(int N, int Np, int nb, int nz, int zper, long long zstride,
                                      long long Rld, const TP* __restrict__ part,
@@ -384,24 +398,25 @@ __global__ void k_reduce_partials_p1(int N, int Np, int nb, int nz, int zper, lo
     const int i = rr / N, j = rr % N;
     const long long r_re = (long long)u * 2 * Np + j, r_im = r_re + Np;
     const int z0 = zc * zper, z1 = min(nz, z0 + zper);
-    double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
+    KahanSum<TP> re[2], im[2];
     const TP* base = part + (long long)i * Rld;
     int z = z0;
-    for (; z + 4 <= z1; z += 4) {
+    for (; z + 2 <= z1; z += 2) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
             const TP* pz = base + (long long)(z + q) * zstride;
-            re[q] += (double)pz[r_re];
-            im[q] += (double)pz[r_im];
+            re[q].add(pz[r_re]);
+            im[q].add(pz[r_im]);
         }
     }
-    for (; z < z1; ++z) {
+    if (z < z1) {
         const TP* pz = base + (long long)z * zstride;
-        re[0] += (double)pz[r_re];
-        im[0] += (double)pz[r_im];
+        re[0].add(pz[r_re]);
+        im[0].add(pz[r_im]);
     }
-    tmp[(long long)zc * NN * nb + e] =
-        make_double2((re[0] + re[1]) + (re[2] + re[3]), (im[0] + im[1]) + (im[2] + im[3]));
+    const double sre = ((double)re[0].s - (double)re[0].c) + ((double)re[1].s - (double)re[1].c);
+    const double sim = ((double)im[0].s - (double)im[0].c) + ((double)im[1].s - (double)im[1].c);
+    tmp[(long long)zc * NN * nb + e] = make_double2(sre, sim);
 }
 
 __global__ void k_reduce_partials_p2(long long n, int nzc, const double2* __restrict__ tmp,
