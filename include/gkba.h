@@ -59,14 +59,19 @@ typedef enum {
 
 typedef enum {
     GKBA_FP64 = 0,       /* every contraction in FP64 on the CUDA cores */
-    GKBA_SPLIT_TF32 = 1  /* contractions on tcgen05 tensor cores: FP32 data,
+    GKBA_SPLIT_TF32 = 1, /* contractions on tcgen05 tensor cores: FP32 data,
                             3 TF32 products (hi*hi + hi*lo + lo*hi), FP32
                             accumulation inside a K-chunk, FP64 across chunks;
                             P/Q, T recursion, I history sum and rho update stay FP64 */
+    GKBA_SPLIT_TF32_ACC = 2 /* as GKBA_SPLIT_TF32 with the correction products
+                            accumulated apart from hi*hi and 64-long FP32 chunks in
+                            the last contraction: about half the error of
+                            GKBA_SPLIT_TF32 (tensor-core accumulation truncates),
+                            about 25% slower */
 } gkba_precision;
 
 typedef struct {
-    int N;             /* basis size, 1 <= N <= 128 (GKBA_SPLIT_TF32: N <= 96) */
+    int N;             /* basis size, 1 <= N <= 128 (tensor-core modes: N <= 96) */
     double dt;         /* time step delta (> 0) */
     int max_steps;     /* history capacity: t_0 .. t_{max_steps} (>= 0) */
     int precision;     /* gkba_precision */
@@ -78,7 +83,8 @@ typedef struct {
                           (see gkba_get_stats) */
     int s4_kchunk;     /* GKBA_SPLIT_TF32: length of the FP32 partial sums of the
                           last contraction (K = N^3) before they are added in
-                          FP64; a multiple of 32, 0 = default 512.  Shorter chunks
+                          FP64; a multiple of 32, 0 = default (512 for
+                          GKBA_SPLIT_TF32, 64 for GKBA_SPLIT_TF32_ACC).  Shorter chunks
                           bound the tensor-core accumulation error, longer ones
                           write fewer partials. */
 } gkba_config;

@@ -660,7 +660,7 @@ gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstrid
     const long long NN = (long long)c->N * c->N;
     const int nzc = nz < kReduceSplit ? nz : kReduceSplit;
     const int zper = (nz + nzc - 1) / nzc;
-    const int Np = c->prec == GKBA_SPLIT_TF32 ? c->Np : c->N;
+    const int Np = tensor_core_path(c) ? c->Np : c->N;
     dim3 g1(grid1(nb * NN, 256), nzc);
     auto t = launch_begin(c, K_RED, 0.0, 0.0);
     if (fp32)

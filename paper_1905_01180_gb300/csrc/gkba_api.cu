@@ -98,7 +98,7 @@ struct Carver {
 gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const long long N = c->N, NN = N * N;
     want_units = std::max(2, want_units + (want_units & 1));
-    const bool tc = c->prec == GKBA_SPLIT_TF32;
+    const bool tc = tensor_core_path(c);
     const long long Np = c->Np;
     const double x_bytes = tc ? 2.0 * Np * Np * Np * Np * 4 : 2.0 * NN * NN * 8;
     const double form_bytes = tc ? 4.0 * 2 * Np * Np * 4 : (2.0 * NN + 4.0 * NN) * 8;
@@ -128,7 +128,10 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
         c->ws_bytes = 0;
     }
     Carver cv;
-    const size_t oX13 = cv.take((size_t)(x_bytes * ub));
+    // the last stage's K-blocked X3 pads the batch's 2 Np ub rows to 256
+    const double x3_blocked = tc ? (double)Np * Np * Np * (((2.0 * Np * ub + 255) / 256) * 256) * 4 : 0.0;
+    const size_t x13_bytes = (size_t)std::max(x_bytes * ub, std::floor(x3_blocked));
+    const size_t oX13 = cv.take(x13_bytes);
     const size_t oX2 = cv.take((size_t)(x_bytes * ub));
     size_t part_bytes;
     if (tc) part_bytes = tf32_part_bytes((int)Np, ub, c->s4_kchunk);
@@ -156,6 +159,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     c->ub = ub;
     c->ub_cap = ub;
     c->X13 = b + oX13;
+    c->x13_bytes = x13_bytes;
     c->X2 = b + oX2;
     c->part = b + oPart;
     c->part_bytes = part_bytes;
@@ -184,7 +188,7 @@ gkba_status ensure_stage(gkba_ctx* c, size_t bytes) {
 }
 
 static gkba_status contract(gkba_ctx* c, int nb) {
-    if (c->prec == GKBA_SPLIT_TF32) return contract_batch_tf32(c, nb);
+    if (tensor_core_path(c)) return contract_batch_tf32(c, nb);
     return contract_batch_fp64(c, nb);
 }
 
@@ -334,10 +338,11 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     if (cfg->s4_kchunk < 0 || cfg->s4_kchunk % 32 != 0)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: s4_kchunk=%d must be a non-negative multiple of 32",
                     cfg->s4_kchunk);
-    if (cfg->precision != GKBA_FP64 && cfg->precision != GKBA_SPLIT_TF32)
+    if (cfg->precision != GKBA_FP64 && cfg->precision != GKBA_SPLIT_TF32 &&
+        cfg->precision != GKBA_SPLIT_TF32_ACC)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown precision %d", cfg->precision);
     const int Np = ((N + 15) / 16) * 16;
-    if (cfg->precision == GKBA_SPLIT_TF32 && Np > 96)
+    if (cfg->precision != GKBA_FP64 && Np > 96)
         return fail(nullptr, GKBA_EINVAL,
                     "gkba_init: the split-TF32 path supports N <= 96 (N=%d)", N);
     const size_t NN = (size_t)N * N, N4 = NN * NN;
@@ -375,7 +380,8 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     c->prec = cfg->precision;
     c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)16 << 30);
     c->timing = cfg->timing != 0;
-    c->s4_kchunk = cfg->s4_kchunk > 0 ? cfg->s4_kchunk : 512;
+    c->s4_kchunk = cfg->s4_kchunk > 0 ? cfg->s4_kchunk
+                                       : (cfg->precision == GKBA_SPLIT_TF32_ACC ? 64 : 512);
     c->device = -1;
     auto bail = [&](gkba_status st) {
         {
@@ -405,7 +411,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         return bail(GKBA_ECUDA);
     }
     c->num_sms = prop.multiProcessorCount;
-    if (c->prec == GKBA_SPLIT_TF32 && !(prop.major == 10 && prop.minor == 3)) {
+    if (tensor_core_path(c) && !(prop.major == 10 && prop.minor == 3)) {
         fail(c, GKBA_EUNSUPPORTED, "gkba_init: split-TF32 path needs an sm_103 GPU (found sm_%d%d)",
              prop.major, prop.minor);
         return bail(GKBA_EUNSUPPORTED);
@@ -474,7 +480,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     }
     if ((st = set_identity(c, c->T_a, 1)) != GKBA_OK) return bail(st);
     if ((st = fp64_prepare_model(c)) != GKBA_OK) return bail(st);
-    if (c->prec == GKBA_SPLIT_TF32 && (st = tf32_prepare_model(c)) != GKBA_OK) return bail(st);
+    if (tensor_core_path(c) && (st = tf32_prepare_model(c)) != GKBA_OK) return bail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         fail(c, GKBA_ECUDA, "gkba_init: %s", cudaGetErrorString(cudaGetLastError()));
         return bail(GKBA_ECUDA);

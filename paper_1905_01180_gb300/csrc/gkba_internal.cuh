@@ -98,6 +98,7 @@ struct gkba_ctx {
     int ub_cap = 0;              // units the workspace was sized for
     // sub-buffers inside ws
     void* X13 = nullptr;
+    size_t x13_bytes = 0;
     void* X2 = nullptr;
     void* part = nullptr;
     size_t part_bytes = 0;
@@ -130,6 +131,9 @@ namespace gkba {
 
 // Record an error message on the context and return the status.
 gkba_status fail(gkba_ctx* c, gkba_status st, const char* fmt, ...);
+
+// The contraction runs on the tensor cores (split-TF32 modes) or in FP64.
+inline bool tensor_core_path(const gkba_ctx* c) { return c->prec != GKBA_FP64; }
 
 // Check a CUDA runtime call; on failure record it and return GKBA_ECUDA.
 #define GKBA_CUDA(ctx, call)                                                              \
@@ -165,6 +169,7 @@ gkba_status harvest_timing(gkba_ctx* c);
 struct StageMap {
     long long SA, SB, SX, SC, SY;
     int Dx, Db, Dy;
+    long long XB = 0;  // nonzero: x enters as (x / 32) * XB + x % 32 (K-blocked layout)
 };
 
 // D[z][row][col] = sum_k A[z][row*lda + k] * B[z][col*ldb + k] (FP64, K-major).

@@ -215,12 +215,13 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n, int negB) {
 }
 
 // TF32 split of the streamed A operand, selected at compile time:
-//   0: hi = rna(x), lo = rna(x - hi)           (|error| <= 2^-23 |x| per element)
+//   0: hi = rna(x), lo = rna(x - hi)           (|error| <= 2^-23 |x| per element,
+//      unbiased: lo is exact in TF32, so no truncation toward zero remains)
 //   1: hi = x truncated to TF32, lo = rna(x - hi)
 //   2: hi = x truncated to TF32, lo = x - hi    (the MMA keeps lo's leading
 //      11 bits: |error| <= 2^-21 |x|), two full-rate integer/FP ops per element
 #ifndef GKBA_SPLIT_MODE
-#define GKBA_SPLIT_MODE 2
+#define GKBA_SPLIT_MODE 0
 #endif
 
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
@@ -271,6 +272,11 @@ struct StageParams {
 constexpr int kStageAStages = 4;
 constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-11 epilogue
 
+// SPLIT_ACC: hi*hi accumulates into one TMEM accumulator and the two
+// correction products into a second one, summed in the epilogue.  The main
+// accumulator then sees a third of the truncating accumulator additions, at
+// the price of a single (not double-buffered) accumulator pair.
+template <bool SPLIT_ACC>
 __global__ void __launch_bounds__(kStageThreads, 1)
     k_tc_stage(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                const __grid_constant__ CUtensorMap tmBlo, const StageParams p) {
@@ -396,11 +402,12 @@ __global__ void __launch_bounds__(kStageThreads, 1)
                     cur_u = u;
                     tc_fence_after();
                 }
-                const int ab = (int)(tile_i & 1);
-                const uint32_t abph = (uint32_t)((tile_i >> 1) & 1);
+                const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
+                const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
                 if (!mbar_wait(bar(ACCE + ab), abph ^ 1, abort_flag, p.err, 4)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dacc = tmem + (uint32_t)(ab * 256);
+                const uint32_t dcor = SPLIT_ACC ? tmem + 256u : dacc;
                 for (int c = 0; c < chunks_per_tile; ++c, ++it) {
                     const int pl = c / p.kch, kc = c % p.kch;
                     const int slot = (int)(it & 1);
@@ -420,8 +427,8 @@ __global__ void __launch_bounds__(kStageThreads, 1)
                             const uint32_t ah = ahi + kk * 8, al = ah + 32;
                             const unsigned long long o = 2ull * kk;
                             mma_tf32(dacc, ah, dh + o, id_full, (c | kk) ? 1u : 0u);
-                            mma_tf32(dacc, ah, dl + o, id_full, 1u);
-                            mma_tf32(dacc, al, dh + o, id_full, 1u);
+                            mma_tf32(dcor, ah, dl + o, id_full, (SPLIT_ACC && !(c | kk)) ? 0u : 1u);
+                            mma_tf32(dcor, al, dh + o, id_full, 1u);
                         }
                     } else {
                         // D[:, 0:Np] += A_im * (-Im G);  D[:, Np:2Np] += A_im * Re G
@@ -431,11 +438,11 @@ __global__ void __launch_bounds__(kStageThreads, 1)
                             const uint32_t ah = ahi + kk * 8, al = ah + 32;
                             const unsigned long long o = 2ull * kk;
                             mma_tf32(dacc, ah, dh + im + o, id_half_neg, 1u);
-                            mma_tf32(dacc, ah, dl + im + o, id_half_neg, 1u);
-                            mma_tf32(dacc, al, dh + im + o, id_half_neg, 1u);
+                            mma_tf32(dcor, ah, dl + im + o, id_half_neg, 1u);
+                            mma_tf32(dcor, al, dh + im + o, id_half_neg, 1u);
                             mma_tf32(dacc + Np, ah, dh + o, id_half, 1u);
-                            mma_tf32(dacc + Np, ah, dl + o, id_half, 1u);
-                            mma_tf32(dacc + Np, al, dh + o, id_half, 1u);
+                            mma_tf32(dcor + Np, ah, dl + o, id_half, 1u);
+                            mma_tf32(dcor + Np, al, dh + o, id_half, 1u);
                         }
                     }
                     mma_commit(bar(TEMPTY + slot));
@@ -489,20 +496,30 @@ __global__ void __launch_bounds__(kStageThreads, 1)
         bool ok = true;
         for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
             const int u = (int)(t / p.mtiles), mt = (int)(t % p.mtiles);
-            const int ab = (int)(tile_i & 1);
-            const uint32_t abph = (uint32_t)((tile_i >> 1) & 1);
+            const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
+            const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
             if (!warp_wait(bar(ACCF + ab), abph, abort_flag, p.err, 8)) { ok = false; break; }
             tc_fence_after();
             const long long row = (long long)mt * kBM + rloc;
             const bool valid = row < p.M;
             const long long x = row % p.map.Dx;
             const long long rb = row / p.map.Dx;
+            const long long xo = p.map.XB ? (x >> 5) * p.map.XB + (x & 31) : x * p.map.SX;
             float* o = p.out + (long long)u * p.out_unit + (rb / p.map.Db) * p.map.SA +
-                       (rb % p.map.Db) * p.map.SB + x * p.map.SX;
+                       (rb % p.map.Db) * p.map.SB + xo;
             for (int cc = 0; cc < ncc; ++cc) {
                 uint32_t v[32];
                 tmem_ld32(lane_base + (uint32_t)(ab * 256 + cc * 32), v);
-                tmem_wait_ld();
+                if (SPLIT_ACC) {
+                    uint32_t w[32];
+                    tmem_ld32(lane_base + (uint32_t)(256 + cc * 32), w);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+                } else {
+                    tmem_wait_ld();
+                }
                 if (valid) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -539,6 +556,7 @@ struct FinalParams {
     float* part;   // [ks][i][Rld]
     long long Rld;
     int* err;
+    int blocked;   // A is K-blocked: [K/32][Rld rows][32] (3-D map) instead of [rows][K]
 };
 
 constexpr int kFinStages = 3;
@@ -606,8 +624,13 @@ __global__ void __launch_bounds__(kFinThreads, 1)
                     const uint32_t ph = (uint32_t)((it / kFinStages) & 1);
                     if (!mbar_wait(bar(EMPTY + s), ph ^ 1, abort_flag, p.err, 11)) { ok = false; break; }
                     mbar_expect_tx(bar(FULL + s), stage_bytes);
-                    tma_2d(smem_u32(stA(s, 0)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM);
-                    tma_2d(smem_u32(stA(s, 1)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM + kBM);
+                    if (p.blocked) {
+                        tma_3d(smem_u32(stA(s, 0)), &tmA, bar(FULL + s), 0, g * 2 * kBM, (int)(k >> 5));
+                        tma_3d(smem_u32(stA(s, 1)), &tmA, bar(FULL + s), 0, g * 2 * kBM + kBM, (int)(k >> 5));
+                    } else {
+                        tma_2d(smem_u32(stA(s, 0)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM);
+                        tma_2d(smem_u32(stA(s, 1)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM + kBM);
+                    }
                     tma_2d(smem_u32(stBhi(s)), &tmBhi, bar(FULL + s), (int)k, 0);
                     tma_2d(smem_u32(stBlo(s)), &tmBlo, bar(FULL + s), (int)k, 0);
                 }
@@ -863,7 +886,9 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
     t = launch_begin(c, K_PREP, 0.0, 0.0);
     k_build_vK32<<<grid1(Np4, 256), 256, 0, c->stream>>>(c->N, c->Np, c->v, c->vKhi, c->vKlo);
     GKBA_TRY(launch_end(c, t));
-    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)stage_smem_bytes(c->Np)));
+    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)stage_smem_bytes(c->Np)));
     GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)final_smem_bytes(c->Np)));
@@ -882,7 +907,7 @@ gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG, con
                         long long sGb, int) {
     (void)sG;
     (void)sGb;
-    if (c->prec == GKBA_SPLIT_TF32) return build_forms_tf32(c, nb, G, Gb);
+    if (tensor_core_path(c)) return build_forms_tf32(c, nb, G, Gb);
     return build_forms_fp64(c, nb, G, Gb);
 }
 
@@ -928,9 +953,14 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         GKBA_TRY(make_map(c, &mGh, Gshi, 3, d, s, b));
         GKBA_TRY(make_map(c, &mGl, Gslo, 3, d, s, b));
     }
-    const long long rows = 2LL * Np * nb;
-    {
-        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)rows};
+    if ((Np % 32) == 0) {
+        const long long Rl = ((2LL * Np * nb + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
+        cuuint64_t d[3] = {32, (cuuint64_t)Rl, (cuuint64_t)(N3 / 32)};
+        cuuint64_t s[2] = {32 * 4, (cuuint64_t)(Rl * 32 * 4)};
+        cuuint32_t b[3] = {kKC, kBM, 1};
+        GKBA_TRY(make_map(c, &mAf, X13, 3, d, s, b));
+    } else {
+        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)(2LL * Np * nb)};
         cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
         cuuint32_t b[2] = {kKC, kBM};
         GKBA_TRY(make_map(c, &mAf, X13, 2, d, s, b));
@@ -944,6 +974,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     }
 
     const size_t ssm = stage_smem_bytes(Np);
+    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_stage<true> : k_tc_stage<false>;
     const long long total = (long long)nb * mtiles;
     const int grid = (int)(total < c->num_sms ? total : c->num_sms);
     StageParams sp{};
@@ -961,7 +992,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     sp.map = StageMap{2 * N3, 2 * Np, 1, Np, 2 * N2, Np, Np, Np};
     {
         auto t = launch_begin(c, K_W1, fl_cr * nb, 4.0 * (N4r + 2 * N4r * nb));
-        k_tc_stage<<<grid, kStageThreads, ssm, c->stream>>>(mA1, mB1h, mB1l, sp);
+        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA1, mB1h, mB1l, sp);
         GKBA_TRY(launch_end(c, t));
     }
     // S2: rows (j,r,m), K (c,q), cols (c',p) -> X2[j][r][p][c'][m]
@@ -971,15 +1002,25 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     sp.map = StageMap{2 * N3, 2 * N2, 1, Np, 2 * Np, Np, Np, Np};
     {
         auto t = launch_begin(c, K_W2, fl_cc * nb, 4.0 * 4 * N4r * nb);
-        k_tc_stage<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in1, mGh, mGl, sp);
+        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in1, mGh, mGl, sp);
         GKBA_TRY(launch_end(c, t));
     }
-    // S3: rows (j,r,p), K (c,m), cols (c',n) -> X3[c'][j][n][r][p]
+    // S3: rows (j,r,p), K (c,m), cols (c',n) -> X3 with rows (u,c',j) and K (n,r,p):
+    // K-blocked X3[K/32][Rld][32] when Np % 32 == 0 (one contiguous 16 KB block
+    // per 128 x 32 tile of the last stage), else X3[u][c'][j][n][r][p].
+    const long long rows = 2LL * Np * nb;
+    const long long Rld = ((rows + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
+    const bool blocked = (Np % 32) == 0;
     sp.out = X13;
-    sp.map = StageMap{N3, Np, 1, N4, N2, Np, Np, Np};
+    if (blocked) {
+        sp.map = StageMap{32, Np * Rld, 0, 32 * Np, N2 * Rld, Np, Np, Np, 32 * Rld};
+        sp.out_unit = 2LL * Np * 32;
+    } else {
+        sp.map = StageMap{N3, Np, 1, N4, N2, Np, Np, Np};
+    }
     {
         auto t = launch_begin(c, K_W3, fl_cc * nb, 4.0 * 4 * N4r * nb);
-        k_tc_stage<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in2, mGh, mGl, sp);
+        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in2, mGh, mGl, sp);
         GKBA_TRY(launch_end(c, t));
     }
     // S4: split-K over (n,r,p)
@@ -991,8 +1032,11 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     fp.rows = rows;
     fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
     fp.Rld = (long long)fp.ngroups * 2 * kBM;
+    fp.blocked = blocked ? 1 : 0;
     fp.part = (float*)c->part;
     fp.err = err;
+    if (blocked && (size_t)(N3 * Rld * 4) > c->x13_bytes)
+        return fail(c, GKBA_ESTATE, "X3 buffer too small for the K-blocked layout");
     if ((size_t)fp.nks * Np * fp.Rld * 4 > c->part_bytes)
         return fail(c, GKBA_ESTATE, "partial buffer too small");
     {

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgkba.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC, EUNSUPPORTED = range(8)
-FP64, SPLIT_TF32 = 0, 1
+FP64, SPLIT_TF32, SPLIT_TF32_ACC = 0, 1, 2
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT",
            6: "ENUMERIC", 7: "EUNSUPPORTED"}
 
@@ -117,7 +117,8 @@ class Context:
             ph = _host(h, np.complex128); pv = _host(v, np.float64)
             pd = _host(d, np.complex128); pr = _host(rho0, np.complex128)
         keep += [ph, pv, pd, pr]
-        prec = {"fp64": FP64, "tf32": SPLIT_TF32, FP64: FP64, SPLIT_TF32: SPLIT_TF32}[precision]
+        prec = {"fp64": FP64, "tf32": SPLIT_TF32, "tf32acc": SPLIT_TF32_ACC, FP64: FP64,
+                SPLIT_TF32: SPLIT_TF32, SPLIT_TF32_ACC: SPLIT_TF32_ACC}[precision]
         cfg = Config(N=N, dt=float(dt), max_steps=int(max_steps), precision=prec,
                      cuda_stream=stream, workspace_bytes=int(workspace_bytes), device=int(device),
                      timing=1 if timing else 0, s4_kchunk=int(s4_kchunk))
