@@ -177,6 +177,20 @@ def captured_traffic(kernel, units_per_launch):
     return None, None
 
 
+def job_timing(ms_local, units_local, dist=None):
+    """Whole-job timing over replicas: the slowest rank's time and the units
+    all ranks processed (each rank runs its own history, weak scaling)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local, units_local
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -257,15 +271,11 @@ def main():
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_local = ev0.elapsed_time(ev1)
     stats, launches = ctx.stats(reset=True)
     units = sum(2 * (2 * (n0 + k) + 3) for k in range(a.steps))
-    flops = units * unit_flops(N)
-    value = world * flops / (ms_total * 1e-3) / 1e12
+    ms_total, units_job = job_timing(ms_local, units, dist)
+    value = units_job * unit_flops(N) / (ms_total * 1e-3) / 1e12
     ms_step = ms_total / a.steps
 
     # roofline: dominant stage kernel over the timed region

@@ -128,14 +128,15 @@ def test_collision_fp64(P, N, L):
     ctx.close()
 
 
-@pytest.mark.parametrize("N,L", [(16, 6), (24, 5), (13, 9)])
-def test_collision_tf32(P, N, L):
-    s, ctx = ctx_for(P, N, seed=N + L, precision="tf32")
+@pytest.mark.parametrize("N,L,precision", [(16, 6, "tf32"), (24, 5, "tf32"), (13, 9, "tf32"),
+                                           (24, 5, "tf32acc"), (40, 3, "tf32acc")])
+def test_collision_tf32(P, N, L, precision):
+    s, ctx = ctx_for(P, N, seed=N + L, precision=precision)
     rho, T = gi.history(N, L, 0.05, seed=L)
     I = ctx.collision(rho, T)
     ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.05))
     e = rel(I, ref)
-    print(f"N={N} L={L} split-TF32 collision rel err {e:.3e}")
+    print(f"N={N} L={L} {precision} collision rel err {e:.3e}")
     assert e < TOL_TC
     ctx.close()
 
@@ -204,25 +205,104 @@ def test_config0_full_run_fp64(P, config0_ref):
     ctx.close()
 
 
-def test_config1_first_steps_fp64_and_tf32(P):
-    # N=24, 32 factors, dt=0.02: FP64 path vs the oracle, and split-TF32 vs FP64
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                    "config1_oracle_100steps.npz")
+
+
+@pytest.fixture(scope="module")
+def config1():
+    # N=24, 32 factors, dt=0.02, the pulse on [0, 10] (written by
+    # tests/golden/make_config1_oracle.py with the oracle only)
+    g = np.load(GOLDEN)
     s = gi.system(24, 32, seed=0)
-    dt, n = 0.02, 12
-    E = gi.field(dt * np.arange(n + 1))
-    ref = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, E)
+    dt = float(g["dt"])
+    E = gi.field(dt * np.arange(1001))
+    return g, s, dt, E
+
+
+def test_config1_fp64_vs_oracle_100_steps(P, config1):
+    g, s, dt, E = config1
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=100)
+    rho_at, I_at, tr = {}, {}, []
+    for k in range(100):
+        rho, I, diag = ctx.step(E[k], E[k + 1])
+        rho_at[k + 1] = rho
+        I_at[k] = I
+        tr.append(diag[0])
+        assert abs(diag[2] - g["energy_corr"][k]) < 1e-10 * max(1.0, abs(g["energy_corr"][k]))
+        assert abs(diag[1] - g["energy_total"][k]) < 1e-10 * max(1.0, abs(g["energy_total"][k]))
+    w_rho = max(rel(rho_at[n], r) for n, r in zip(g["steps"][1:], g["rho"][1:]))
+    w_I = max(rel(I_at[n], i) for n, i in zip(g["steps"][1:-1], g["I"][1:-1]))
+    print(f"config1 100 steps FP64 vs oracle: rho {w_rho:.2e}, I {w_I:.2e}")
+    assert w_rho < TOL64 and w_I < TOL64
+    assert np.abs(np.array(tr) - g["trace"][:100]).max() < 1e-12
+    ctx.close()
+
+
+# split-TF32 rho drifts systematically (the tensor core truncates accumulator
+# additions), so the error grows with the number of steps: the accurate mode
+# keeps it below 1e-5 over the first 100 steps of this configuration; the fast
+# mode's error is stated and bounded at 2.5e-5.
+@pytest.mark.parametrize("precision,bound", [("tf32acc", 1e-5), ("tf32", 2.5e-5)])
+def test_config1_tf32_vs_fp64_100_steps(P, config1, precision, bound):
+    g, s, dt, E = config1
+    n = 100
     c64 = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
-    ctc = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision="tf32")
-    w64 = wtc = 0.0
+    ctc = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=precision)
+    worst = 0.0
     for k in range(n):
         r64, _, _ = c64.step(E[k], E[k + 1])
         rtc, _, _ = ctc.step(E[k], E[k + 1])
-        w64 = max(w64, rel(r64, ref.rho[k + 1]))
-        wtc = max(wtc, rel(rtc, r64))
-    print(f"config1 {n} steps: FP64 vs oracle {w64:.2e}, split-TF32 vs FP64 {wtc:.2e}")
-    assert w64 < TOL64
-    assert wtc < 1e-5
+        worst = max(worst, rel(rtc, r64))
+    print(f"config1 {n} steps: {precision} rho vs FP64 GPU path, max rel err {worst:.2e}")
+    assert worst < bound
     c64.close()
     ctc.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,trace_bound", [("tf32acc", 5e-5), ("tf32", 5e-4)])
+def test_config1_tf32_full_run_invariants(P, config1, precision, trace_bound):
+    # 1000 Heun steps (t in [0, 20]).  Particle number is conserved exactly by
+    # the method (Re Tr I = 0); on the split-TF32 paths its drift measures the
+    # systematic part of the contraction error (the tensor core truncates
+    # accumulator additions): measured 1.7e-5 (accurate mode) and 1.9e-4
+    # (fast mode) after 1000 steps, against 3e-14 on the FP64 path.  rho stays
+    # Hermitian and the correlation energy negative.
+    g, s, dt, E = config1
+    n = 1000
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=precision)
+    tr, ec, herm = [], [], 0.0
+    for k in range(n):
+        rho, I, diag = ctx.step(E[k], E[k + 1])
+        tr.append(diag[0])
+        ec.append(diag[2])
+        herm = max(herm, np.abs(rho - rho.conj().T).max())
+    tr = np.array(tr)
+    print(f"config1 1000 steps {precision}: |Tr rho - 6| {np.abs(tr - 6).max():.2e}, "
+          f"herm {herm:.2e}, E_c end {ec[-1]:.4e}")
+    assert np.abs(tr - 6.0).max() < trace_bound
+    assert herm < 1e-12
+    assert ec[-1] < 0.0
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32acc"])
+def test_config1_field_free_energy_second_order(P, precision):
+    # After a sudden switch-on of the correlations the N=24 model relaxes
+    # strongly (E_c ~ -6); without a field the energy is conserved up to the
+    # Heun step error, which falls faster than dt^2 here: drift ratios on
+    # halving dt were 3.7 and 6.8 (identical on both paths).
+    s = gi.system(24, 32, seed=0)
+    drifts = []
+    for dt in (0.04, 0.02, 0.01):
+        m = int(round(2.0 / dt))
+        ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=m, precision=precision)
+        en = [ctx.step(0.0, 0.0)[2][1] for _ in range(m)]
+        ctx.close()
+        drifts.append(np.abs(np.array(en) - en[0]).max())
+    print(f"{precision} field-free energy drift over t <= 2: {drifts}")
+    assert drifts[0] / drifts[1] > 3.0 and drifts[1] / drifts[2] > 3.0
 
 
 def test_checkpoint_resume_bitwise(P):
