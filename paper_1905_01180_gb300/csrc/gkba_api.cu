@@ -141,7 +141,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     }
     const size_t oPart = cv.take(part_bytes);
     const size_t oB1 = cv.take(tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(2LL * NN * ub * 8));
-    const size_t oG = cv.take(tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(4LL * NN * ub * 8));
+    const size_t oG = cv.take(tc ? (size_t)(2LL * 4 * Np * Np * ub * 4) : (size_t)(4LL * NN * ub * 8));
     const size_t oPQ = cv.take((size_t)(ub * NN * 16));
     const size_t oMb = cv.take((size_t)(ub * NN * 16));
     const size_t oCoef = cv.take((size_t)ub * 8);

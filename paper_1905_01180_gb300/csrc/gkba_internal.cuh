@@ -51,6 +51,7 @@ struct gkba_ctx {
     size_t ws_cap = 0;
     bool timing = false;
     int num_sms = 0;
+    int pair_clusters = 0;  // co-resident 2-CTA clusters of the stage kernel
     int s4_kchunk = 512;
 
     // model on the device

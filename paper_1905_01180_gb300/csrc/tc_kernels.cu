@@ -16,15 +16,18 @@
 //   * B (the small per-unit matrix, or v for S4) is stored pre-split hi/lo;
 //   * each K-step issues hi*hi + hi*lo + lo*hi (3xTF32) into an FP32 TMEM
 //     accumulator; S4 is split over K in chunks (default 512) whose FP32 partial
-//     sums are added in FP64 by the reduction kernel.
-// Complex data is planar: S2/S3 read the (re, im) planes of A as separate
-// K-chunks; the im plane multiplies the [Im G; Re G] halves of B with the
-// instruction descriptor's negate-B bit for -Im A Im G.
+//     sums are added by the reduction kernel.
+// S1-S3 run on CTA pairs (cta_group::2, M = 256): B's rows are split between
+// the two CTAs' shared memory, which leaves room for the complex B' that
+// turns the planar (Re, Im) halves of A into one real K range:
+// [[Re G | -Im G]; [Im G | Re G]].
 //
 // Every mbarrier wait is bounded (globaltimer); on timeout the kernel raises
 // an abort flag, records an error word, drains its in-flight TMA loads and
 // MMAs, frees its tensor memory and returns.
 #include <cuda.h>
+
+#include <cstdlib>
 
 #include "gkba_internal.cuh"
 
@@ -137,6 +140,100 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
                  : "memory");
 }
+// --- CTA-pair (cta_group::2) forms ---
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Shared::cluster address of the same shared variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+// Arrive on an mbarrier of another CTA of the cluster (default .release.cta
+// semantics: what the peer consumes is tensor memory written and completed
+// with tcgen05.wait::st / read with tcgen05.wait::ld before the arrive, or
+// shared memory filled by TMA, so the arrive itself orders the hand-off; a
+// cluster-scope release here made every arrive of the converter a fence that
+// doubled its time per chunk).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+// Bounded wait of the CTA-pair kernel; on timeout it raises this CTA's and the
+// peer CTA's abort flags (peer_abort: shared::cluster address).
+__device__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                             uint32_t peer_abort, int* err, int code) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63u) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > kWaitLimitNs) {
+                *abort_flag = 1;
+                st_cluster_u32(peer_abort, 1u);
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ bool warp_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                             uint32_t peer_abort, int* err, int code) {
+    const bool r = mbar_wait_cl(bar, parity, abort_flag, peer_abort, err, code);
+    return __all_sync(0xffffffffu, r);
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+// D[tmem] (+)= A[tmem] * B[smem desc] over the CTA pair: M = 256 (128 rows per
+// CTA's TMEM), B's N rows split in halves across the two CTAs' shared memory.
+__device__ __forceinline__ void mma_tf32_pair(uint32_t d, uint32_t a, unsigned long long bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Arrive (once the issuing thread's earlier MMAs are done) on the mbarrier at
+// this shared offset in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -213,6 +310,11 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n, int negB) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negB << 14) |
            ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
+// Same for the CTA-pair MMA: M = 256 (two 128-row halves), N = n.
+__host__ __device__ constexpr uint32_t idesc_tf32_pair(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)((2 * kBM) >> 4) << 24);
+}
 
 // TF32 split of the streamed A operand, selected at compile time:
 //   0: hi = rna(x), lo = rna(x - hi)           (|error| <= 2^-23 |x| per element,
@@ -272,43 +374,70 @@ struct StageParams {
 constexpr int kStageAStages = 4;
 constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-11 epilogue
 
-// SPLIT_ACC: hi*hi accumulates into one TMEM accumulator and the two
-// correction products into a second one, summed in the epilogue.  The main
-// accumulator then sees a third of the truncating accumulator additions, at
-// the price of a single (not double-buffered) accumulator pair.
+// ---------------------------------------------------------------------------
+// Stages S1-S3 on CTA pairs (cta_group::2).  A cluster of two CTAs on two SMs
+// computes 256-row tiles: each CTA stages, splits and holds its own 128 rows
+// of A in its tensor memory and its own half of the B rows in shared memory;
+// the even CTA issues every MMA for the pair (M = 256, N = 2 Np), and each
+// CTA's TMEM receives the full 2 Np columns of its 128 rows.
+//
+// With B split by rows the complex stages need no half-width MMAs: B' holds
+//   even CTA (Re output columns):  [ Re G | -Im G ]   over K = (plane, q)
+//   odd CTA  (Im output columns):  [ Im G |  Re G ]
+// so the Re and Im planes of A are two K ranges of one real GEMM of
+// N = 2 Np.  S1 (real A) uses the Re / Im halves of [Re Gb^T; Im Gb^T].
+//
+// Barriers: A pipeline (AFULL/AEMPTY) and B loads (BFULL) are per CTA; the
+// converters and epilogues of both CTAs arrive on the even CTA's TFULL / ACCE
+// (count 8: four warps per CTA); MMA completion is multicast to both CTAs'
+// TEMPTY / ACCF / BEMPTY.  The odd CTA forwards its B completion to the even
+// CTA's BPEER.  Every wait is bounded and a timeout raises both CTAs' abort
+// flags.
+//
+// Tensor memory (512 columns, same address in both CTAs): accumulators at
+// columns 0 and 256 (2 Np <= 192 each, double-buffered over tiles), A slots
+// (TF32 hi in 32 columns, lo in the next 32) at 192 and 448.  SPLIT_ACC:
+// hi*hi accumulates at column 0 and the two correction products at 256 (a
+// single, not double-buffered, pair), summed in the epilogue; the main
+// accumulator then sees a third of the truncating accumulator additions.
+// ---------------------------------------------------------------------------
 template <bool SPLIT_ACC>
-__global__ void __launch_bounds__(kStageThreads, 1)
-    k_tc_stage(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-               const __grid_constant__ CUtensorMap tmBlo, const StageParams p) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
+    k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+              const __grid_constant__ CUtensorMap tmBlo, const StageParams p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int Np = p.Np;
-    const uint32_t chunkB = (uint32_t)(2 * Np * 128);  // one K-chunk of the 2Np-row B operand
+    const int nchunk = p.planes * p.kch;                // K-chunks per tile
+    const uint32_t chunkB = (uint32_t)(Np * 128);       // one K-chunk of this CTA's Np B rows
     uint8_t* sBhi = smem;
-    uint8_t* sBlo = sBhi + p.kch * chunkB;
-    uint8_t* sA = sBlo + p.kch * chunkB;
+    uint8_t* sBlo = sBhi + nchunk * chunkB;
+    uint8_t* sA = sBlo + nchunk * chunkB;
     uint64_t* bars = (uint64_t*)(sA + kStageAStages * kTileBytes);
-    // barrier indices
-    constexpr int BFULL = 0, BEMPTY = 1, AFULL = 2, AEMPTY = AFULL + kStageAStages,
+    constexpr int BFULL = 0, BPEER = 1, BEMPTY = 2, AFULL = 3, AEMPTY = AFULL + kStageAStages,
                   TFULL = AEMPTY + kStageAStages, TEMPTY = TFULL + 2, ACCF = TEMPTY + 2,
                   ACCE = ACCF + 2, DRAIN = ACCE + 2, NBARS = DRAIN + 1;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     auto bar = [&](int i) { return smem_u32(bars + i); };
 
+    const uint32_t rank = cluster_rank();
+    const uint32_t peer_abort = mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
+    auto bar0 = [&](int i) { return mapa_rank(bar(i), 0); };  // the even CTA's barrier
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         mbar_init(bar(BFULL), 1);
+        mbar_init(bar(BPEER), 1);
         mbar_init(bar(BEMPTY), 1);
         for (int s = 0; s < kStageAStages; ++s) {
             mbar_init(bar(AFULL + s), 1);
             mbar_init(bar(AEMPTY + s), 4);
         }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(bar(TFULL + s), 4);
+            mbar_init(bar(TFULL + s), 8);
             mbar_init(bar(TEMPTY + s), 1);
             mbar_init(bar(ACCF + s), 1);
-            mbar_init(bar(ACCE + s), 4);
+            mbar_init(bar(ACCE + s), 8);
         }
         mbar_init(bar(DRAIN), 1);
         *abort_flag = 0;
@@ -320,54 +449,58 @@ __global__ void __launch_bounds__(kStageThreads, 1)
         prefetch_tmap(&tmBlo);
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), 512);
-        tmem_relinquish();
+        tmem_alloc_pair(smem_u32(tmem_slot), 512);
+        tmem_relinquish_pair();
+        tc_fence_before();
     }
     __syncthreads();
+    cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const long long total = (long long)p.units * p.mtiles;
-    const long long t0 = total * blockIdx.x / gridDim.x;
-    const long long t1 = total * (blockIdx.x + 1) / gridDim.x;
-    const int chunks_per_tile = p.planes * p.kch;
+    const long long ipu = p.mtiles / 2;  // 256-row tiles per unit
+    const long long total = (long long)p.units * ipu;
+    const long long ncl = cluster_count_x(), cid = cluster_id_x();
+    const long long t0 = total * cid / ncl;
+    const long long t1 = total * (cid + 1) / ncl;
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer ----------------
+            // ---------------- TMA producer (both CTAs) ----------------
             int cur_u = -1;
             uint32_t bph = 0;
             long long it = 0;
-            bool ok = true;
-            bool loaded_b = false;
+            bool ok = true, loaded_b = false;
             for (long long t = t0; t < t1 && ok; ++t) {
-                const int u = (int)(t / p.mtiles), mt = (int)(t % p.mtiles);
+                const int u = (int)(t / ipu);
+                const long long row0 = (t % ipu) * (2 * kBM) + (long long)rank * kBM;
                 if (u != cur_u) {
                     if (cur_u >= 0) {
-                        if (!mbar_wait(bar(BEMPTY), bph, abort_flag, p.err, 1)) { ok = false; break; }
+                        if (!mbar_wait_cl(bar(BEMPTY), bph, abort_flag, peer_abort, p.err, 1)) { ok = false; break; }
                         bph ^= 1;
                     }
-                    mbar_expect_tx(bar(BFULL), 2u * p.kch * chunkB);
-                    for (int kc = 0; kc < p.kch; ++kc) {
-                        tma_3d(smem_u32(sBhi + kc * chunkB), &tmBhi, bar(BFULL), kc * kKC, 0, u);
-                        tma_3d(smem_u32(sBlo + kc * chunkB), &tmBlo, bar(BFULL), kc * kKC, 0, u);
+                    mbar_expect_tx(bar(BFULL), 2u * nchunk * chunkB);
+                    for (int c = 0; c < nchunk; ++c) {
+                        const int pl = c / p.kch, kc = c % p.kch;
+                        const int y = (pl * 2 + (int)rank) * Np;
+                        tma_3d(smem_u32(sBhi + c * chunkB), &tmBhi, bar(BFULL), kc * kKC, y, u);
+                        tma_3d(smem_u32(sBlo + c * chunkB), &tmBlo, bar(BFULL), kc * kKC, y, u);
                     }
                     loaded_b = true;
                     cur_u = u;
                 }
-                for (int c = 0; c < chunks_per_tile && ok; ++c, ++it) {
+                for (int c = 0; c < nchunk && ok; ++c, ++it) {
                     const int pl = c / p.kch, kc = c % p.kch;
                     const int s = (int)(it % kStageAStages);
                     const uint32_t ph = (uint32_t)((it / kStageAStages) & 1);
-                    if (!mbar_wait(bar(AEMPTY + s), ph ^ 1, abort_flag, p.err, 2)) { ok = false; break; }
+                    if (!mbar_wait_cl(bar(AEMPTY + s), ph ^ 1, abort_flag, peer_abort, p.err, 2)) { ok = false; break; }
                     mbar_expect_tx(bar(AFULL + s), kTileBytes);
                     const uint32_t dst = smem_u32(sA + s * kTileBytes);
-                    if (p.a_unit) tma_4d(dst, &tmA, bar(AFULL + s), kc * kKC, pl, mt * kBM, u);
-                    else tma_2d(dst, &tmA, bar(AFULL + s), kc * kKC, mt * kBM);
+                    if (p.a_unit) tma_4d(dst, &tmA, bar(AFULL + s), kc * kKC, pl, (int)row0, u);
+                    else tma_2d(dst, &tmA, bar(AFULL + s), kc * kKC, (int)row0);
                 }
             }
             if (*abort_flag) {
-                // drain: wait for the last load issued into every stage and for B
                 for (int s = 0; s < kStageAStages; ++s) {
                     if (it > s) {
                         const long long last = it - 1 - ((it - 1 - s) % kStageAStages);
@@ -383,99 +516,99 @@ __global__ void __launch_bounds__(kStageThreads, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer ----------------
-            const uint32_t id_full = idesc_tf32(2 * Np, 0);
-            const uint32_t id_half = idesc_tf32(Np, 0);
-            const uint32_t id_half_neg = idesc_tf32(Np, 1);
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer (even CTA, for the pair) ----------------
+            const uint32_t id = idesc_tf32_pair(2 * Np);
             const unsigned long long dBhi0 = desc_sw128(smem_u32(sBhi));
             const unsigned long long dBlo0 = desc_sw128(smem_u32(sBlo));
             int cur_u = -1;
             uint32_t bfph = 0;
             long long it = 0, tile_i = 0;
-            bool ok = true;
+            bool ok = true, issued = false;
             for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
-                const int u = (int)(t / p.mtiles);
+                const int u = (int)(t / ipu);
                 if (u != cur_u) {
-                    if (!mbar_wait(bar(BFULL), bfph, abort_flag, p.err, 3)) { ok = false; break; }
+                    if (!mbar_wait_cl(bar(BFULL), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
+                    if (!mbar_wait_cl(bar(BPEER), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
                     bfph ^= 1;
                     cur_u = u;
                     tc_fence_after();
                 }
                 const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
                 const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
-                if (!mbar_wait(bar(ACCE + ab), abph ^ 1, abort_flag, p.err, 4)) { ok = false; break; }
+                if (!mbar_wait_cl(bar(ACCE + ab), abph ^ 1, abort_flag, peer_abort, p.err, 4)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dacc = tmem + (uint32_t)(ab * 256);
                 const uint32_t dcor = SPLIT_ACC ? tmem + 256u : dacc;
-                for (int c = 0; c < chunks_per_tile; ++c, ++it) {
-                    const int pl = c / p.kch, kc = c % p.kch;
+                for (int c = 0; c < nchunk; ++c, ++it) {
                     const int slot = (int)(it & 1);
                     const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                    if (!mbar_wait(bar(TFULL + slot), sph, abort_flag, p.err, 5)) { ok = false; break; }
+                    if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
                     tc_fence_after();
-                    // Compact issue loop (a long unrolled body stalls this single
-                    // issuing thread on instruction fetch).  The start-address
-                    // field of a descriptor is addr >> 4, so a 32-byte K-step
-                    // adds 2 and the Im-half of B adds Np*128 >> 4.
+                    // descriptor start field = address >> 4: a 32-byte K step adds 2
                     const uint32_t ahi = tmem + (slot ? 448u : 192u);
-                    const unsigned long long dh = dBhi0 + ((unsigned long long)(kc * chunkB) >> 4);
-                    const unsigned long long dl = dBlo0 + ((unsigned long long)(kc * chunkB) >> 4);
-                    if (pl == 0) {
+                    const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
+                    const unsigned long long dl = dBlo0 + ((unsigned long long)(c * chunkB) >> 4);
 #pragma unroll 1
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint32_t ah = ahi + kk * 8, al = ah + 32;
-                            const unsigned long long o = 2ull * kk;
-                            mma_tf32(dacc, ah, dh + o, id_full, (c | kk) ? 1u : 0u);
-                            mma_tf32(dcor, ah, dl + o, id_full, (SPLIT_ACC && !(c | kk)) ? 0u : 1u);
-                            mma_tf32(dcor, al, dh + o, id_full, 1u);
-                        }
-                    } else {
-                        // D[:, 0:Np] += A_im * (-Im G);  D[:, Np:2Np] += A_im * Re G
-                        const unsigned long long im = (unsigned long long)(Np * 128) >> 4;
-#pragma unroll 1
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint32_t ah = ahi + kk * 8, al = ah + 32;
-                            const unsigned long long o = 2ull * kk;
-                            mma_tf32(dacc, ah, dh + im + o, id_half_neg, 1u);
-                            mma_tf32(dcor, ah, dl + im + o, id_half_neg, 1u);
-                            mma_tf32(dcor, al, dh + im + o, id_half_neg, 1u);
-                            mma_tf32(dacc + Np, ah, dh + o, id_half, 1u);
-                            mma_tf32(dcor + Np, ah, dl + o, id_half, 1u);
-                            mma_tf32(dcor + Np, al, dh + o, id_half, 1u);
-                        }
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t ah = ahi + kk * 8, al = ah + 32;
+                        const unsigned long long o = 2ull * kk;
+                        mma_tf32_pair(dacc, ah, dh + o, id, (c | kk) ? 1u : 0u);
+                        mma_tf32_pair(dcor, ah, dl + o, id, (SPLIT_ACC && !(c | kk)) ? 0u : 1u);
+                        mma_tf32_pair(dcor, al, dh + o, id, 1u);
                     }
-                    mma_commit(bar(TEMPTY + slot));
+                    issued = true;
+                    mma_commit_pair(bar(TEMPTY + slot), (uint16_t)3);
                 }
                 if (!ok) break;
-                mma_commit(bar(ACCF + ab));
-                if (t + 1 < t1 && (int)((t + 1) / p.mtiles) != u) mma_commit(bar(BEMPTY));
+                mma_commit_pair(bar(ACCF + ab), (uint16_t)3);
+                if (t + 1 < t1 && (int)((t + 1) / ipu) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
             }
-            if (*abort_flag) {
-                mma_commit(bar(DRAIN));
-                const unsigned long long g0 = gtimer();
-                while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
+            (void)issued;
+            // Closing commit to both CTAs: it completes once every MMA this
+            // thread issued is done, so neither CTA leaves (or frees its TMEM)
+            // while an MMA still reads its shared memory or tensor memory,
+            // also when a wait gave up.
+            mma_commit_pair(bar(DRAIN), (uint16_t)3);
+            const unsigned long long g0 = gtimer();
+            while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
+        } else if (lane == 0) {
+            const unsigned long long g0 = gtimer();
+            while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
+        }
+    } else if (warp == 2) {
+        if (lane == 0 && rank == 1) {
+            // ---------------- B relay (odd CTA): its B half landed -> even CTA ----------------
+            int cur_u = -1;
+            uint32_t bph = 0;
+            for (long long t = t0; t < t1; ++t) {
+                const int u = (int)(t / ipu);
+                if (u == cur_u) continue;
+                cur_u = u;
+                if (!mbar_wait_cl(bar(BFULL), bph, abort_flag, peer_abort, p.err, 9)) break;
+                bph ^= 1;
+                mbar_arrive_cluster(bar0(BPEER));
             }
         }
     } else if (warp >= 4 && warp < 8) {
-        // ---------------- converter: FP32 A tile -> TF32 hi/lo in TMEM ----------------
+        // ---------------- converter: FP32 A tile -> TF32 hi/lo in this CTA's TMEM ----------------
         const int wq = warp & 3;
         const int r = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
         long long it = 0;
         bool ok = true;
         for (long long t = t0; t < t1 && ok; ++t) {
-            for (int c = 0; c < chunks_per_tile; ++c, ++it) {
+            for (int c = 0; c < nchunk; ++c, ++it) {
                 const int s = (int)(it % kStageAStages);
                 const uint32_t ph = (uint32_t)((it / kStageAStages) & 1);
-                if (!warp_wait(bar(AFULL + s), ph, abort_flag, p.err, 6)) { ok = false; break; }
+                if (!warp_wait_cl(bar(AFULL + s), ph, abort_flag, peer_abort, p.err, 6)) { ok = false; break; }
                 uint32_t hi[32], lo[32];
                 load_split_row(sA + s * kTileBytes, r, hi, lo);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(AEMPTY + s));
                 const int slot = (int)(it & 1);
                 const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                if (!warp_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 7)) { ok = false; break; }
+                if (!warp_wait_cl(bar(TEMPTY + slot), sph ^ 1, abort_flag, peer_abort, p.err, 7)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t ta = lane_base + (slot ? 448u : 192u);
                 tmem_st32(ta, hi);
@@ -483,11 +616,11 @@ __global__ void __launch_bounds__(kStageThreads, 1)
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(bar(TFULL + slot));
+                if (lane == 0) mbar_arrive_cluster(bar0(TFULL + slot));
             }
         }
     } else if (warp >= 8) {
-        // ---------------- epilogue: TMEM -> registers -> HBM (scattered layout) ----------------
+        // ---------------- epilogue: this CTA's 128 rows, TMEM -> HBM ----------------
         const int wq = warp & 3;
         const int rloc = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
@@ -495,12 +628,12 @@ __global__ void __launch_bounds__(kStageThreads, 1)
         long long tile_i = 0;
         bool ok = true;
         for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
-            const int u = (int)(t / p.mtiles), mt = (int)(t % p.mtiles);
+            const int u = (int)(t / ipu);
             const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
             const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
-            if (!warp_wait(bar(ACCF + ab), abph, abort_flag, p.err, 8)) { ok = false; break; }
+            if (!warp_wait_cl(bar(ACCF + ab), abph, abort_flag, peer_abort, p.err, 8)) { ok = false; break; }
             tc_fence_after();
-            const long long row = (long long)mt * kBM + rloc;
+            const long long row = (t % ipu) * (2 * kBM) + (long long)rank * kBM + rloc;
             const bool valid = row < p.M;
             const long long x = row % p.map.Dx;
             const long long rb = row / p.map.Dx;
@@ -532,13 +665,15 @@ __global__ void __launch_bounds__(kStageThreads, 1)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar(ACCE + ab));
+            if (lane == 0) mbar_arrive_cluster(bar0(ACCE + ab));
         }
     }
+    tc_fence_before();
     __syncthreads();
+    cluster_sync_all();  // no MMA, remote arrive or peer read of this CTA's memory remains
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc_pair(tmem, 512);
     }
 }
 
@@ -799,9 +934,12 @@ __global__ void k_build_vK32(int N, int Np, const double* __restrict__ v, float*
     lo[e] = l;
 }
 
-// Per-unit B operands of the tensor-core path (padded to Np, zero padding):
-//   B1[u][(c,r)][s] = Gb_c[s][r]   (S1)      Gs[u][(c,p)][q] = G_c[p][q]   (S2, S3)
-// each stored as TF32 hi then lo blocks of ub units.
+// Per-unit B operands of the tensor-core path (padded to Np, zero padding),
+// stored as TF32 hi then lo blocks of ub units:
+//   B1[u][(c,r)][s] = Gb_c[s][r]                                   (S1)
+//   Gs[u][b][p][q]  = (Re G, Im G, -Im G, Re G)[b] [p][q]           (S2, S3)
+// Block 2 pl + h is the K-plane pl of output half h (the rows held by CTA h
+// of a pair) of B' = [[Re G | -Im G]; [Im G | Re G]].
 __global__ void k_forms_tf32(int N, int Np, int nb, int ub, const double2* __restrict__ G,
                              const double2* __restrict__ Gb, float* __restrict__ B1,
                              float* __restrict__ Gs) {
@@ -820,11 +958,16 @@ __global__ void k_forms_tf32(int N, int Np, int nb, int ub, const double2* __res
         const double2 g = G[u * NN + (long long)idx * N + k];    // G[p = idx][q = k]
         split_f64(comp ? g.y : g.x, gh, gl);
     }
-    const long long lo_off = per * ub;
     B1[e] = bh;
-    B1[lo_off + e] = bl;
-    Gs[e] = gh;
-    Gs[lo_off + e] = gl;
+    B1[per * ub + e] = bl;
+    // Gs: Re G -> blocks 0 and 3, Im G -> block 1 and (negated) block 2
+    const long long pg = 2 * per;
+    const long long g0 = (long long)u * pg + rr;
+    const long long g1 = (long long)u * pg + per + (comp ? 0 : Np * (long long)Np) + (long long)idx * Np + k;
+    Gs[g0] = gh;
+    Gs[pg * ub + g0] = gl;
+    Gs[g1] = comp ? -gh : gh;
+    Gs[pg * ub + g1] = comp ? -gl : gl;
 }
 
 inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -886,10 +1029,20 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
     t = launch_begin(c, K_PREP, 0.0, 0.0);
     k_build_vK32<<<grid1(Np4, 256), 256, 0, c->stream>>>(c->N, c->Np, c->v, c->vKhi, c->vKlo);
     GKBA_TRY(launch_end(c, t));
-    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)stage_smem_bytes(c->Np)));
-    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)stage_smem_bytes(c->Np)));
+    for (auto kfn : {k_tc_pair<false>, k_tc_pair<true>})
+        GKBA_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)stage_smem_bytes(c->Np)));
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(c->num_sms & ~1));
+        cfg.blockDim = dim3(kStageThreads);
+        cfg.dynamicSmemBytes = stage_smem_bytes(c->Np);
+        cfg.stream = c->stream;
+        int ncl = 0;
+        GKBA_CUDA(c, cudaOccupancyMaxActiveClusters(&ncl, k_tc_pair<false>, &cfg));
+        if (ncl < 1) return fail(c, GKBA_ECUDA, "no 2-CTA cluster of the stage kernel fits on an SM pair");
+        c->pair_clusters = ncl;
+    }
     GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)final_smem_bytes(c->Np)));
     return GKBA_OK;
@@ -923,7 +1076,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     float* B1hi = (float*)c->formsB1;
     float* B1lo = B1hi + per * c->ub_cap;
     float* Gshi = (float*)c->formsG;
-    float* Gslo = Gshi + per * c->ub_cap;
+    float* Gslo = Gshi + 2 * per * c->ub_cap;
     int* err = c->dint + 1;
     // Flops below are the algorithmic counts of the N-basis problem (padding excluded).
     const double Nr = c->N;
@@ -945,13 +1098,16 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         GKBA_TRY(make_map(c, &mA23_in2, X2, 4, d, s, b));
     }
     {
+        // B1[u][(c,r)][s]; Gs[u][4 blocks][p][q]; each CTA of a pair loads Np rows
         cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)2 * Np, (cuuint64_t)nb};
         cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)per * 4};
-        cuuint32_t b[3] = {kKC, (cuuint32_t)(2 * Np), 1};
+        cuuint32_t b[3] = {kKC, (cuuint32_t)Np, 1};
         GKBA_TRY(make_map(c, &mB1h, B1hi, 3, d, s, b));
         GKBA_TRY(make_map(c, &mB1l, B1lo, 3, d, s, b));
-        GKBA_TRY(make_map(c, &mGh, Gshi, 3, d, s, b));
-        GKBA_TRY(make_map(c, &mGl, Gslo, 3, d, s, b));
+        cuuint64_t dg[3] = {(cuuint64_t)Np, (cuuint64_t)4 * Np, (cuuint64_t)nb};
+        cuuint64_t sg[2] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * per * 4};
+        GKBA_TRY(make_map(c, &mGh, Gshi, 3, dg, sg, b));
+        GKBA_TRY(make_map(c, &mGl, Gslo, 3, dg, sg, b));
     }
     if ((Np % 32) == 0) {
         const long long Rl = ((2LL * Np * nb + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
@@ -974,9 +1130,9 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     }
 
     const size_t ssm = stage_smem_bytes(Np);
-    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_stage<true> : k_tc_stage<false>;
-    const long long total = (long long)nb * mtiles;
-    const int grid = (int)(total < c->num_sms ? total : c->num_sms);
+    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_pair<true> : k_tc_pair<false>;
+    const long long pair_tiles = (long long)nb * mtiles / 2;  // 256-row tiles
+    const int grid = 2 * (int)(pair_tiles < c->pair_clusters ? pair_tiles : c->pair_clusters);
     StageParams sp{};
     sp.Np = Np;
     sp.kch = kch;
