@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--chains", action="store_true",
+                    help="time the Sec. IV propagations at N_b = 10 (Table I context)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one split-TF32 collision over one history point at N "
                          "with a two-unit workspace (the small case for ncu captures) and exit")
@@ -219,8 +221,54 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_chains(a):
+    """The paper's Sec. IV propagations at N_b = 10, each a whole GKBA run of
+    N_t Heun steps through gkba_step (field-free, from the initial state):
+    (1) Hubbard chain, diagonal basis, 5000 x 0.01; (2) Ohno chain, symmetric
+    basis, 2000 x 0.025; (3) general basis (the seeded stand-in for the CH4
+    integrals, 2 occupied orbitals), 1000 x 0.05.  One JSON line per run; the
+    paper's single-core CPU times (Table I, tensor-contraction column) are
+    context, not a target."""
+    import torch
+    import gkba_inputs as gi
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as P
+    cases = [("hubbard_chain_N10", "diagonal", 0.01, 5000, "fp64", 164.0),
+             ("ohno_chain_N10", "symmetric", 0.025, 2000, "fp64", 731.0),
+             ("general_basis_N10", "general", 0.05, 1000, "fp64", 1333.0),
+             ("general_basis_N10", "general", 0.05, 1000, "tf32acc", 1333.0)]
+    for name, kind, dt, n, prec, paper in cases:
+        s = gi.system(10, 8, seed=0) if kind == "general" else gi.chain(10, kind)
+        ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=prec,
+                        interaction=kind)
+        tr0 = float(np.trace(s["rho0"]).real)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr, en = [], []
+        for _ in range(n):
+            _, _, diag = ctx.step(0.0, 0.0)
+            tr.append(diag[0])
+            en.append(diag[1])
+        wall = time.perf_counter() - t0
+        _, launches = ctx.stats(reset=True)
+        ctx.close()
+        print(json.dumps({"workload": name, "metric": "GKBA propagation wall time (N_t steps)",
+                          "value": wall, "unit": "s", "higher_is_better": False,
+                          "interaction": kind, "precision": prec, "N": 10, "steps": n, "dt": dt,
+                          "ms_per_step": 1e3 * wall / n, "gpu_launches": launches,
+                          "trace_drift": float(np.abs(np.array(tr) - tr0).max()),
+                          "energy_drift": float(np.abs(np.array(en) - en[0]).max()),
+                          "paper_table1_s": paper,
+                          "paper_hardware": "Intel i5-4460, 1 core, NumPy/Armadillo (context)"}),
+              flush=True)
+
+
 def main():
     a = parse()
+    if a.chains:
+        run_chains(a)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -41,6 +41,7 @@ __all__ = [
     "history",
     "random_pair",
     "random_symmetric_v",
+    "chain",
 ]
 
 
@@ -154,3 +155,39 @@ def random_symmetric_v(N, n_P=None, seed=0):
     B = rng.normal(size=(n_P, N, N))
     B = 0.5 * (B + B.transpose(0, 2, 1))
     return np.ascontiguousarray(np.einsum("pil,pjk->ijkl", B, B, optimize=True))
+
+
+def chain(N, interaction="diagonal", J=-1.0, U=1.0, W=100.0):
+    """Polymer-chain workloads of Sec. IV: a 1D chain of N sites with
+    nearest-neighbour hopping J (open ends) and either
+
+    * interaction="diagonal":  on-site U_i = U (Hubbard-like, Sec. III A), or
+    * interaction="symmetric": Ohno V_ij = U / sqrt(1 + |i - j|^2) (Sec. III B).
+
+    Initial state: N//2 particles per spin confined to the N//2 leftmost sites,
+    rho0 = projector on the N//2 lowest eigenvectors of h + W sum_{i >= N//2}
+    |i><i| (W = 100, a strong confinement); the propagation uses h alone (the
+    confinement is released at t = 0).  d = diag(i - (N-1)/2), the site
+    position, for a field if one is applied.  Deterministic (no draws).
+
+    Returns dict(h, v, d, rho0) with v = the vector U (diagonal) or the matrix
+    V (symmetric), the form gkba_init takes for those interactions.
+    """
+    h = np.zeros((N, N), np.complex128)
+    for i in range(N - 1):
+        h[i, i + 1] = h[i + 1, i] = J
+    idx = np.arange(N)
+    if interaction == "diagonal":
+        v = np.full(N, float(U))
+    elif interaction == "symmetric":
+        v = U / np.sqrt(1.0 + (idx[:, None] - idx[None, :]) ** 2.0)
+    else:
+        raise ValueError(f"unknown interaction {interaction!r}")
+    n_occ = max(1, N // 2)
+    hc = h + np.diag(np.where(idx >= N // 2, W, 0.0))
+    _, vec = np.linalg.eigh(hc)
+    occ = vec[:, :n_occ]
+    rho0 = occ @ occ.conj().T
+    rho0 = 0.5 * (rho0 + rho0.conj().T)
+    d = np.diag(idx - 0.5 * (N - 1)).astype(np.complex128)
+    return dict(h=h, v=np.ascontiguousarray(v), d=d, rho0=rho0)

@@ -70,6 +70,15 @@ typedef enum {
                             about 25% slower */
 } gkba_precision;
 
+typedef enum {
+    GKBA_V_GENERAL = 0,   /* v: N^4 real Coulomb integrals v_ijkl (Sec. III C) */
+    GKBA_V_DIAGONAL = 1,  /* v: N reals U_i, v_ijkl = U_i d_ij d_ik d_il (Sec. III A,
+                             Hubbard-like on-site interaction); Sigma by Eq. (2b-diag) */
+    GKBA_V_SYMMETRIC = 2  /* v: N*N real symmetric V_ij, v_ijkl = V_ij d_il d_jk
+                             (Sec. III B, density-density interaction); Sigma by
+                             Eq. (2b-symm), bubble and exchange */
+} gkba_interaction;
+
 typedef struct {
     int N;             /* basis size, 1 <= N <= 128 (tensor-core modes: N <= 96) */
     double dt;         /* time step delta (> 0) */
@@ -87,6 +96,8 @@ typedef struct {
                           GKBA_SPLIT_TF32, 64 for GKBA_SPLIT_TF32_ACC).  Shorter chunks
                           bound the tensor-core accumulation error, longer ones
                           write fewer partials. */
+    int interaction;   /* gkba_interaction: form of the v argument of gkba_init;
+                          GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC need precision GKBA_FP64 */
 } gkba_config;
 
 /* Per-kernel-class counters (see gkba_get_stats). */
@@ -101,13 +112,20 @@ typedef struct {
 /*
  * gkba_init - create a context for the model of Sec. II, Eq. (hamiltonian).
  *   h    N*N complex Hermitian one-body matrix h_ij (Eq. onebody), no field
- *   v    N^4 real Coulomb integrals with the 8-fold symmetry of Eq. (symmetries)
+ *   v    the interaction, by cfg->interaction:
+ *          GKBA_V_GENERAL   N^4 real Coulomb integrals with the 8-fold symmetry
+ *                           of Eq. (symmetries)
+ *          GKBA_V_DIAGONAL  N reals U_i (v_ijkl = U_i d_ij d_ik d_il)
+ *          GKBA_V_SYMMETRIC N*N real symmetric V_ij (v_ijkl = V_ij d_il d_jk)
  *   d    N*N complex Hermitian dipole matrix; the field enters as h + E(t) d
  *   rho0 N*N complex Hermitian initial density matrix rho(t_0) (per spin)
- * Builds the contraction layouts of v and w = 2v - v_exch on the device, and
- * the history store (rho_0 = rho0, T(t_0,t_0) = 1).  Returns GKBA_EINVAL for
- * non-Hermitian h/d/rho0 or a v that breaks Eq. (symmetries) (tolerance
- * 1e-10 relative), non-finite data or bad sizes; *out is NULL on failure.
+ * Builds the contraction layouts of v and w = 2v - v_exch on the device (the
+ * diagonal and symmetric forms are expanded to v_ijkl for the mean field;
+ * their self-energy uses Eq. (2b-diag) / Eq. (2b-symm) directly), and the
+ * history store (rho_0 = rho0, T(t_0,t_0) = 1).  Returns GKBA_EINVAL for
+ * non-Hermitian h/d/rho0, a v that breaks Eq. (symmetries) (tolerance 1e-10
+ * relative), an asymmetric V, a structured interaction with a split-TF32
+ * precision, non-finite data or bad sizes; *out is NULL on failure.
  */
 gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, const double* v,
                       const double* d, const double* rho0, int inputs_on_device);

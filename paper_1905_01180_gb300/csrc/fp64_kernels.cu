@@ -432,17 +432,37 @@ __global__ void k_reduce_partials_p2(long long n, int nzc, const double2* __rest
     S[e] = make_double2(re, im);
 }
 
-// I_acc[e] += sum_u coef[u] * Y[u][e] (fixed unit order: deterministic).
-__global__ void k_weighted_sum(int NN, int nb, const double* __restrict__ coef,
-                               const double2* __restrict__ Y, double2* __restrict__ I_acc) {
+// I_acc[e] += sum_u coef[u] * Y[u][e] in two passes with a fixed order
+// (deterministic): pass 1 sums the contiguous unit range z of every element
+// into tmp[z][e] (blockIdx.y = z), pass 2 adds the ranges in order.  Small
+// bases have few elements and many units (N = 10: 100 elements, up to 10^4
+// units per batch), so the units are spread over the grid, not looped by one
+// thread per element.
+constexpr int kWsumRanges = 256;
+__global__ void k_weighted_sum_p1(int NN, int nb, int per, const double* __restrict__ coef,
+                                  const double2* __restrict__ Y, double2* __restrict__ tmp) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NN) return;
+    const int u0 = blockIdx.y * per;
+    const int u1 = min(nb, u0 + per);
     double re = 0.0, im = 0.0;
-    for (int u = 0; u < nb; ++u) {
+    for (int u = u0; u < u1; ++u) {
         const double c = coef[u];
         const double2 y = Y[(long long)u * NN + e];
         re = fma(c, y.x, re);
         im = fma(c, y.y, im);
+    }
+    tmp[(long long)blockIdx.y * NN + e] = make_double2(re, im);
+}
+__global__ void k_weighted_sum_p2(int NN, int nz, const double2* __restrict__ tmp,
+                                  double2* __restrict__ I_acc) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NN) return;
+    double re = 0.0, im = 0.0;
+    for (int z = 0; z < nz; ++z) {
+        const double2 t = tmp[(long long)z * NN + e];
+        re += t.x;
+        im += t.y;
     }
     I_acc[e].x += re;
     I_acc[e].y += im;
@@ -478,6 +498,72 @@ __global__ void k_build_vK64(int N, const double* __restrict__ v, double* __rest
 
 inline unsigned grid1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// ---------------------------------------------------------------------------
+// Structured interactions (Sec. III A, B): the self-energy without the N^5
+// contraction chain.
+// ---------------------------------------------------------------------------
+// Diagonal basis, Eq. (2b-diag): S_ij = U_i U_j G_ij Gb_ji G_ij
+// (the entrywise form diag(V) o diag(V) o G o Gb^T o G of Eq. (2b-diag-opt)).
+__global__ void k_sigma_diag(int N, int nb, const double* __restrict__ U,
+                             const double2* __restrict__ G, const double2* __restrict__ Gb,
+                             double2* __restrict__ S) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)N * N;
+    if (e >= NN * nb) return;
+    const long long u = e / NN;
+    const int rr = (int)(e % NN);
+    const int i = rr / N, j = rr % N;
+    const double2 g = G[e];
+    const double2 x = cmul(cmul(g, g), Gb[u * NN + (long long)j * N + i]);
+    const double s = U[i] * U[j];
+    S[e] = make_double2(s * x.x, s * x.y);
+}
+
+// Symmetric basis, Eq. (2b-symm), bubble and exchange together:
+//   S_ij = sum_kl V_ik V_jl (2 G_ij Gb_lk G_kl - G_il Gb_lk G_kj)
+//        = sum_l V_jl (2 G_ij r_l - G_il W_lj)
+// with, for the row i of the block,
+//   r_l  = sum_k V_ik Gb_lk G_kl   (the bubble's [V x (Gb^T o G)]_il, Eq. bubble-contract)
+//   W_lj = sum_k V_ik Gb_lk G_kj   (N^3 per row: the exchange term has no
+//                                   matrix-product form for the full matrix).
+// One block per (row i, unit u); r_l in shared memory; a thread per column j
+// (the Gb_lk loads are the same for all threads of a warp, the G_kj loads are
+// consecutive in j).  N^4 per unit.
+__global__ void k_sigma_symm(int N, const double* __restrict__ V, const double2* __restrict__ G,
+                             const double2* __restrict__ Gb, double2* __restrict__ S) {
+    extern __shared__ double2 r_sh[];
+    const int i = blockIdx.x;
+    const long long NN = (long long)N * N;
+    const double2* g = G + (long long)blockIdx.y * NN;
+    const double2* gb = Gb + (long long)blockIdx.y * NN;
+    const double* vi = V + (long long)i * N;
+    for (int l = threadIdx.x; l < N; l += blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < N; ++k) {
+            const double2 a = gb[(long long)l * N + k];
+            acc = cadd(acc, cmul(make_double2(vi[k] * a.x, vi[k] * a.y), g[(long long)k * N + l]));
+        }
+        r_sh[l] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const double2 gij = g[(long long)i * N + j];
+        double2 s = make_double2(0.0, 0.0);
+        for (int l = 0; l < N; ++l) {
+            double2 w = make_double2(0.0, 0.0);
+            for (int k = 0; k < N; ++k) {
+                const double2 a = gb[(long long)l * N + k];
+                w = cadd(w, cmul(make_double2(vi[k] * a.x, vi[k] * a.y), g[(long long)k * N + j]));
+            }
+            const double2 b = cmul(gij, r_sh[l]);
+            const double2 x = cmul(g[(long long)i * N + l], w);
+            const double vjl = V[(long long)j * N + l];
+            s = cadd(s, make_double2(vjl * (2.0 * b.x - x.x), vjl * (2.0 * b.y - x.y)));
+        }
+        S[(long long)blockIdx.y * NN + (long long)i * N + j] = s;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -489,7 +575,7 @@ gkba_status fp64_prepare_model(gkba_ctx* c) {
     auto t = launch_begin(c, K_PREP, 0.0, 0.0);
     k_build_hfK<<<grid1(N4, 256), 256, 0, c->stream>>>(c->N, c->v, c->hfK);
     GKBA_TRY(launch_end(c, t));
-    if (c->prec != GKBA_FP64) return GKBA_OK;
+    if (c->prec != GKBA_FP64 || c->kind != GKBA_V_GENERAL) return GKBA_OK;
     t = launch_begin(c, K_PREP, 0.0, 0.0);
     k_build_wS64<<<grid1(N4, 256), 256, 0, c->stream>>>(c->N, c->v, c->wS64);
     GKBA_TRY(launch_end(c, t));
@@ -687,8 +773,15 @@ gkba_status reduce_batch(gkba_ctx* c, int nb, double2* I_acc, double2* S_out) {
     }
     GKBA_TRY(zgemm_batched(c, K_RED, N, 'N', 'N', make_double2(1.0, 0.0), c->Su, NN, c->Mb, NN,
                            make_double2(0.0, 0.0), c->Yu, NN, nb, 0));
+    // nz <= nb <= ub ranges of N*N entries: red_tmp holds 16 ub of them
+    const int nz = nb < kWsumRanges ? nb : kWsumRanges;
+    const int per = (nb + nz - 1) / nz;
     auto t = launch_begin(c, K_RED, 0.0, 0.0);
-    k_weighted_sum<<<grid1(NN, 256), 256, 0, c->stream>>>((int)NN, nb, c->coef, c->Yu, I_acc);
+    k_weighted_sum_p1<<<dim3(grid1(NN, 128), nz), 128, 0, c->stream>>>((int)NN, nb, per, c->coef,
+                                                                       c->Yu, c->red_tmp);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_weighted_sum_p2<<<grid1(NN, 256), 256, 0, c->stream>>>((int)NN, nz, c->red_tmp, I_acc);
     return launch_end(c, t);
 }
 
@@ -733,6 +826,28 @@ gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
                               8.0 * (2 * N4 * nb + N4)));
     }
     return reduce_partials_launch(c, nb, nz, N * R, R, c->part, false, c->Su);
+}
+
+// Self-energy of a structured interaction for nb units (G_u, Gb_u device
+// pointers with stride N*N) into c->Su; the kernels write c->PQ (free at this
+// point of a batch) because G may alias c->Su.
+gkba_status contract_structured(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
+    const int N = c->N;
+    const long long NN = (long long)N * N;
+    const double n = N;
+    if (c->kind == GKBA_V_DIAGONAL) {
+        auto t = launch_begin(c, K_W1, 6.0 * n * n * nb, 48.0 * n * n * nb);
+        k_sigma_diag<<<grid1(nb * NN, 256), 256, 0, c->stream>>>(N, nb, c->vm, G, Gb, c->PQ);
+        GKBA_TRY(launch_end(c, t));
+    } else {
+        const int bs = N >= 128 ? 128 : ((N + 31) / 32) * 32;
+        auto t = launch_begin(c, K_W1, 8.0 * n * n * n * n * nb, 48.0 * n * n * nb);
+        k_sigma_symm<<<dim3(N, nb), bs, N * sizeof(double2), c->stream>>>(N, c->vm, G, Gb, c->PQ);
+        GKBA_TRY(launch_end(c, t));
+    }
+    GKBA_CUDA(c, cudaMemcpyAsync(c->Su, c->PQ, nb * NN * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    return GKBA_OK;
 }
 
 }  // namespace gkba

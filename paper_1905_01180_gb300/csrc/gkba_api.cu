@@ -99,12 +99,14 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const long long N = c->N, NN = N * N;
     want_units = std::max(2, want_units + (want_units & 1));
     const bool tc = tensor_core_path(c);
+    const bool gen = c->kind == GKBA_V_GENERAL;  // structured kinds need no stage buffers
     const long long Np = c->Np;
-    const double x_bytes = tc ? 2.0 * Np * Np * Np * Np * 4 : 2.0 * NN * NN * 8;
-    const double form_bytes = tc ? 4.0 * 2 * Np * Np * 4 : (2.0 * NN + 4.0 * NN) * 8;
+    const double x_bytes = !gen ? 0.0 : tc ? 2.0 * Np * Np * Np * Np * 4 : 2.0 * NN * NN * 8;
+    const double form_bytes = !gen ? 0.0 : tc ? 4.0 * 2 * Np * Np * 4 : (2.0 * NN + 4.0 * NN) * 8;
     const double N3 = (double)NN * N;
-    const double part_per_unit = tc ? (std::ceil((double)Np * Np * Np / c->s4_kchunk) * Np * 2.0 * Np * 4)
-                                    : (std::ceil(N3 / 8192.0) * N * 2.0 * N * 8);
+    const double part_per_unit = !gen ? 0.0
+                                 : tc ? (std::ceil((double)Np * Np * Np / c->s4_kchunk) * Np * 2.0 * Np * 4)
+                                      : (std::ceil(N3 / 8192.0) * N * 2.0 * N * 8);
     const double per_unit = 2 * x_bytes + form_bytes + part_per_unit + (4.0 + kReduceSplit) * NN * 16 + 8;
     size_t cap = c->ws_cap;
     size_t free_b = 0, total_b = 0;
@@ -129,19 +131,20 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     }
     Carver cv;
     // the last stage's K-blocked X3 pads the batch's 2 Np ub rows to 256
-    const double x3_blocked = tc ? (double)Np * Np * Np * (((2.0 * Np * ub + 255) / 256) * 256) * 4 : 0.0;
+    const double x3_blocked = tc && gen ? (double)Np * Np * Np * (((2.0 * Np * ub + 255) / 256) * 256) * 4 : 0.0;
     const size_t x13_bytes = (size_t)std::max(x_bytes * ub, std::floor(x3_blocked));
     const size_t oX13 = cv.take(x13_bytes);
     const size_t oX2 = cv.take((size_t)(x_bytes * ub));
     size_t part_bytes;
-    if (tc) part_bytes = tf32_part_bytes((int)Np, ub, c->s4_kchunk);
+    if (!gen) part_bytes = 0;
+    else if (tc) part_bytes = tf32_part_bytes((int)Np, ub, c->s4_kchunk);
     else {
         const long long nz = (long long)std::ceil(N3 / 8192.0);
         part_bytes = (size_t)(nz * N * 2LL * N * ub * 8);
     }
     const size_t oPart = cv.take(part_bytes);
-    const size_t oB1 = cv.take(tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(2LL * NN * ub * 8));
-    const size_t oG = cv.take(tc ? (size_t)(2LL * 4 * Np * Np * ub * 4) : (size_t)(4LL * NN * ub * 8));
+    const size_t oB1 = cv.take(!gen ? 0 : tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(2LL * NN * ub * 8));
+    const size_t oG = cv.take(!gen ? 0 : tc ? (size_t)(2LL * 4 * Np * Np * ub * 4) : (size_t)(4LL * NN * ub * 8));
     const size_t oPQ = cv.take((size_t)(ub * NN * 16));
     const size_t oMb = cv.take((size_t)(ub * NN * 16));
     const size_t oCoef = cv.take((size_t)ub * 8);
@@ -187,7 +190,10 @@ gkba_status ensure_stage(gkba_ctx* c, size_t bytes) {
     return GKBA_OK;
 }
 
-static gkba_status contract(gkba_ctx* c, int nb) {
+// One batch of nb units: (G_u, Gb_u) at G, Gb (stride N*N; the general paths
+// read the forms built from them) -> S_u in c->Su.
+static gkba_status contract(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
+    if (c->kind != GKBA_V_GENERAL) return contract_structured(c, nb, G, Gb);
     if (tensor_core_path(c)) return contract_batch_tf32(c, nb);
     return contract_batch_fp64(c, nb);
 }
@@ -202,7 +208,7 @@ gkba_status collision_dev(gkba_ctx* c, int L, const double2* rho, const double2*
     for (int k0 = 0; k0 < L; k0 += nk_per) {
         const int nk = std::min(nk_per, L - k0);
         GKBA_TRY(build_forms_gkba(c, k0, nk, L, rho, T, weights_dev));
-        GKBA_TRY(contract(c, 2 * nk));
+        GKBA_TRY(contract(c, 2 * nk, c->Su, c->Mb));
         GKBA_TRY(reduce_batch(c, 2 * nk, I_out, nullptr));
     }
     return GKBA_OK;
@@ -214,7 +220,7 @@ gkba_status sigma_dev(gkba_ctx* c, int n_units, const double2* G, const double2*
     for (int u0 = 0; u0 < n_units; u0 += c->ub) {
         const int nb = std::min(c->ub, n_units - u0);
         GKBA_TRY(build_forms(c, nb, G + u0 * NN, NN, Gb + u0 * NN, NN, 0));
-        GKBA_TRY(contract(c, nb));
+        GKBA_TRY(contract(c, nb, G + u0 * NN, Gb + u0 * NN));
         GKBA_TRY(reduce_batch(c, nb, nullptr, S_out + u0 * NN));
     }
     return GKBA_OK;
@@ -300,7 +306,7 @@ void free_ctx(gkba_ctx* c) {
     if (!c) return;
     if (c->device >= 0) cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->h, c->d, c->v, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
+    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
                     c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
                     c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
                     c->stage};
@@ -341,6 +347,13 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     if (cfg->precision != GKBA_FP64 && cfg->precision != GKBA_SPLIT_TF32 &&
         cfg->precision != GKBA_SPLIT_TF32_ACC)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown precision %d", cfg->precision);
+    const int kind = cfg->interaction;
+    if (kind != GKBA_V_GENERAL && kind != GKBA_V_DIAGONAL && kind != GKBA_V_SYMMETRIC)
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown interaction %d", kind);
+    if (kind != GKBA_V_GENERAL && cfg->precision != GKBA_FP64)
+        return fail(nullptr, GKBA_EINVAL,
+                    "gkba_init: diagonal and symmetric interactions run in FP64 (precision %d)",
+                    cfg->precision);
     const int Np = ((N + 15) / 16) * 16;
     if (cfg->precision != GKBA_FP64 && Np > 96)
         return fail(nullptr, GKBA_EINVAL,
@@ -348,12 +361,14 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     const size_t NN = (size_t)N * N, N4 = NN * NN;
 
     // Host copies for validation (device inputs are copied back first).
-    std::vector<double> hh(2 * NN), dh(2 * NN), rh(2 * NN), vh(N4);
+    // v as given (N^4, N or N*N values) and expanded to v_ijkl
+    const size_t nv = kind == GKBA_V_GENERAL ? N4 : kind == GKBA_V_DIAGONAL ? (size_t)N : NN;
+    std::vector<double> hh(2 * NN), dh(2 * NN), rh(2 * NN), vm(nv), vh;
     if (inputs_on_device) {
         if (cudaMemcpy(hh.data(), h, 2 * NN * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(dh.data(), d, 2 * NN * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(rh.data(), rho0, 2 * NN * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(vh.data(), v, N4 * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaMemcpy(vm.data(), v, nv * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
             cudaGetLastError();
             return fail(nullptr, GKBA_EINVAL, "gkba_init: inputs_on_device but a pointer is not readable device memory");
         }
@@ -361,11 +376,33 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         memcpy(hh.data(), h, 2 * NN * 8);
         memcpy(dh.data(), d, 2 * NN * 8);
         memcpy(rh.data(), rho0, 2 * NN * 8);
-        memcpy(vh.data(), v, N4 * 8);
+        memcpy(vm.data(), v, nv * 8);
     }
     if (!finite_all(hh.data(), 2 * NN) || !finite_all(dh.data(), 2 * NN) ||
-        !finite_all(rh.data(), 2 * NN) || !finite_all(vh.data(), N4))
+        !finite_all(rh.data(), 2 * NN) || !finite_all(vm.data(), nv))
         return fail(nullptr, GKBA_EINVAL, "gkba_init: non-finite values in h, v, d or rho0");
+    if (kind == GKBA_V_GENERAL) {
+        vh.swap(vm);
+    } else {
+        // Sec. III A: v_iiii = U_i;  Sec. III B: v_ijji = V_ij (l = i, k = j)
+        vh.assign(N4, 0.0);
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                if (kind == GKBA_V_DIAGONAL && i != j) continue;
+                const double x = kind == GKBA_V_DIAGONAL ? vm[i] : vm[(size_t)i * N + j];
+                vh[(((size_t)i * N + j) * N + j) * N + i] = x;
+            }
+        if (kind == GKBA_V_SYMMETRIC) {
+            double mx = 0.0, dev = 0.0;
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) {
+                    mx = std::max(mx, std::fabs(vm[(size_t)i * N + j]));
+                    dev = std::max(dev, std::fabs(vm[(size_t)i * N + j] - vm[(size_t)j * N + i]));
+                }
+            if (dev > 1e-12 * std::max(mx, 1e-300))
+                return fail(nullptr, GKBA_EINVAL, "gkba_init: V of a symmetric interaction is not symmetric");
+        }
+    }
     if (!hermitian(hh.data(), N, 1e-10)) return fail(nullptr, GKBA_EINVAL, "gkba_init: h is not Hermitian");
     if (!hermitian(dh.data(), N, 1e-10)) return fail(nullptr, GKBA_EINVAL, "gkba_init: d is not Hermitian");
     if (!hermitian(rh.data(), N, 1e-10)) return fail(nullptr, GKBA_EINVAL, "gkba_init: rho0 is not Hermitian");
@@ -378,6 +415,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     c->dt = cfg->dt;
     c->max_steps = cfg->max_steps;
     c->prec = cfg->precision;
+    c->kind = kind;
     c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)16 << 30);
     c->timing = cfg->timing != 0;
     c->s4_kchunk = cfg->s4_kchunk > 0 ? cfg->s4_kchunk
@@ -455,7 +493,9 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     ALLOC(c->tmp1, NN * 16);
     ALLOC(c->dscal, 16 * 8);
     ALLOC(c->dint, 4 * 4);
-    if (c->prec == GKBA_FP64) {
+    if (kind != GKBA_V_GENERAL) {
+        ALLOC(c->vm, nv * 8);
+    } else if (c->prec == GKBA_FP64) {
         ALLOC(c->wS64, N4 * 8);
         ALLOC(c->vK64, N4 * 8);
     } else {
@@ -472,6 +512,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     if ((st = copy_in(c, c->h, hh.data(), NN * 16, 0)) != GKBA_OK) return bail(st);
     if ((st = copy_in(c, c->d, dh.data(), NN * 16, 0)) != GKBA_OK) return bail(st);
     if ((st = copy_in(c, c->v, vh.data(), N4 * 8, 0)) != GKBA_OK) return bail(st);
+    if (c->vm && (st = copy_in(c, c->vm, vm.data(), nv * 8, 0)) != GKBA_OK) return bail(st);
     if ((st = copy_in(c, c->rho_hist, rh.data(), NN * 16, 0)) != GKBA_OK) return bail(st);
     if (cudaMemsetAsync(c->dint, 0, 16, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->dscal, 0, 128, c->stream) != cudaSuccess) {

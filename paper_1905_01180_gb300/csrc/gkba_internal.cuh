@@ -52,6 +52,8 @@ struct gkba_ctx {
     bool timing = false;
     int num_sms = 0;
     int pair_clusters = 0;  // co-resident 2-CTA clusters of the stage kernel
+    int kind = GKBA_V_GENERAL;  // gkba_interaction
+    double* vm = nullptr;       // U (N) or V (N*N) of a structured interaction
     int s4_kchunk = 512;
 
     // model on the device
@@ -210,6 +212,8 @@ gkba_status sigma_dev(gkba_ctx* c, int n_units, const double2* G, const double2*
 // Contraction backends (one batch of units whose forms are already built).
 gkba_status contract_batch_fp64(gkba_ctx* c, int nb);
 gkba_status contract_batch_tf32(gkba_ctx* c, int nb);
+// Structured interaction (GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC): S(G_u, Gb_u) into Su.
+gkba_status contract_structured(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
 gkba_status tf32_prepare_model(gkba_ctx* c);  // build wS32, vKhi, vKlo
 gkba_status fp64_prepare_model(gkba_ctx* c);  // build wS64, vK64, hfK
 

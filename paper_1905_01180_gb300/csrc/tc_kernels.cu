@@ -1060,6 +1060,7 @@ gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG, con
                         long long sGb, int) {
     (void)sG;
     (void)sGb;
+    if (c->kind != GKBA_V_GENERAL) return GKBA_OK;  // structured: no contraction forms
     if (tensor_core_path(c)) return build_forms_tf32(c, nb, G, Gb);
     return build_forms_fp64(c, nb, G, Gb);
 }

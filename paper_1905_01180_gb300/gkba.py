@@ -6,7 +6,8 @@ this module converts numpy arrays (host buffers) or torch CUDA tensors
 the shared library is missing: there is no CPU fallback.
 
 Complex arrays are complex128 (interleaved re, im), N x N row-major; v is
-float64 with shape (N, N, N, N).
+float64 with shape (N, N, N, N) (general interaction), (N,) (U_i of the
+diagonal basis) or (N, N) (V_ij of the symmetric basis).
 """
 from __future__ import annotations
 
@@ -20,6 +21,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgkba.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC, EUNSUPPORTED = range(8)
 FP64, SPLIT_TF32, SPLIT_TF32_ACC = 0, 1, 2
+V_GENERAL, V_DIAGONAL, V_SYMMETRIC = 0, 1, 2
+_INTERACTION = {"general": V_GENERAL, "diagonal": V_DIAGONAL, "symmetric": V_SYMMETRIC,
+                V_GENERAL: V_GENERAL, V_DIAGONAL: V_DIAGONAL, V_SYMMETRIC: V_SYMMETRIC}
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT",
            6: "ENUMERIC", 7: "EUNSUPPORTED"}
 
@@ -38,7 +42,8 @@ class Config(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dt", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
-                ("timing", ctypes.c_int), ("s4_kchunk", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("s4_kchunk", ctypes.c_int),
+                ("interaction", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -106,10 +111,14 @@ class Context:
     """One GKBA system on one GPU (wraps a gkba_ctx)."""
 
     def __init__(self, h, v, d, rho0, dt, max_steps=0, precision="fp64", stream=None,
-                 workspace_bytes=0, device=-1, timing=False, s4_kchunk=0):
+                 workspace_bytes=0, device=-1, timing=False, s4_kchunk=0, interaction="general"):
         L = load()
         on_dev = _is_torch(h)
         N = int(h.shape[0])
+        kind = _INTERACTION[interaction]
+        want = {V_GENERAL: (N, N, N, N), V_DIAGONAL: (N,), V_SYMMETRIC: (N, N)}[kind]
+        if tuple(v.shape) != want:
+            raise ValueError(f"v has shape {tuple(v.shape)}, the {interaction} interaction takes {want}")
         keep = []
         if on_dev:
             ph = _dev(h, "c16"); pv = _dev(v, "f64"); pd = _dev(d, "c16"); pr = _dev(rho0, "c16")
@@ -121,7 +130,7 @@ class Context:
                 SPLIT_TF32: SPLIT_TF32, SPLIT_TF32_ACC: SPLIT_TF32_ACC}[precision]
         cfg = Config(N=N, dt=float(dt), max_steps=int(max_steps), precision=prec,
                      cuda_stream=stream, workspace_bytes=int(workspace_bytes), device=int(device),
-                     timing=1 if timing else 0, s4_kchunk=int(s4_kchunk))
+                     timing=1 if timing else 0, s4_kchunk=int(s4_kchunk), interaction=kind)
         handle = ctypes.c_void_p()
         st = L.gkba_init(ctypes.byref(handle), ctypes.byref(cfg), ph[1], pv[1], pd[1], pr[1],
                          1 if on_dev else 0)
@@ -132,6 +141,7 @@ class Context:
         self.dt = float(dt)
         self.max_steps = int(max_steps)
         self.precision = prec
+        self.interaction = kind
 
     # -- helpers -------------------------------------------------------
     def _check(self, st):

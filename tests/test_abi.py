@@ -36,7 +36,17 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(gkba.EXPORTED) == names
 
 
-def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None):
+def test_config_struct_matches_header():
+    # the binding's ctypes struct lists gkba_config's members in the header's order
+    from paper_1905_01180_gb300 import gkba
+    src = open(os.path.join(ROOT, "include", "gkba.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} gkba_config;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    members = re.findall(r"\b([A-Za-z_0-9]+)\s*;", body)
+    assert members == [f[0] for f in gkba.Config._fields_]
+
+
+def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None, interaction=0):
     from paper_1905_01180_gb300 import gkba
     s = gi.system(4, 4, seed=0)
     h = s["h"] if h is None else h
@@ -44,7 +54,8 @@ def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None):
     d = s["d"] if d is None else d
     rho = s["rho0"] if rho is None else rho
     cfg = gkba.Config(N=N, dt=dt, max_steps=1, precision=prec, cuda_stream=None,
-                      workspace_bytes=0, device=-1, timing=0, s4_kchunk=0)
+                      workspace_bytes=0, device=-1, timing=0, s4_kchunk=0,
+                      interaction=interaction)
     out = ctypes.c_void_p()
     arrs = [np.ascontiguousarray(x) for x in (h, v, d, rho)]
     st = lib.gkba_init(ctypes.byref(out), ctypes.byref(cfg), *[a.ctypes.data for a in arrs], 0)
@@ -73,6 +84,24 @@ def test_init_rejects_bad_sizes_and_inputs(lib):
     rho = s["rho0"].copy()
     rho[1, 1] = np.nan
     st, _, msg = _init(lib, rho=rho)
+    assert st == gkba.EINVAL and "non-finite" in msg
+
+
+def test_init_rejects_bad_structured_interactions(lib):
+    # Sec. III A/B interactions: an unknown kind, a split-TF32 precision (these
+    # paths run in FP64) and a non-symmetric V are refused before device work
+    from paper_1905_01180_gb300 import gkba
+    c = gi.chain(4, "symmetric")
+    st, _, msg = _init(lib, interaction=3, v=c["v"])
+    assert st == gkba.EINVAL and "interaction" in msg
+    st, _, msg = _init(lib, interaction=gkba.V_SYMMETRIC, prec=gkba.SPLIT_TF32, v=c["v"])
+    assert st == gkba.EINVAL and "FP64" in msg
+    V = c["v"].copy()
+    V[0, 2] += 0.1
+    st, _, msg = _init(lib, interaction=gkba.V_SYMMETRIC, v=V)
+    assert st == gkba.EINVAL and "not symmetric" in msg
+    U = np.array([1.0, np.inf, 1.0, 1.0])
+    st, _, msg = _init(lib, interaction=gkba.V_DIAGONAL, v=U)
     assert st == gkba.EINVAL and "non-finite" in msg
 
 

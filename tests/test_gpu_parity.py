@@ -355,6 +355,29 @@ def test_full_size_n96_sigma_tf32(P):
     ctx.close()
 
 
+@pytest.mark.slow
+def test_full_size_collision_sampled_units(P):
+    # The bench's workload in the bench's launch configuration: N = 96, 64
+    # factors, a 2001-point history contracted in batches of the default
+    # workspace (the last batch ragged).  I is linear in the weights c_k:
+    # with c_k nonzero only at sampled points in the first, a middle and the
+    # last batch every batch still runs, and the result must equal the
+    # oracle's sum over those points (Eq. collint, first line).
+    N, L, dt = 96, 2001, 0.02
+    s = gi.system(N, 64, seed=0)
+    rho, T = gi.history(N, L, dt, seed=0)
+    ks = np.array([0, 1001, L - 1])
+    w = np.zeros(L)
+    w[ks] = [0.5 * dt, dt, 0.5 * dt]
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, precision="tf32")
+    I = ctx.collision(rho, T, w)
+    ctx.close()
+    ref = O.collision(s["v"], rho[ks], T[ks], w[ks], chunk=1)
+    e = rel(I, ref)
+    print(f"N=96 L=2001 split-TF32 collision, sampled units {list(ks)}: rel err {e:.3e}")
+    assert e < TOL_TC
+
+
 def test_collision_n48_tf32(P):
     N, L = 48, 3
     s, ctx = ctx_for(P, N, n_P=16, seed=1, precision="tf32", dt=0.02)
