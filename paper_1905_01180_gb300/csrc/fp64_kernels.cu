@@ -261,6 +261,72 @@ __global__ void k_expm_setup(int N, double dt, const double2* __restrict__ hA,
     }
 }
 
+// The whole exponential for N <= 24 in one block, matrices in shared memory
+// (the same algorithm as k_expm_setup followed by the Horner and squaring
+// products: A = -i dt (hA + hB)/2 scaled by 2^-s so that ||A||_1 / 2^s <= 1/2,
+// the degree-18 Taylor polynomial by Horner, Y = I + X Y / k for k = 18 .. 1,
+// then min(s, 16) squarings).  One launch instead of 37 for small bases.
+constexpr int kExpmSmallN = 24;
+__device__ void smem_zgemm(int N, const double2* A, const double2* B, double2* C, double alpha,
+                           int add_identity) {
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i = e / N, j = e % N;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < N; ++k) acc = cadd(acc, cmul(A[i * N + k], B[k * N + j]));
+        double2 r = make_double2(alpha * acc.x, alpha * acc.y);
+        if (add_identity && i == j) r.x += 1.0;
+        C[e] = r;
+    }
+}
+__global__ void __launch_bounds__(256) k_expm_small(int N, double dt, const double2* __restrict__ hA,
+                                                     const double2* __restrict__ hB,
+                                                     double2* __restrict__ U,
+                                                     double* __restrict__ norm_out,
+                                                     int* __restrict__ s_out) {
+    __shared__ double2 X[kExpmSmallN * kExpmSmallN], Y[kExpmSmallN * kExpmSmallN],
+        Z[kExpmSmallN * kExpmSmallN];
+    __shared__ double colsum[kExpmSmallN];
+    const int tid = threadIdx.x, NN = N * N;
+    for (int j = tid; j < N; j += blockDim.x) {
+        double sum = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const int e = i * N + j;
+            const double hr = 0.5 * (hA[e].x + hB[e].x), hi = 0.5 * (hA[e].y + hB[e].y);
+            sum += dt * sqrt(hr * hr + hi * hi);
+        }
+        colsum[j] = sum;
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    for (int j = 0; j < N; ++j) nrm = fmax(nrm, colsum[j]);
+    int s = 0;
+    while (s < 30 && ldexp(nrm, -s) > 0.5) ++s;
+    const double scale = ldexp(1.0, -s);
+    for (int e = tid; e < NN; e += blockDim.x) {
+        const double hr = 0.5 * (hA[e].x + hB[e].x), hi = 0.5 * (hA[e].y + hB[e].y);
+        X[e] = make_double2(scale * dt * hi, -scale * dt * hr);  // -i dt h / 2^s
+        Y[e] = make_double2((e / N == e % N) ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    double2 *y = Y, *z = Z;
+    for (int k = 18; k >= 1; --k) {
+        smem_zgemm(N, X, y, z, 1.0 / k, 1);
+        __syncthreads();
+        double2* t = y; y = z; z = t;
+    }
+    const int nsq = s < 16 ? s : 16;
+    for (int q = 0; q < nsq; ++q) {
+        smem_zgemm(N, y, y, z, 1.0, 0);
+        __syncthreads();
+        double2* t = y; y = z; z = t;
+    }
+    for (int e = tid; e < NN; e += blockDim.x) U[e] = y[e];
+    if (tid == 0) {
+        *norm_out = nrm;
+        *s_out = s;
+    }
+}
+
 // Diagnostics at t_n: {Tr rho, E_total, E_corr, Re Tr I}.
 // E_total = 1/2 (Tr[(h+E d) rho] + Tr[h_HF rho]) + 1/2 Im Tr I.
 __global__ void k_diagnostics(int N, double E, const double2* __restrict__ h,
@@ -564,6 +630,54 @@ __global__ void k_sigma_symm(int N, const double* __restrict__ V, const double2*
     }
 }
 
+// Same for N <= 24, one block per unit with G, Gb, V and r in shared memory:
+//   r[i][l] = sum_k V_ik Gb_lk G_kl = [V x (Gb^T o G)]_il   (N^3)
+//   S_ij    = sum_l V_jl (2 G_ij r[i][l] - G_il sum_k V_ik Gb_lk G_kj)   (N^2 per (i, j))
+constexpr int kSymmSmallN = 24;  // 32 KB of static shared memory
+__global__ void __launch_bounds__(256) k_sigma_symm_small(int N, const double* __restrict__ V,
+                                                           const double2* __restrict__ G,
+                                                           const double2* __restrict__ Gb,
+                                                           double2* __restrict__ S) {
+    __shared__ double2 g[kSymmSmallN * kSymmSmallN], gb[kSymmSmallN * kSymmSmallN],
+        r[kSymmSmallN * kSymmSmallN];
+    __shared__ double vs[kSymmSmallN * kSymmSmallN];
+    const int NN = N * N;
+    const long long base = (long long)blockIdx.x * NN;
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+        g[e] = G[base + e];
+        gb[e] = Gb[base + e];
+        vs[e] = V[e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+        const int i = e / N, l = e % N;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < N; ++k) {
+            const double2 a = cmul(gb[l * N + k], g[k * N + l]);
+            acc = make_double2(fma(vs[i * N + k], a.x, acc.x), fma(vs[i * N + k], a.y, acc.y));
+        }
+        r[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+        const int i = e / N, j = e % N;
+        const double2 gij = g[e];
+        double2 s = make_double2(0.0, 0.0);
+        for (int l = 0; l < N; ++l) {
+            double2 w = make_double2(0.0, 0.0);
+            for (int k = 0; k < N; ++k) {
+                const double2 a = gb[l * N + k];
+                w = cadd(w, cmul(make_double2(vs[i * N + k] * a.x, vs[i * N + k] * a.y), g[k * N + j]));
+            }
+            const double2 b = cmul(gij, r[i * N + l]);
+            const double2 x = cmul(g[i * N + l], w);
+            const double vjl = vs[j * N + l];
+            s = cadd(s, make_double2(vjl * (2.0 * b.x - x.x), vjl * (2.0 * b.y - x.y)));
+        }
+        S[base + e] = s;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -657,6 +771,11 @@ gkba_status expm_step(gkba_ctx* c, const double2* hA, const double2* hB, double2
     double2* X = c->ex0;  // scaled argument B = A / 2^s
     double2* Y = c->ex1;
     double2* Z = c->ex2;
+    if (N <= kExpmSmallN) {
+        auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+        k_expm_small<<<1, 256, 0, c->stream>>>(N, c->dt, hA, hB, U, c->dscal + 8, c->dint + 0);
+        return launch_end(c, t);
+    }
     {
         auto t = launch_begin(c, K_STEP, 0.0, 0.0);
         k_expm_setup<<<1, 256, 0, c->stream>>>(N, c->dt, hA, hB, X, c->dscal + 8, c->dint + 0);
@@ -838,6 +957,11 @@ gkba_status contract_structured(gkba_ctx* c, int nb, const double2* G, const dou
     if (c->kind == GKBA_V_DIAGONAL) {
         auto t = launch_begin(c, K_W1, 6.0 * n * n * nb, 48.0 * n * n * nb);
         k_sigma_diag<<<grid1(nb * NN, 256), 256, 0, c->stream>>>(N, nb, c->vm, G, Gb, c->PQ);
+        GKBA_TRY(launch_end(c, t));
+    } else if (N <= kSymmSmallN) {
+        const int bs = N * N >= 256 ? 256 : ((N * N + 31) / 32) * 32;
+        auto t = launch_begin(c, K_W1, 8.0 * n * n * n * n * nb, 48.0 * n * n * nb);
+        k_sigma_symm_small<<<nb, bs, 0, c->stream>>>(N, c->vm, G, Gb, c->PQ);
         GKBA_TRY(launch_end(c, t));
     } else {
         const int bs = N >= 128 ? 128 : ((N + 31) / 32) * 32;
