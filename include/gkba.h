@@ -85,17 +85,19 @@ typedef struct {
     int max_steps;     /* history capacity: t_0 .. t_{max_steps} (>= 0) */
     int precision;     /* gkba_precision */
     void* cuda_stream; /* cudaStream_t to run on; NULL = the library creates one */
-    size_t workspace_bytes; /* cap on the contraction workspace (0 = default 16 GiB);
+    size_t workspace_bytes; /* cap on the contraction workspace (0 = default 64 GiB, at most
+                               85 % of the free device memory);
                                the batch of (t_k, component) units is sized to fit */
     int device;        /* CUDA device ordinal (-1 = current device) */
     int timing;        /* nonzero: time every contraction kernel with CUDA events
                           (see gkba_get_stats) */
-    int s4_kchunk;     /* GKBA_SPLIT_TF32: length of the FP32 partial sums of the
-                          last contraction (K = N^3) before they are added in
-                          FP64; a multiple of 32, 0 = default (512 for
-                          GKBA_SPLIT_TF32, 64 for GKBA_SPLIT_TF32_ACC).  Shorter chunks
-                          bound the tensor-core accumulation error, longer ones
-                          write fewer partials. */
+    int s4_kchunk;     /* split-TF32 modes: length of the K ranges (K = N^3) the
+                          tensor core accumulates in FP32 in the last contraction
+                          before they are added on the CUDA cores (8 ranges per
+                          FP32 partial, partials summed in FP64); a multiple of 64,
+                          0 = default (512 for GKBA_SPLIT_TF32, 64 for
+                          GKBA_SPLIT_TF32_ACC).  Shorter ranges bound the
+                          tensor-core accumulation error. */
     int interaction;   /* gkba_interaction: form of the v argument of gkba_init;
                           GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC need precision GKBA_FP64 */
 } gkba_config;

@@ -105,7 +105,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const double form_bytes = !gen ? 0.0 : tc ? 4.0 * 2 * Np * Np * 4 : (2.0 * NN + 4.0 * NN) * 8;
     const double N3 = (double)NN * N;
     const double part_per_unit = !gen ? 0.0
-                                 : tc ? (std::ceil((double)Np * Np * Np / c->s4_kchunk) * Np * 2.0 * Np * 4)
+                                 : tc ? (std::ceil((double)Np * Np * Np / (8.0 * c->s4_kchunk)) * Np * 2.0 * Np * 4)
                                       : (std::ceil(N3 / 8192.0) * N * 2.0 * N * 8);
     const double per_unit = 2 * x_bytes + form_bytes + part_per_unit + (4.0 + kReduceSplit) * NN * 16 + 8;
     size_t cap = c->ws_cap;
@@ -341,8 +341,8 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         return fail(nullptr, GKBA_EINVAL, "gkba_init: dt must be positive and finite");
     if (cfg->max_steps < 0 || cfg->max_steps > 100000000)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: max_steps=%d invalid", cfg->max_steps);
-    if (cfg->s4_kchunk < 0 || cfg->s4_kchunk % 32 != 0)
-        return fail(nullptr, GKBA_EINVAL, "gkba_init: s4_kchunk=%d must be a non-negative multiple of 32",
+    if (cfg->s4_kchunk < 0 || cfg->s4_kchunk % 64 != 0)
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: s4_kchunk=%d must be a non-negative multiple of 64",
                     cfg->s4_kchunk);
     if (cfg->precision != GKBA_FP64 && cfg->precision != GKBA_SPLIT_TF32 &&
         cfg->precision != GKBA_SPLIT_TF32_ACC)
@@ -416,7 +416,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     c->max_steps = cfg->max_steps;
     c->prec = cfg->precision;
     c->kind = kind;
-    c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)16 << 30);
+    c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)64 << 30);
     c->timing = cfg->timing != 0;
     c->s4_kchunk = cfg->s4_kchunk > 0 ? cfg->s4_kchunk
                                        : (cfg->precision == GKBA_SPLIT_TF32_ACC ? 64 : 512);

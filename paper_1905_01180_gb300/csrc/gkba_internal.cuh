@@ -52,6 +52,7 @@ struct gkba_ctx {
     bool timing = false;
     int num_sms = 0;
     int pair_clusters = 0;  // co-resident 2-CTA clusters of the stage kernel
+    int fin_pair_clusters = 0;  // same for the S4 kernel
     int kind = GKBA_V_GENERAL;  // gkba_interaction
     double* vm = nullptr;       // U (N) or V (N*N) of a structured interaction
     int s4_kchunk = 512;

@@ -679,12 +679,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
 
 // ---------------------------------------------------------------------------
 // Stage S4: D[(u,c,j)][i] = sum_K X3[(u,c,j)][K] vK[i][K], K = Np^3, split-K.
-// Work item = (group of two 128-row tiles, K range of kKW); B is streamed.
 // ---------------------------------------------------------------------------
 struct FinalParams {
     int Np;
     long long K;
-    int KW;
+    int KW;        // K length of a work item (one FP32 partial per item and row)
     int nks;
     long long rows;
     int ngroups;
@@ -692,42 +691,64 @@ struct FinalParams {
     long long Rld;
     int* err;
     int blocked;   // A is K-blocked: [K/32][Rld rows][32] (3-D map) instead of [rows][K]
+    int KS;        // pair kernel: K length accumulated in TMEM before the epilogue adds it
 };
 
-constexpr int kFinStages = 3;
 constexpr int kFinThreads = 384;
 
-__global__ void __launch_bounds__(kFinThreads, 1)
-    k_tc_final(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-               const __grid_constant__ CUtensorMap tmBlo, const FinalParams p) {
+// ---------------------------------------------------------------------------
+// Stage S4 on CTA pairs: D[(u,c,j)][i] = sum_K X3[(u,c,j)][K] vK[i][K].
+// Work item = (256-row group g: one 128-row tile per CTA, K range of KW).
+// Each CTA stages, per 64-wide K chunk, its A tile (two 32-wide boxes) and its
+// Np/2 rows of vK (hi and lo); the even CTA
+// issues M = 256, N = Np MMAs for the pair.  The accumulator is double
+// buffered: every KS of K the MMAs switch buffers and the epilogue adds the
+// finished FP32 partial (the tensor core's own accumulation covers at most
+// KS terms, which bounds its truncation error) into per-thread register
+// sums, written once per item.  Barrier protocol as in k_tc_pair; a stage is
+// free again when both CTAs' converters have read A and the pair's MMAs have
+// read B (EMPTY count 4 + 1 multicast commit).
+// ---------------------------------------------------------------------------
+constexpr int kFinPairStages = 3;
+constexpr int kFinKC = 2 * kKC;  // K per pipeline chunk: two 32-wide TMA boxes
+constexpr int kFinMaxNp = 96;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
+    k_tc_final_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+                    const __grid_constant__ CUtensorMap tmBlo, const FinalParams p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int Np = p.Np;
-    const uint32_t bbytes = (uint32_t)(Np * 128);
-    const uint32_t stage_bytes = 2 * kTileBytes + 2 * bbytes;
-    uint64_t* bars = (uint64_t*)(smem + kFinStages * stage_bytes);
-    constexpr int FULL = 0, EMPTY = FULL + kFinStages, TFULL = EMPTY + kFinStages,
-                  TEMPTY = TFULL + 2, ACCF = TEMPTY + 2, ACCE = ACCF + 1, DRAIN = ACCE + 1,
+    const int Np = p.Np, Nh = Np / 2;
+    const uint32_t bbytes = (uint32_t)(Nh * 128);  // this CTA's B rows, one 32-wide box
+    const uint32_t stage_bytes = 2 * kTileBytes + 4 * bbytes;  // A0 A1 Bhi0 Bhi1 Blo0 Blo1
+    uint64_t* bars = (uint64_t*)(smem + kFinPairStages * stage_bytes);
+    constexpr int FULL = 0, EMPTY = FULL + kFinPairStages, TFULL = EMPTY + kFinPairStages,
+                  TEMPTY = TFULL + 2, ACCF = TEMPTY + 2, ACCE = ACCF + 2, DRAIN = ACCE + 2,
                   NBARS = DRAIN + 1;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     auto bar = [&](int i) { return smem_u32(bars + i); };
-    auto stA = [&](int s, int t) { return smem + s * stage_bytes + t * kTileBytes; };
-    auto stBhi = [&](int s) { return smem + s * stage_bytes + 2 * kTileBytes; };
-    auto stBlo = [&](int s) { return smem + s * stage_bytes + 2 * kTileBytes + bbytes; };
+    auto stA = [&](int s, int h) { return smem + s * stage_bytes + h * kTileBytes; };
+    auto stBhi = [&](int s, int h) { return smem + s * stage_bytes + 2 * kTileBytes + h * bbytes; };
+    auto stBlo = [&](int s, int h) {
+        return smem + s * stage_bytes + 2 * kTileBytes + (2 + h) * bbytes;
+    };
 
+    const uint32_t rank = cluster_rank();
+    const uint32_t peer_abort = mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
+    auto bar0 = [&](int i) { return mapa_rank(bar(i), 0); };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kFinStages; ++s) {
+        for (int s = 0; s < kFinPairStages; ++s) {
             mbar_init(bar(FULL + s), 1);
-            mbar_init(bar(EMPTY + s), 5);  // 4 converter warps + 1 MMA commit
+            mbar_init(bar(EMPTY + s), 5);  // 4 converter warps + 1 multicast MMA commit
         }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(bar(TFULL + s), 4);
+            mbar_init(bar(TFULL + s), 8);
             mbar_init(bar(TEMPTY + s), 1);
+            mbar_init(bar(ACCF + s), 1);
+            mbar_init(bar(ACCE + s), 8);
         }
-        mbar_init(bar(ACCF), 1);
-        mbar_init(bar(ACCE), 4);
         mbar_init(bar(DRAIN), 1);
         *abort_flag = 0;
         fence_barrier_init();
@@ -738,43 +759,46 @@ __global__ void __launch_bounds__(kFinThreads, 1)
         prefetch_tmap(&tmBlo);
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), 512);
-        tmem_relinquish();
+        tmem_alloc_pair(smem_u32(tmem_slot), 512);
+        tmem_relinquish_pair();
+        tc_fence_before();
     }
     __syncthreads();
+    cluster_sync_all();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem = *tmem_slot;  // accumulators at 0 and 128, A slots at 256 and 384
     const long long items = (long long)p.ngroups * p.nks;
+    const long long ncl = cluster_count_x(), cid = cluster_id_x();
 
     if (warp == 0) {
         if (lane == 0) {
+            // ---------------- TMA producer (both CTAs) ----------------
             long long it = 0;
             bool ok = true;
-            for (long long item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            for (long long item = cid; item < items && ok; item += ncl) {
                 const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
                 const long long k0 = (long long)ks * p.KW;
                 const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-                for (long long k = k0; k < k1; k += kKC, ++it) {
-                    const int s = (int)(it % kFinStages);
-                    const uint32_t ph = (uint32_t)((it / kFinStages) & 1);
-                    if (!mbar_wait(bar(EMPTY + s), ph ^ 1, abort_flag, p.err, 11)) { ok = false; break; }
+                const int row0 = g * 2 * kBM + (int)rank * kBM;
+                for (long long k = k0; k < k1; k += kFinKC, ++it) {
+                    const int s = (int)(it % kFinPairStages);
+                    const uint32_t ph = (uint32_t)((it / kFinPairStages) & 1);
+                    if (!mbar_wait_cl(bar(EMPTY + s), ph ^ 1, abort_flag, peer_abort, p.err, 11)) { ok = false; break; }
                     mbar_expect_tx(bar(FULL + s), stage_bytes);
-                    if (p.blocked) {
-                        tma_3d(smem_u32(stA(s, 0)), &tmA, bar(FULL + s), 0, g * 2 * kBM, (int)(k >> 5));
-                        tma_3d(smem_u32(stA(s, 1)), &tmA, bar(FULL + s), 0, g * 2 * kBM + kBM, (int)(k >> 5));
-                    } else {
-                        tma_2d(smem_u32(stA(s, 0)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM);
-                        tma_2d(smem_u32(stA(s, 1)), &tmA, bar(FULL + s), (int)k, g * 2 * kBM + kBM);
+                    for (int h = 0; h < 2; ++h) {
+                        const int kh = (int)k + h * kKC;
+                        if (p.blocked) tma_3d(smem_u32(stA(s, h)), &tmA, bar(FULL + s), 0, row0, kh >> 5);
+                        else tma_2d(smem_u32(stA(s, h)), &tmA, bar(FULL + s), kh, row0);
+                        tma_2d(smem_u32(stBhi(s, h)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh);
+                        tma_2d(smem_u32(stBlo(s, h)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh);
                     }
-                    tma_2d(smem_u32(stBhi(s)), &tmBhi, bar(FULL + s), (int)k, 0);
-                    tma_2d(smem_u32(stBlo(s)), &tmBlo, bar(FULL + s), (int)k, 0);
                 }
             }
             if (*abort_flag) {
-                for (int s = 0; s < kFinStages; ++s) {
+                for (int s = 0; s < kFinPairStages; ++s) {
                     if (it > s) {
-                        const long long last = it - 1 - ((it - 1 - s) % kFinStages);
-                        const uint32_t ph = (uint32_t)((last / kFinStages) & 1);
+                        const long long last = it - 1 - ((it - 1 - s) % kFinPairStages);
+                        const uint32_t ph = (uint32_t)((last / kFinPairStages) & 1);
                         const unsigned long long g0 = gtimer();
                         while (!mbar_try(bar(FULL + s), ph) && gtimer() - g0 < kWaitLimitNs) {}
                     }
@@ -782,62 +806,71 @@ __global__ void __launch_bounds__(kFinThreads, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            const uint32_t id = idesc_tf32(Np, 0);
-            long long it = 0, item_i = 0;
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer (even CTA, for the pair) ----------------
+            const uint32_t id = idesc_tf32_pair(Np);
+            long long it = 0, sub_i = 0;
             bool ok = true;
-            for (long long item = blockIdx.x; item < items && ok; item += gridDim.x, ++item_i) {
+            for (long long item = cid; item < items && ok; item += ncl) {
                 const int ks = (int)(item / p.ngroups);
                 const long long k0 = (long long)ks * p.KW;
                 const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-                if (!mbar_wait(bar(ACCE), (uint32_t)((item_i & 1) ^ 1), abort_flag, p.err, 12)) { ok = false; break; }
-                tc_fence_after();
-                bool first_chunk = true;
-                for (long long k = k0; k < k1; k += kKC, ++it) {
-                    const int s = (int)(it % kFinStages);
-                    const int slot = (int)(it & 1);
-                    const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                    if (!mbar_wait(bar(TFULL + slot), sph, abort_flag, p.err, 13)) { ok = false; break; }
+                for (long long ksub = k0; ksub < k1 && ok; ksub += p.KS, ++sub_i) {
+                    const int ab = (int)(sub_i & 1);
+                    const uint32_t abph = (uint32_t)((sub_i >> 1) & 1);
+                    if (!mbar_wait_cl(bar(ACCE + ab), abph ^ 1, abort_flag, peer_abort, p.err, 12)) { ok = false; break; }
                     tc_fence_after();
-                    const unsigned long long dh = desc_sw128(smem_u32(stBhi(s)));
-                    const unsigned long long dl = desc_sw128(smem_u32(stBlo(s)));
+                    const uint32_t dacc = tmem + (uint32_t)(ab * 128);
+                    const long long kend = ksub + p.KS < k1 ? ksub + p.KS : k1;
+                    for (long long k = ksub; k < kend; k += kFinKC, ++it) {
+                        const int s = (int)(it % kFinPairStages);
+                        const int slot = (int)(it & 1);
+                        const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                        if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 13)) { ok = false; break; }
+                        tc_fence_after();
+                        // B boxes h = 0, 1 are bbytes apart: descriptor start field + (bbytes >> 4)
+                        const unsigned long long dh = desc_sw128(smem_u32(stBhi(s, 0)));
+                        const unsigned long long dl = desc_sw128(smem_u32(stBlo(s, 0)));
+                        const uint32_t ah0 = tmem + 256u + (uint32_t)(slot * 128);  // hi 64 cols, lo 64 cols
 #pragma unroll 1
-                    for (int q = 0; q < 8; ++q) {  // q = (tile t, K-step kk), compact issue loop
-                        const int t = q >> 2, kk = q & 3;
-                        const uint32_t dacc = tmem + (uint32_t)(t * 128);
-                        const uint32_t ah = tmem + 256u + (uint32_t)(slot * 128 + t * 64) + kk * 8;
-                        const unsigned long long o = 2ull * kk;
-                        mma_tf32(dacc, ah, dh + o, id, (first_chunk && kk == 0) ? 0u : 1u);
-                        mma_tf32(dacc, ah, dl + o, id, 1u);
-                        mma_tf32(dacc, ah + 32, dh + o, id, 1u);
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint32_t ah = ah0 + kk * 8;
+                            const unsigned long long o =
+                                (unsigned long long)((kk >> 2) * (bbytes >> 4)) + 2ull * (kk & 3);
+                            mma_tf32_pair(dacc, ah, dh + o, id, (k == ksub && kk == 0) ? 0u : 1u);
+                            mma_tf32_pair(dacc, ah, dl + o, id, 1u);
+                            mma_tf32_pair(dacc, ah + 64, dh + o, id, 1u);
+                        }
+                        mma_commit_pair(bar(TEMPTY + slot), (uint16_t)3);
+                        mma_commit_pair(bar(EMPTY + s), (uint16_t)3);
                     }
-                    first_chunk = false;
-                    mma_commit(bar(TEMPTY + slot));
-                    mma_commit(bar(EMPTY + s));
+                    if (!ok) break;
+                    mma_commit_pair(bar(ACCF + ab), (uint16_t)3);
                 }
-                if (!ok) break;
-                mma_commit(bar(ACCF));
             }
-            if (*abort_flag) {
-                mma_commit(bar(DRAIN));
-                const unsigned long long g0 = gtimer();
-                while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
-            }
+            // closing commit: no CTA leaves while an MMA reads its memory
+            mma_commit_pair(bar(DRAIN), (uint16_t)3);
+            const unsigned long long g0 = gtimer();
+            while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
+        } else if (lane == 0) {
+            const unsigned long long g0 = gtimer();
+            while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
         }
     } else if (warp >= 4 && warp < 8) {
+        // ---------------- converter: A tile -> TF32 hi/lo in this CTA's TMEM ----------------
         const int wq = warp & 3;
         const int r = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
         long long it = 0;
         bool ok = true;
-        for (long long item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        for (long long item = cid; item < items && ok; item += ncl) {
             const int ks = (int)(item / p.ngroups);
             const long long k0 = (long long)ks * p.KW;
             const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-            for (long long k = k0; k < k1; k += kKC, ++it) {
-                const int s = (int)(it % kFinStages);
-                const uint32_t ph = (uint32_t)((it / kFinStages) & 1);
-                if (!warp_wait(bar(FULL + s), ph, abort_flag, p.err, 14)) { ok = false; break; }
+            for (long long k = k0; k < k1; k += kFinKC, ++it) {
+                const int s = (int)(it % kFinPairStages);
+                const uint32_t ph = (uint32_t)((it / kFinPairStages) & 1);
+                if (!warp_wait_cl(bar(FULL + s), ph, abort_flag, peer_abort, p.err, 14)) { ok = false; break; }
                 uint32_t hi0[32], lo0[32], hi1[32], lo1[32];
                 load_split_row(stA(s, 0), r, hi0, lo0);
                 load_split_row(stA(s, 1), r, hi1, lo1);
@@ -845,49 +878,71 @@ __global__ void __launch_bounds__(kFinThreads, 1)
                 if (lane == 0) mbar_arrive(bar(EMPTY + s));
                 const int slot = (int)(it & 1);
                 const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                if (!warp_wait(bar(TEMPTY + slot), sph ^ 1, abort_flag, p.err, 15)) { ok = false; break; }
+                if (!warp_wait_cl(bar(TEMPTY + slot), sph ^ 1, abort_flag, peer_abort, p.err, 15)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t ta = lane_base + 256u + (uint32_t)(slot * 128);
                 tmem_st32(ta, hi0);
-                tmem_st32(ta + 32, lo0);
-                tmem_st32(ta + 64, hi1);
+                tmem_st32(ta + 32, hi1);
+                tmem_st32(ta + 64, lo0);
                 tmem_st32(ta + 96, lo1);
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(bar(TFULL + slot));
+                if (lane == 0) mbar_arrive_cluster(bar0(TFULL + slot));
             }
         }
     } else if (warp >= 8) {
+        // ---------------- epilogue: sum the buffers of an item, write its partial ----------------
         const int wq = warp & 3;
         const int rloc = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
-        long long item_i = 0;
+        const int nq = Np / 16;
+        long long sub_i = 0;
         bool ok = true;
-        for (long long item = blockIdx.x; item < items && ok; item += gridDim.x, ++item_i) {
+        for (long long item = cid; item < items && ok; item += ncl) {
             const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
-            if (!warp_wait(bar(ACCF), (uint32_t)(item_i & 1), abort_flag, p.err, 16)) { ok = false; break; }
-            tc_fence_after();
-            float* base = p.part + (long long)ks * Np * p.Rld;
-            for (int t = 0; t < 2; ++t) {
-                const long long row = (long long)g * 2 * kBM + t * kBM + rloc;
-                for (int cc = 0; cc < Np / 16; ++cc) {
-                    uint32_t v[16];
-                    tmem_ld16(lane_base + (uint32_t)(t * 128 + cc * 16), v);
-                    tmem_wait_ld();
+            const long long k0 = (long long)ks * p.KW;
+            const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
+            float acc[kFinMaxNp];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) base[(long long)(cc * 16 + j) * p.Rld + row] = __uint_as_float(v[j]);
+            for (int j = 0; j < kFinMaxNp; ++j) acc[j] = 0.0f;
+            for (long long ksub = k0; ksub < k1; ksub += p.KS, ++sub_i) {
+                const int ab = (int)(sub_i & 1);
+                const uint32_t abph = (uint32_t)((sub_i >> 1) & 1);
+                if (!warp_wait_cl(bar(ACCF + ab), abph, abort_flag, peer_abort, p.err, 16)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int q = 0; q < kFinMaxNp / 16; ++q) {
+                    if (q < nq) {
+                        uint32_t v[16];
+                        tmem_ld16(lane_base + (uint32_t)(ab * 128 + q * 16), v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __uint_as_float(v[j]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(bar0(ACCE + ab));
+            }
+            if (!ok) break;
+            float* base = p.part + (long long)ks * Np * p.Rld;
+            const long long row = (long long)g * 2 * kBM + (long long)rank * kBM + rloc;
+#pragma unroll
+            for (int q = 0; q < kFinMaxNp / 16; ++q) {
+                if (q < nq) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) base[(long long)(q * 16 + j) * p.Rld + row] = acc[q * 16 + j];
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(ACCE));
         }
     }
+    tc_fence_before();
     __syncthreads();
+    cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc_pair(tmem, 512);
     }
 }
 
@@ -1014,9 +1069,12 @@ size_t stage_smem_bytes(int Np) {
     const int kch = (Np + kKC - 1) / kKC;
     return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 512;
 }
-size_t final_smem_bytes(int Np) {
-    return 1024 + (size_t)kFinStages * (2 * kTileBytes + 2 * Np * 128) + 512;
+size_t final_pair_smem_bytes(int Np) {
+    return 1024 + (size_t)kFinPairStages * (2 * kTileBytes + 4 * (Np / 2) * 128) + 512;
 }
+// K length of one S4 work item (one partial per item and row) for a TMEM
+// accumulation length kchunk.
+constexpr int kFinSubsPerItem = 8;
 
 }  // namespace
 
@@ -1043,8 +1101,19 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
         if (ncl < 1) return fail(c, GKBA_ECUDA, "no 2-CTA cluster of the stage kernel fits on an SM pair");
         c->pair_clusters = ncl;
     }
-    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)final_smem_bytes(c->Np)));
+    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_final_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)final_pair_smem_bytes(c->Np)));
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(c->num_sms & ~1));
+        cfg.blockDim = dim3(kFinThreads);
+        cfg.dynamicSmemBytes = final_pair_smem_bytes(c->Np);
+        cfg.stream = c->stream;
+        int ncl = 0;
+        GKBA_CUDA(c, cudaOccupancyMaxActiveClusters(&ncl, k_tc_final_pair, &cfg));
+        if (ncl < 1) return fail(c, GKBA_ECUDA, "no 2-CTA cluster of the S4 kernel fits on an SM pair");
+        c->fin_pair_clusters = ncl;
+    }
     return GKBA_OK;
 }
 
@@ -1123,9 +1192,10 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         GKBA_TRY(make_map(c, &mAf, X13, 2, d, s, b));
     }
     {
+        // each CTA of an S4 pair loads Np/2 rows of vK
         cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)Np};
         cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
-        cuuint32_t b[2] = {kKC, (cuuint32_t)Np};
+        cuuint32_t b[2] = {kKC, (cuuint32_t)(Np / 2)};
         GKBA_TRY(make_map(c, &mVh, c->vKhi, 2, d, s, b));
         GKBA_TRY(make_map(c, &mVl, c->vKlo, 2, d, s, b));
     }
@@ -1184,7 +1254,8 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     FinalParams fp{};
     fp.Np = Np;
     fp.K = N3;
-    fp.KW = c->s4_kchunk;
+    fp.KS = c->s4_kchunk;
+    fp.KW = kFinSubsPerItem * c->s4_kchunk;
     fp.nks = (int)((N3 + fp.KW - 1) / fp.KW);
     fp.rows = rows;
     fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
@@ -1198,9 +1269,9 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         return fail(c, GKBA_ESTATE, "partial buffer too small");
     {
         const long long items = (long long)fp.ngroups * fp.nks;
-        const int g = (int)(items < c->num_sms ? items : c->num_sms);
+        const int g = 2 * (int)(items < c->fin_pair_clusters ? items : c->fin_pair_clusters);
         auto t = launch_begin(c, K_FIN, fl_cr * nb, 4.0 * (2 * N4r * nb + 2 * N4r));
-        k_tc_final<<<g, kFinThreads, final_smem_bytes(Np), c->stream>>>(mAf, mVh, mVl, fp);
+        k_tc_final_pair<<<g, kFinThreads, final_pair_smem_bytes(Np), c->stream>>>(mAf, mVh, mVl, fp);
         GKBA_TRY(launch_end(c, t));
     }
     return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
@@ -1208,7 +1279,8 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
 
 size_t tf32_part_bytes(int Np, int ub, int kchunk) {
     const long long N3 = (long long)Np * Np * Np;
-    const long long nks = (N3 + kchunk - 1) / kchunk;
+    const long long kw = (long long)kFinSubsPerItem * kchunk;
+    const long long nks = (N3 + kw - 1) / kw;
     const long long rows = 2LL * Np * ub;
     const long long Rld = ((rows + 255) / 256) * 256;
     return (size_t)(nks * Np * Rld * 4);
