@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="time 32 systems of uneven N and L stacked in one batch vs one by one")
     ap.add_argument("--chains", action="store_true",
                     help="time the Sec. IV propagations at N_b = 10 (Table I context)")
     ap.add_argument("--profile-case", action="store_true",
@@ -264,8 +266,72 @@ def run_chains(a):
               flush=True)
 
 
+def run_batch(a):
+    """Many systems of uneven size and history length: 32 seeded systems with
+    N in {8, 12, 16, 24, 32, 48} and L in U[500, 3000] (then U[20, 200]), one Heun step each
+    (after one warm-up step), split-TF32.  The stacked batch (gkba_batch_step)
+    against the same systems stepped one after another (each alone on the GPU
+    with the default workspace).  Histories: the last L points of one seeded
+    history per N (a valid history of L points)."""
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    for lo, hi in ((500, 3000), (20, 200)):
+        run_batch_case(a, lo, hi)
+
+
+def run_batch_case(a, lo, hi):
+    import torch
+    import gkba_inputs as gi
+    import paper_1905_01180_gb300 as P
+    rng = np.random.default_rng(7)
+    Ns = rng.choice([8, 12, 16, 24, 32, 48], size=32)
+    Ls = rng.integers(lo, hi + 1, size=32)
+    dt = 0.02
+    hist = {int(N): gi.history(int(N), int(Ls[Ns == N].max()) + 2, dt, seed=100 + int(N))
+            for N in sorted(set(Ns.tolist()))}
+
+    def make(i):
+        N, L = int(Ns[i]), int(Ls[i])
+        s = gi.system(N, 8, seed=i)
+        rho, T = hist[N]
+        ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=L + 2, precision="tf32")
+        ctx.set_history(L - 1, rho[-L:], T[-L:])
+        return ctx
+
+    # units of the timed step: history of n + 1 = L + 1 and n + 2 points (after the warm-up)
+    flops = float(sum(2 * (2 * (int(L) + 1) + 1) * 24.0 * int(N) ** 5 for N, L in zip(Ns, Ls)))
+    ctxs = [make(i) for i in range(32)]
+    with P.Batch(ctxs) as bt:
+        bt.step(0.0, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt.step(0.0, 0.0)
+        t_batch = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    t_seq = 0.0
+    for i in range(32):
+        c = make(i)
+        c.step(0.0, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.step(0.0, 0.0)
+        t_seq += time.perf_counter() - t0
+        c.close()
+    print(json.dumps({"workload": f"32_systems_N8-48_L{lo}-{hi}_one_step",
+                      "metric": "contraction TFLOP/s over one Heun step of all systems",
+                      "value": flops / t_batch / 1e12, "unit": "TFLOP/s", "higher_is_better": True,
+                      "batched_s": t_batch, "one_by_one_s": t_seq, "speedup": t_seq / t_batch,
+                      "one_by_one_tflops": flops / t_seq / 1e12, "precision": "split_tf32",
+                      "N": sorted(Ns.tolist()), "L_range": [int(Ls.min()), int(Ls.max())],
+                      "algorithmic_flops": flops}), flush=True)
+
+
 def main():
     a = parse()
+    if a.batch:
+        run_batch(a)
+        return
     if a.chains:
         run_chains(a)
         return

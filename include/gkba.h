@@ -246,6 +246,36 @@ gkba_status gkba_sigma_noalloc(int N, int n_units, const double* v, const double
                                const double* Gbar, double* S_out, void* cuda_stream, char* err,
                                size_t err_len);
 
+/*
+ * Stacked batches of systems: many systems of uneven basis size and history
+ * length advanced together.  The (t_k, component) units of all systems of the
+ * same N share each launch of the contraction kernels (per system only the w
+ * and v layouts differ, and the kernels select them per unit); the per-system
+ * N^2 / N^3 work (mean field, propagator, Heun update) runs per system.
+ *
+ * gkba_batch_create - ctxs: n_ctx distinct contexts made by gkba_init with
+ *   the same split-TF32 precision and s4_kchunk, the general interaction and
+ *   the same device.  They stay owned by the caller and must outlive the
+ *   batch; during gkba_batch_step every member runs on the batch's stream.
+ *   workspace_bytes caps the stacked workspaces of all groups together (0 =
+ *   64 GiB, each group at most 85 % of the free device memory).  Returns
+ *   GKBA_EINVAL for other contexts, GKBA_ENOMEM when a group's workspace does
+ *   not fit.
+ * gkba_batch_step - one Heun step (as gkba_step) of every member; E_n and
+ *   E_np1 hold n_ctx field samples; rho_out and diag_out are arrays of n_ctx
+ *   host pointers (the arrays or their entries may be NULL).  A member whose
+ *   history is full fails the whole call with GKBA_ESTATE before any work.
+ * gkba_batch_last_error - message of the last failing batch call (NULL batch:
+ *   the last failed gkba_batch_create).
+ */
+typedef struct gkba_batch gkba_batch;
+gkba_status gkba_batch_create(gkba_batch** out, gkba_ctx* const* ctxs, int n_ctx,
+                              size_t workspace_bytes);
+gkba_status gkba_batch_step(gkba_batch* batch, const double* E_n, const double* E_np1,
+                            double* const* rho_out, double* const* diag_out);
+const char* gkba_batch_last_error(const gkba_batch* batch);
+void gkba_batch_destroy(gkba_batch* batch);
+
 /* Message for the last failing call on ctx (or the last failed gkba_init when ctx is NULL). */
 const char* gkba_last_error(const gkba_ctx* ctx);
 

@@ -3,4 +3,4 @@
 The compute path lives in the C-ABI library libgkba.so (include/gkba.h,
 CUDA kernels for sm_103a under csrc/); ``gkba`` is its Python binding.
 """
-from .gkba import Context, GKBAError, load, FP64, SPLIT_TF32, SPLIT_TF32_ACC  # noqa: F401
+from .gkba import Batch, Context, GKBAError, load, FP64, SPLIT_TF32, SPLIT_TF32_ACC  # noqa: F401

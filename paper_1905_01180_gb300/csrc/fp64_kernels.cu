@@ -852,6 +852,40 @@ gkba_status build_forms_gkba(gkba_ctx* c, int k0, int nk, int L, const double2* 
     return build_forms(c, 2 * nk, c->Su, NN, c->Mb, NN, 0);
 }
 
+// Units of history points k0 .. k0+nk-1 of one system (history of L points,
+// trapezoid weights with dt when w is null) written to G / Gb / coef (unit
+// stride N*N), with c->PQ as scratch.  Used by stacked batches of systems.
+gkba_status units_from_history(gkba_ctx* c, int N, int k0, int nk, int L, double dt,
+                               const double2* rho, const double2* T, const double* w, double2* G,
+                               double2* Gb, double* coef) {
+    const long long NN = (long long)N * N;
+    double2* P = c->PQ;
+    double2* Q = c->PQ + (long long)nk * NN;
+    GKBA_TRY(zgemm_batched(c, K_PREP, N, 'N', 'N', make_double2(1.0, 0.0), T + k0 * NN, NN,
+                           rho + k0 * NN, NN, make_double2(0.0, 0.0), P, NN, nk, 0));
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_lincomb<<<grid1(nk * NN, 256), 256, 0, c->stream>>>(nk * NN, Q, T + k0 * NN, P, 1.0, -1.0);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_gkba_units<<<grid1(nk * NN, 256), 256, 0, c->stream>>>(N, nk, k0, L, dt, P, Q, w, G, Gb, coef);
+    return launch_end(c, t);
+}
+
+// I += sum_u coef[u] Y[u] over nb units of one system (N x N), two passes.
+gkba_status weighted_sum_units(gkba_ctx* c, int N, int nb, const double* coef, const double2* Y,
+                               double2* I) {
+    const long long NN = (long long)N * N;
+    const int nz = nb < kWsumRanges ? nb : kWsumRanges;
+    const int per = (nb + nz - 1) / nz;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_weighted_sum_p1<<<dim3(grid1(NN, 128), nz), 128, 0, c->stream>>>((int)NN, nb, per, coef, Y,
+                                                                       c->red_tmp);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_weighted_sum_p2<<<grid1(NN, 256), 256, 0, c->stream>>>((int)NN, nz, c->red_tmp, I);
+    return launch_end(c, t);
+}
+
 gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
     const long long NN = (long long)c->N * c->N;
     auto t = launch_begin(c, K_PREP, 0.0, 0.0);

@@ -736,3 +736,361 @@ const char* gkba_last_error(const gkba_ctx* c) {
 void gkba_destroy(gkba_ctx* c) { free_ctx(c); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Stacked batches of systems (many systems of uneven N and history length).
+// Systems of the same N form a group; the (t_k, component) units of all
+// systems of a group are stacked into shared launches of the contraction
+// kernels.  Per system only the w layout (S1's A) and the v layout (S4's B)
+// differ; both sit in group buffers [system][...] that the kernels index with
+// a per-unit system table.  Each system's units are padded with zero units
+// (G = Gbar = 0, coefficient 0) to a multiple of 256 / gcd(256, 2 Np) so that
+// no 256-row group of S4 straddles two systems.
+// ---------------------------------------------------------------------------
+struct gkba_batch {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<gkba_ctx*> ctx;  // members (owned by the caller)
+    struct Group {
+        int N = 0;
+        std::vector<int> members;  // indices into ctx
+        gkba_ctx* sh = nullptr;    // workspace, group layouts and stream of the group
+        int pu = 1;                // unit padding quantum
+        int* sys_dev = nullptr;    // unit -> system (group-local index), per collision
+        int* sys_host[2] = {nullptr, nullptr};  // pinned staging, one per collision of a step
+        long long sys_cap = 0;
+    };
+    std::vector<Group> groups;
+};
+
+namespace {
+
+gkba_status batch_fail(gkba_batch* b, gkba_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    std::lock_guard<std::mutex> g(g_err_mu);
+    g_last_init_error = buf;
+    return st;
+}
+
+void free_batch(gkba_batch* b) {
+    if (!b) return;
+    if (b->device >= 0) cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto& g : b->groups) {
+        if (g.sys_dev) cudaFree(g.sys_dev);
+        for (int i = 0; i < 2; ++i)
+            if (g.sys_host[i]) cudaFreeHost(g.sys_host[i]);
+        if (g.sh) {
+            g.sh->stream = nullptr;  // the batch's stream, destroyed below
+            free_ctx(g.sh);
+        }
+    }
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// Collision integrals of every member of group g over its own history (L =
+// n + 1 points with T = T_a, or n + 2 points with T = T_b), into Ia or Ib.
+gkba_status batch_collision(gkba_batch* b, gkba_batch::Group& g, int which) {
+    gkba_ctx* sh = g.sh;
+    const int N = g.N;
+    const long long NN = (long long)N * N;
+    struct Seg {
+        gkba_ctx* c;
+        int L;
+        const double2* T;
+        double2* I;
+        long long u0;   // first unit in the group's stacked list
+        long long nu;   // real units 2 L
+        long long np;   // padded units
+    };
+    std::vector<Seg> segs;
+    long long total = 0;
+    for (int m : g.members) {
+        gkba_ctx* c = b->ctx[m];
+        Seg s;
+        s.c = c;
+        s.L = which == 0 ? c->n + 1 : c->n + 2;
+        s.T = which == 0 ? c->T_a : c->T_b;
+        s.I = which == 0 ? c->Ia : c->Ib;
+        s.u0 = total;
+        s.nu = 2LL * s.L;
+        s.np = ((s.nu + g.pu - 1) / g.pu) * g.pu;
+        total += s.np;
+        GKBA_CUDA(sh, cudaMemsetAsync(s.I, 0, NN * sizeof(double2), sh->stream));
+        segs.push_back(s);
+    }
+    if (total > g.sys_cap) {
+        if (g.sys_dev) cudaFree(g.sys_dev);
+        for (int i = 0; i < 2; ++i)
+            if (g.sys_host[i]) cudaFreeHost(g.sys_host[i]);
+        g.sys_dev = nullptr;
+        g.sys_host[0] = g.sys_host[1] = nullptr;
+        g.sys_cap = 0;
+        // one device table per collision of a step (the first may still be read)
+        if (cudaMalloc(&g.sys_dev, 2 * total * sizeof(int)) != cudaSuccess ||
+            cudaMallocHost(&g.sys_host[0], total * sizeof(int)) != cudaSuccess ||
+            cudaMallocHost(&g.sys_host[1], total * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(sh, GKBA_ENOMEM, "batch: unit table allocation failed");
+        }
+        g.sys_cap = total;
+    }
+    int* host = g.sys_host[which];
+    int* dev = g.sys_dev + (long long)which * g.sys_cap;
+    for (size_t i = 0; i < segs.size(); ++i)
+        for (long long u = 0; u < segs[i].np; ++u) host[segs[i].u0 + u] = (int)i;
+    GKBA_CUDA(sh, cudaMemcpyAsync(dev, host, total * sizeof(int), cudaMemcpyHostToDevice, sh->stream));
+    const long long ub = sh->ub;
+    for (long long U0 = 0; U0 < total; U0 += ub) {
+        const long long nb = std::min(ub, total - U0);
+        for (auto& s : segs) {
+            const long long a = std::max(U0, s.u0), e = std::min(U0 + nb, s.u0 + s.np);
+            if (a >= e) continue;
+            const long long ra = a - s.u0, re = e - s.u0;  // units of this system in the batch
+            const long long off = a - U0;                  // their offset in the batch
+            const long long real_end = std::min(re, s.nu);
+            if (ra < real_end) {
+                const int k0 = (int)(ra / 2), nk = (int)((real_end - ra) / 2);
+                GKBA_TRY(units_from_history(sh, N, k0, nk, s.L, s.c->dt, s.c->rho_hist, s.T,
+                                            nullptr, sh->Su + off * NN, sh->Mb + off * NN,
+                                            sh->coef + off));
+            }
+            const long long pad0 = std::max(ra, s.nu);
+            if (pad0 < re) {
+                const long long po = off + (pad0 - ra), pn = re - pad0;
+                GKBA_CUDA(sh, cudaMemsetAsync(sh->Su + po * NN, 0, pn * NN * sizeof(double2), sh->stream));
+                GKBA_CUDA(sh, cudaMemsetAsync(sh->Mb + po * NN, 0, pn * NN * sizeof(double2), sh->stream));
+                GKBA_CUDA(sh, cudaMemsetAsync(sh->coef + po, 0, pn * sizeof(double), sh->stream));
+            }
+        }
+        GKBA_TRY(build_forms_tf32(sh, (int)nb, sh->Su, sh->Mb));
+        sh->unit_sys = dev + U0;
+        const gkba_status st = contract_batch_tf32(sh, (int)nb);
+        sh->unit_sys = nullptr;
+        GKBA_TRY(st);
+        GKBA_TRY(zgemm_batched(sh, K_RED, N, 'N', 'N', make_double2(1.0, 0.0), sh->Su, NN, sh->Mb,
+                               NN, make_double2(0.0, 0.0), sh->Yu, NN, (int)nb, 0));
+        for (auto& s : segs) {
+            const long long a = std::max(U0, s.u0), e = std::min(U0 + nb, s.u0 + s.nu);
+            if (a >= e) continue;
+            GKBA_TRY(weighted_sum_units(sh, N, (int)(e - a), sh->coef + (a - U0),
+                                        sh->Yu + (a - U0) * NN, s.I));
+        }
+    }
+    return GKBA_OK;
+}
+
+// One Heun step of every member (the sequence of gkba_step, with both
+// collision integrals of all members evaluated in stacked launches).
+gkba_status batch_step(gkba_batch* b, const double* E_n, const double* E_np1,
+                       double* const* rho_out, double* const* diag_out) {
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        gkba_ctx* c = b->ctx[i];
+        const long long NN = (long long)c->N * c->N;
+        GKBA_TRY(h_hf(c, E_n[i], c->rho_hist + c->n * NN, c->hhf_n));
+    }
+    for (auto& g : b->groups) GKBA_TRY(batch_collision(b, g, 0));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        gkba_ctx* c = b->ctx[i];
+        const int n = c->n;
+        const long long NN = (long long)c->N * c->N;
+        double2* rho_n = c->rho_hist + n * NN;
+        double2* rho_t = c->rho_hist + (n + 1) * NN;
+        GKBA_TRY(diagnostics(c, E_n[i], rho_n, c->Ia, c->dscal));
+        GKBA_TRY(rhs(c, c->hhf_n, rho_n, c->Ia, c->k1));
+        GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k1, 1.0, c->dt, (int)NN));
+        GKBA_TRY(h_hf(c, E_np1[i], rho_t, c->hhf_t));
+        GKBA_TRY(expm_step(c, c->hhf_n, c->hhf_t, c->U));
+        GKBA_TRY(zgemm_batched(c, K_STEP, c->N, 'N', 'N', make_double2(1.0, 0.0), c->U, 0, c->T_a,
+                               NN, make_double2(0.0, 0.0), c->T_b, NN, n + 1, 0));
+        GKBA_TRY(set_identity(c, c->T_b + (n + 1) * NN, 1));
+    }
+    for (auto& g : b->groups) GKBA_TRY(batch_collision(b, g, 1));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        gkba_ctx* c = b->ctx[i];
+        const int n = c->n;
+        const long long NN = (long long)c->N * c->N;
+        double2* rho_n = c->rho_hist + n * NN;
+        double2* rho_t = c->rho_hist + (n + 1) * NN;
+        GKBA_TRY(rhs(c, c->hhf_t, rho_t, c->Ib, c->k2));
+        GKBA_TRY(axpy_c(c, c->k2, c->k1, c->k2, 1.0, 1.0, (int)NN));
+        GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k2, 1.0, 0.5 * c->dt, (int)NN));
+        std::swap(c->T_a, c->T_b);
+        c->n = n + 1;
+        if (rho_out && rho_out[i])
+            GKBA_CUDA(c, cudaMemcpyAsync(rho_out[i], rho_t, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+        if (diag_out && diag_out[i])
+            GKBA_CUDA(c, cudaMemcpyAsync(c->hdiag, c->dscal, 4 * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return GKBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gkba_status gkba_batch_create(gkba_batch** out, gkba_ctx* const* ctxs, int n_ctx,
+                              size_t workspace_bytes) {
+    if (out) *out = nullptr;
+    if (!out || !ctxs || n_ctx < 1)
+        return batch_fail(nullptr, GKBA_EINVAL, "gkba_batch_create: out, ctxs and n_ctx >= 1 required");
+    for (int i = 0; i < n_ctx; ++i) {
+        gkba_ctx* c = ctxs[i];
+        if (!c) return batch_fail(nullptr, GKBA_EINVAL, "gkba_batch_create: context %d is NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c)
+                return batch_fail(nullptr, GKBA_EINVAL, "gkba_batch_create: context %d listed twice", i);
+        if (!tensor_core_path(c) || c->kind != GKBA_V_GENERAL)
+            return batch_fail(nullptr, GKBA_EINVAL,
+                              "gkba_batch_create: context %d is not a split-TF32 general-basis context", i);
+        if (c->prec != ctxs[0]->prec || c->device != ctxs[0]->device || c->s4_kchunk != ctxs[0]->s4_kchunk)
+            return batch_fail(nullptr, GKBA_EINVAL,
+                              "gkba_batch_create: contexts differ in precision, device or s4_kchunk");
+    }
+    gkba_batch* b = new gkba_batch();
+    b->device = ctxs[0]->device;
+    b->ctx.assign(ctxs, ctxs + n_ctx);
+    auto bail = [&](gkba_status st) {
+        free_batch(b);
+        return st;
+    };
+    if (cudaSetDevice(b->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(batch_fail(nullptr, GKBA_ECUDA, "gkba_batch_create: stream creation failed"));
+    }
+    for (int i = 0; i < n_ctx; ++i) {
+        int gi = -1;
+        for (size_t k = 0; k < b->groups.size(); ++k)
+            if (b->groups[k].N == ctxs[i]->N) gi = (int)k;
+        if (gi < 0) {
+            b->groups.emplace_back();
+            b->groups.back().N = ctxs[i]->N;
+            gi = (int)b->groups.size() - 1;
+        }
+        b->groups[gi].members.push_back(i);
+    }
+    const size_t cap_total = workspace_bytes ? workspace_bytes : ((size_t)64 << 30);
+    for (auto& g : b->groups) {
+        gkba_ctx* c0 = ctxs[g.members[0]];
+        gkba_ctx* sh = new gkba_ctx();
+        g.sh = sh;
+        sh->N = g.N;
+        sh->Np = c0->Np;
+        sh->prec = c0->prec;
+        sh->dt = c0->dt;
+        sh->device = b->device;
+        sh->stream = b->stream;
+        sh->num_sms = c0->num_sms;
+        sh->pair_clusters = c0->pair_clusters;
+        sh->fin_pair_clusters = c0->fin_pair_clusters;
+        sh->s4_kchunk = c0->s4_kchunk;
+        sh->ws_cap = cap_total / b->groups.size();
+        sh->nsys = (int)g.members.size();
+        const long long Np = sh->Np, Np4 = Np * Np * Np * Np;
+        const size_t lay = (size_t)sh->nsys * Np4 * 4;
+        if (cudaMalloc(&sh->dint, 16) != cudaSuccess || cudaMalloc(&sh->wS32, lay) != cudaSuccess ||
+            cudaMalloc(&sh->vKhi, lay) != cudaSuccess || cudaMalloc(&sh->vKlo, lay) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(batch_fail(nullptr, GKBA_ENOMEM, "gkba_batch_create: layout allocation failed"));
+        }
+        cudaMemsetAsync(sh->dint, 0, 16, b->stream);
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            gkba_ctx* c = ctxs[g.members[k]];
+            cudaStreamSynchronize(c->stream);
+            cudaMemcpyAsync(sh->wS32 + k * Np4, c->wS32, Np4 * 4, cudaMemcpyDeviceToDevice, b->stream);
+            cudaMemcpyAsync(sh->vKhi + k * Np4, c->vKhi, Np4 * 4, cudaMemcpyDeviceToDevice, b->stream);
+            cudaMemcpyAsync(sh->vKlo + k * Np4, c->vKlo, Np4 * 4, cudaMemcpyDeviceToDevice, b->stream);
+        }
+        const long long rows = 2 * Np;
+        long long gcd = 256, r = rows;
+        while (r) {
+            const long long t = gcd % r;
+            gcd = r;
+            r = t;
+        }
+        g.pu = (int)(256 / gcd);
+        // the largest collision of the group: every member at a full history
+        long long want = 0;
+        for (int m : g.members)
+            want += ((2LL * (ctxs[m]->max_steps + 1) + g.pu - 1) / g.pu) * g.pu;
+        gkba_status st = ensure_workspace(sh, (int)std::min<long long>(want, 1 << 30));
+        if (st != GKBA_OK) {
+            batch_fail(nullptr, st, "gkba_batch_create: %s", sh->err.c_str());
+            return bail(st);
+        }
+        sh->ub = (sh->ub / g.pu) * g.pu;
+        if (sh->ub < g.pu)
+            return bail(batch_fail(nullptr, GKBA_ENOMEM,
+                                   "gkba_batch_create: workspace holds fewer than %d units at N=%d", g.pu, g.N));
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(batch_fail(nullptr, GKBA_ECUDA, "gkba_batch_create: device copies failed"));
+    }
+    *out = b;
+    return GKBA_OK;
+}
+
+gkba_status gkba_batch_step(gkba_batch* b, const double* E_n, const double* E_np1,
+                            double* const* rho_out, double* const* diag_out) {
+    if (!b) return batch_fail(nullptr, GKBA_EINVAL, "gkba_batch_step: NULL batch");
+    if (!E_n || !E_np1) return batch_fail(b, GKBA_EINVAL, "gkba_batch_step: NULL field samples");
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        if (!std::isfinite(E_n[i]) || !std::isfinite(E_np1[i]))
+            return batch_fail(b, GKBA_EINVAL, "gkba_batch_step: non-finite field sample for system %zu", i);
+        if (b->ctx[i]->n >= b->ctx[i]->max_steps)
+            return batch_fail(b, GKBA_ESTATE, "gkba_batch_step: history of system %zu is full", i);
+    }
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+        cudaGetLastError();
+        return batch_fail(b, GKBA_ECUDA, "gkba_batch_step: cudaSetDevice failed");
+    }
+    // members run on the batch's stream for the duration of the step
+    std::vector<cudaStream_t> saved(b->ctx.size());
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        cudaStreamSynchronize(b->ctx[i]->stream);
+        saved[i] = b->ctx[i]->stream;
+        b->ctx[i]->stream = b->stream;
+    }
+    gkba_status st = batch_step(b, E_n, E_np1, rho_out, diag_out);
+    const cudaError_t se = cudaStreamSynchronize(b->stream);
+    for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->stream = saved[i];
+    if (st != GKBA_OK) {
+        for (gkba_ctx* c : b->ctx)
+            if (!c->err.empty()) b->err = c->err;
+        for (auto& g : b->groups)
+            if (!g.sh->err.empty()) b->err = g.sh->err;
+        return st;
+    }
+    if (se != cudaSuccess) return batch_fail(b, GKBA_ECUDA, "gkba_batch_step: %s", cudaGetErrorString(se));
+    for (auto& g : b->groups) {
+        int errw = 0;
+        if (cudaMemcpy(&errw, g.sh->dint + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return batch_fail(b, GKBA_ECUDA, "gkba_batch_step: error word read failed");
+        if (errw != 0) {
+            cudaMemset(g.sh->dint + 1, 0, sizeof(int));
+            return batch_fail(b, GKBA_ETIMEOUT, "gkba_batch_step: device-side wait timed out (code %d)", errw);
+        }
+    }
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+        if (diag_out && diag_out[i]) memcpy(diag_out[i], b->ctx[i]->hdiag, 4 * 8);
+    return GKBA_OK;
+}
+
+const char* gkba_batch_last_error(const gkba_batch* b) {
+    if (b) return b->err.c_str();
+    std::lock_guard<std::mutex> g(g_err_mu);
+    return g_last_init_error.c_str();
+}
+
+void gkba_batch_destroy(gkba_batch* b) { free_batch(b); }
+
+}  // extern "C"

@@ -54,6 +54,10 @@ struct gkba_ctx {
     int pair_clusters = 0;  // co-resident 2-CTA clusters of the stage kernel
     int fin_pair_clusters = 0;  // same for the S4 kernel
     int kind = GKBA_V_GENERAL;  // gkba_interaction
+    // Stacked batches of several systems (gkba_batch): wS32 / vKhi / vKlo hold
+    // nsys systems' layouts and unit_sys (device) maps each unit to its system.
+    const int* unit_sys = nullptr;
+    int nsys = 1;
     double* vm = nullptr;       // U (N) or V (N*N) of a structured interaction
     int s4_kchunk = 512;
 
@@ -226,6 +230,11 @@ gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG,
 gkba_status build_forms_gkba(gkba_ctx* c, int k0, int nk, int L, const double2* rho,
                              const double2* T, const double* w);
 gkba_status reduce_batch(gkba_ctx* c, int nb, double2* I_acc, double2* S_out);
+gkba_status units_from_history(gkba_ctx* c, int N, int k0, int nk, int L, double dt,
+                               const double2* rho, const double2* T, const double* w, double2* G,
+                               double2* Gb, double* coef);
+gkba_status weighted_sum_units(gkba_ctx* c, int N, int nb, const double* coef, const double2* Y,
+                               double2* I);
 gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
 gkba_status build_forms_tf32(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,

@@ -365,6 +365,7 @@ struct StageParams {
     long long M;       // rows = Np^3
     int units;         // units in the batch
     int a_unit;        // A has a unit coordinate (S2/S3) or is shared (S1)
+    const int* unit_sys;  // batches of several systems: unit -> system (3-D S1 map), else null
     float* out;
     long long out_unit;
     StageMap map;
@@ -497,6 +498,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     mbar_expect_tx(bar(AFULL + s), kTileBytes);
                     const uint32_t dst = smem_u32(sA + s * kTileBytes);
                     if (p.a_unit) tma_4d(dst, &tmA, bar(AFULL + s), kc * kKC, pl, (int)row0, u);
+                    else if (p.unit_sys) tma_3d(dst, &tmA, bar(AFULL + s), kc * kKC, (int)row0, p.unit_sys[u]);
                     else tma_2d(dst, &tmA, bar(AFULL + s), kc * kKC, (int)row0);
                 }
             }
@@ -549,8 +551,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     const uint32_t ahi = tmem + (slot ? 448u : 192u);
                     const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
                     const unsigned long long dl = dBlo0 + ((unsigned long long)(c * chunkB) >> 4);
+                    // the last chunk of a plane holds Np % 32 = 16 valid K when Np is an odd
+                    // multiple of 16 (the rest is the TMA's zero fill): skip its zero K steps
+                    const int kvalid = Np - (c % p.kch) * kKC;
+                    const int ksteps = kvalid >= kKC ? 4 : kvalid / 8;
 #pragma unroll 1
-                    for (int kk = 0; kk < 4; ++kk) {
+                    for (int kk = 0; kk < ksteps; ++kk) {
                         const uint32_t ah = ahi + kk * 8, al = ah + 32;
                         const unsigned long long o = 2ull * kk;
                         mma_tf32_pair(dacc, ah, dh + o, id, (c | kk) ? 1u : 0u);
@@ -692,6 +698,7 @@ struct FinalParams {
     int* err;
     int blocked;   // A is K-blocked: [K/32][Rld rows][32] (3-D map) instead of [rows][K]
     int KS;        // pair kernel: K length accumulated in TMEM before the epilogue adds it
+    const int* unit_sys;  // batches of several systems: unit -> system (3-D vK maps), else null
 };
 
 constexpr int kFinThreads = 384;
@@ -780,6 +787,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                 const long long k0 = (long long)ks * p.KW;
                 const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
                 const int row0 = g * 2 * kBM + (int)rank * kBM;
+                // a 256-row group never straddles two systems (their units are padded)
+                const int sys = p.unit_sys ? p.unit_sys[(g * 2 * kBM) / (2 * Np)] : 0;
                 for (long long k = k0; k < k1; k += kFinKC, ++it) {
                     const int s = (int)(it % kFinPairStages);
                     const uint32_t ph = (uint32_t)((it / kFinPairStages) & 1);
@@ -789,8 +798,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                         const int kh = (int)k + h * kKC;
                         if (p.blocked) tma_3d(smem_u32(stA(s, h)), &tmA, bar(FULL + s), 0, row0, kh >> 5);
                         else tma_2d(smem_u32(stA(s, h)), &tmA, bar(FULL + s), kh, row0);
-                        tma_2d(smem_u32(stBhi(s, h)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh);
-                        tma_2d(smem_u32(stBlo(s, h)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh);
+                        if (p.unit_sys) {
+                            tma_3d(smem_u32(stBhi(s, h)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh, sys);
+                            tma_3d(smem_u32(stBlo(s, h)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh, sys);
+                        } else {
+                            tma_2d(smem_u32(stBhi(s, h)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh);
+                            tma_2d(smem_u32(stBlo(s, h)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh);
+                        }
                     }
                 }
             }
@@ -1065,6 +1079,7 @@ gkba_status make_map(gkba_ctx* c, CUtensorMap* m, const void* base, int rank, co
     return GKBA_OK;
 }
 
+constexpr int kMaxTcNp = 96;  // largest padded basis of the tensor-core path
 size_t stage_smem_bytes(int Np) {
     const int kch = (Np + kKC - 1) / kKC;
     return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 512;
@@ -1087,9 +1102,11 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
     t = launch_begin(c, K_PREP, 0.0, 0.0);
     k_build_vK32<<<grid1(Np4, 256), 256, 0, c->stream>>>(c->N, c->Np, c->v, c->vKhi, c->vKlo);
     GKBA_TRY(launch_end(c, t));
+    // The shared-memory limit is a property of the kernel, not of a context:
+    // set it for the largest basis so that contexts of different N coexist.
     for (auto kfn : {k_tc_pair<false>, k_tc_pair<true>})
         GKBA_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)stage_smem_bytes(c->Np)));
+                                          (int)stage_smem_bytes(kMaxTcNp)));
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(c->num_sms & ~1));
@@ -1102,7 +1119,7 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
         c->pair_clusters = ncl;
     }
     GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_final_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)final_pair_smem_bytes(c->Np)));
+                                      (int)final_pair_smem_bytes(kMaxTcNp)));
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(c->num_sms & ~1));
@@ -1154,7 +1171,13 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     const double N4r = Nr * Nr * Nr * Nr;
 
     CUtensorMap mA1, mA23_in1, mA23_in2, mB1h, mB1l, mGh, mGl, mAf, mVh, mVl;
-    {
+    const bool multi = c->unit_sys != nullptr;  // several systems: w and v per system
+    if (multi) {
+        cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)N3, (cuuint64_t)c->nsys};
+        cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)(N4 * 4)};
+        cuuint32_t b[3] = {kKC, kBM, 1};
+        GKBA_TRY(make_map(c, &mA1, c->wS32, 3, d, s, b));
+    } else {
         cuuint64_t d[2] = {(cuuint64_t)Np, (cuuint64_t)N3};
         cuuint64_t s[1] = {(cuuint64_t)Np * 4};
         cuuint32_t b[2] = {kKC, kBM};
@@ -1191,7 +1214,13 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         cuuint32_t b[2] = {kKC, kBM};
         GKBA_TRY(make_map(c, &mAf, X13, 2, d, s, b));
     }
-    {
+    if (multi) {
+        cuuint64_t d[3] = {(cuuint64_t)N3, (cuuint64_t)Np, (cuuint64_t)c->nsys};
+        cuuint64_t s[2] = {(cuuint64_t)N3 * 4, (cuuint64_t)(N4 * 4)};
+        cuuint32_t b[3] = {kKC, (cuuint32_t)(Np / 2), 1};
+        GKBA_TRY(make_map(c, &mVh, c->vKhi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &mVl, c->vKlo, 3, d, s, b));
+    } else {
         // each CTA of an S4 pair loads Np/2 rows of vK
         cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)Np};
         cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
@@ -1211,10 +1240,12 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     sp.M = N3;
     sp.units = nb;
     sp.out_unit = 2 * N4;
+    sp.unit_sys = nullptr;
     sp.err = err;
     // S1: rows (j,m,q), cols (c,r) -> X1[j][r][m][c][q]
     sp.planes = 1;
     sp.a_unit = 0;
+    sp.unit_sys = c->unit_sys;
     sp.out = X13;
     sp.map = StageMap{2 * N3, 2 * Np, 1, Np, 2 * N2, Np, Np, Np};
     {
@@ -1225,6 +1256,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     // S2: rows (j,r,m), K (c,q), cols (c',p) -> X2[j][r][p][c'][m]
     sp.planes = 2;
     sp.a_unit = 1;
+    sp.unit_sys = nullptr;
     sp.out = X2;
     sp.map = StageMap{2 * N3, 2 * N2, 1, Np, 2 * Np, Np, Np, Np};
     {
@@ -1263,6 +1295,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     fp.blocked = blocked ? 1 : 0;
     fp.part = (float*)c->part;
     fp.err = err;
+    fp.unit_sys = c->unit_sys;
     if (blocked && (size_t)(N3 * Rld * 4) > c->x13_bytes)
         return fail(c, GKBA_ESTATE, "X3 buffer too small for the K-blocked layout");
     if ((size_t)fp.nks * Np * fp.Rld * 4 > c->part_bytes)

@@ -29,7 +29,8 @@ _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIME
 
 EXPORTED = ["gkba_init", "gkba_sigma", "gkba_collision", "gkba_step", "gkba_set_history",
             "gkba_get_history", "gkba_get_state", "gkba_mean_field", "gkba_adjoint",
-            "gkba_get_stats", "gkba_last_error", "gkba_destroy", "gkba_sigma_noalloc"]
+            "gkba_get_stats", "gkba_last_error", "gkba_destroy", "gkba_sigma_noalloc",
+            "gkba_batch_create", "gkba_batch_step", "gkba_batch_last_error", "gkba_batch_destroy"]
 
 
 class GKBAError(RuntimeError):
@@ -80,8 +81,15 @@ def load():
     L.gkba_destroy.argtypes = [P]
     L.gkba_destroy.restype = None
     L.gkba_sigma_noalloc.argtypes = [I, I, P, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
+    L.gkba_batch_create.argtypes = [ctypes.POINTER(P), P, I, ctypes.c_size_t]
+    L.gkba_batch_step.argtypes = [P, P, P, P, P]
+    L.gkba_batch_last_error.argtypes = [P]
+    L.gkba_batch_last_error.restype = ctypes.c_char_p
+    L.gkba_batch_destroy.argtypes = [P]
+    L.gkba_batch_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("gkba_last_error", "gkba_destroy"):
+        if name not in ("gkba_last_error", "gkba_destroy", "gkba_batch_last_error",
+                        "gkba_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -252,3 +260,53 @@ class Context:
     def adjoint(self, *a, **k):
         st = load().gkba_adjoint(self._h, None, 0, 0, None, None, None)
         self._check(st)
+
+
+class Batch:
+    """Several Contexts (split-TF32, general interaction) advanced together:
+    the history contractions of all systems of the same N share each kernel
+    launch (gkba_batch_*).  The contexts stay usable on their own afterwards."""
+
+    def __init__(self, contexts, workspace_bytes=0):
+        L = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        handle = ctypes.c_void_p()
+        st = L.gkba_batch_create(ctypes.byref(handle), ctypes.cast(arr, ctypes.c_void_p),
+                                 len(self.contexts), int(workspace_bytes))
+        if st != OK:
+            raise GKBAError(st, L.gkba_batch_last_error(None).decode())
+        self._h = handle
+
+    def step(self, E_n, E_np1):
+        """One Heun step of every member; returns (list of rho, list of diagnostics)."""
+        n = len(self.contexts)
+        En = np.ascontiguousarray(np.broadcast_to(np.asarray(E_n, np.float64), (n,)))
+        Enp = np.ascontiguousarray(np.broadcast_to(np.asarray(E_np1, np.float64), (n,)))
+        rhos = [np.empty((c.N, c.N), np.complex128) for c in self.contexts]
+        diags = [np.empty(4, np.float64) for _ in self.contexts]
+        rp = (ctypes.c_void_p * n)(*[r.ctypes.data for r in rhos])
+        dp = (ctypes.c_void_p * n)(*[d.ctypes.data for d in diags])
+        L = load()
+        st = L.gkba_batch_step(self._h, En.ctypes.data, Enp.ctypes.data,
+                               ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(dp, ctypes.c_void_p))
+        if st != OK:
+            raise GKBAError(st, L.gkba_batch_last_error(self._h).decode())
+        return rhos, diags
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gkba_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

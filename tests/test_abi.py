@@ -105,6 +105,19 @@ def test_init_rejects_bad_structured_interactions(lib):
     assert st == gkba.EINVAL and "non-finite" in msg
 
 
+def test_batch_create_rejects_bad_arguments(lib):
+    # host-side validation of gkba_batch_create, before any device work
+    from paper_1905_01180_gb300 import gkba
+    out = ctypes.c_void_p()
+    assert lib.gkba_batch_create(ctypes.byref(out), None, 0, 0) == gkba.EINVAL
+    arr = (ctypes.c_void_p * 2)(None, None)
+    st = lib.gkba_batch_create(ctypes.byref(out), ctypes.cast(arr, ctypes.c_void_p), 2, 0)
+    assert st == gkba.EINVAL and out.value is None
+    assert b"NULL" in lib.gkba_batch_last_error(None)
+    assert lib.gkba_batch_step(None, None, None, None, None) == gkba.EINVAL
+    lib.gkba_batch_destroy(None)
+
+
 def test_null_context_calls_fail_cleanly(lib):
     from paper_1905_01180_gb300 import gkba
     assert lib.gkba_collision(None, 1, None, None, None, None, 0) == gkba.EINVAL

@@ -326,6 +326,18 @@ def test_checkpoint_resume_bitwise(P):
         x.close()
 
 
+def test_contexts_of_different_sizes_coexist(P):
+    # kernel attributes are per kernel, not per context: a smaller context
+    # created after a larger one must not break the larger one's launches
+    big = ctx_for(P, 48, n_P=8, seed=1, precision="tf32")
+    small = ctx_for(P, 8, n_P=4, seed=2, precision="tf32")
+    for (s, ctx), N in ((big, 48), (small, 8)):
+        rho, T = gi.history(N, 2, 0.02, seed=3)
+        I = ctx.collision(rho, T)
+        assert np.isfinite(I).all() and np.abs(I).max() > 0
+        ctx.close()
+
+
 def test_tf32_rejects_large_basis(P):
     s = gi.system(4, 4, seed=0)
     N = 100
