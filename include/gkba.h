@@ -276,6 +276,17 @@ gkba_status gkba_batch_step(gkba_batch* batch, const double* E_n, const double* 
 const char* gkba_batch_last_error(const gkba_batch* batch);
 void gkba_batch_destroy(gkba_batch* batch);
 
+/*
+ * gkba_selftest_timeout - failure detection without a GPU fault: runs a
+ * 2-CTA kernel whose even CTA waits, with the bounded wait of the contraction
+ * kernels and a limit of limit_ms (0 < limit_ms <= 1000), on a barrier that
+ * nothing arrives at; the odd CTA must leave early on its peer's abort flag.
+ * Returns GKBA_ETIMEOUT (the error word the expired wait wrote, read as after
+ * every call), elapsed_ms[0..1] (may be NULL) = each CTA's time in its wait.
+ * The context stays usable.
+ */
+gkba_status gkba_selftest_timeout(gkba_ctx* ctx, double limit_ms, double* elapsed_ms);
+
 /* Message for the last failing call on ctx (or the last failed gkba_init when ctx is NULL). */
 const char* gkba_last_error(const gkba_ctx* ctx);
 

@@ -193,6 +193,7 @@ gkba_status ensure_stage(gkba_ctx* c, size_t bytes) {
 // One batch of nb units: (G_u, Gb_u) at G, Gb (stride N*N; the general paths
 // read the forms built from them) -> S_u in c->Su.
 static gkba_status contract(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
+    NvtxRange r("gkba contraction batch");
     if (c->kind != GKBA_V_GENERAL) return contract_structured(c, nb, G, Gb);
     if (tensor_core_path(c)) return contract_batch_tf32(c, nb);
     return contract_batch_fp64(c, nb);
@@ -200,6 +201,7 @@ static gkba_status contract(gkba_ctx* c, int nb, const double2* G, const double2
 
 gkba_status collision_dev(gkba_ctx* c, int L, const double2* rho, const double2* T,
                           const double* weights_dev, double2* I_out) {
+    NvtxRange r("gkba collision");
     const long long NN = (long long)c->N * c->N;
     GKBA_CUDA(c, cudaMemsetAsync(I_out, 0, NN * sizeof(double2), c->stream));
     if (L <= 1 && weights_dev == nullptr) return GKBA_OK;  // zero-length time interval
@@ -628,6 +630,7 @@ gkba_status gkba_step(gkba_ctx* c, double E_n, double E_np1, double* rho_out, do
     if (c->n >= c->max_steps)
         return fail(c, GKBA_ESTATE, "gkba_step: history full (n=%d, max_steps=%d)", c->n, c->max_steps);
     GKBA_CUDA(c, cudaSetDevice(c->device));
+    NvtxRange r("gkba_step");
     const int n = c->n;
     const long long NN = (long long)c->N * c->N;
     double2* rho_n = c->rho_hist + n * NN;
@@ -727,6 +730,15 @@ gkba_status gkba_get_stats(gkba_ctx* c, gkba_kernel_stat* stats, int max_stats, 
     return GKBA_OK;
 }
 
+gkba_status gkba_selftest_timeout(gkba_ctx* c, double limit_ms, double* elapsed_ms) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_selftest_timeout: NULL context");
+    if (!(limit_ms > 0.0) || limit_ms > 1000.0)
+        return fail(c, GKBA_EINVAL, "gkba_selftest_timeout: limit_ms must be in (0, 1000]");
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    GKBA_TRY(wait_selftest(c, limit_ms, elapsed_ms));
+    return finish(c);  // reads the error word the expired wait wrote: GKBA_ETIMEOUT
+}
+
 const char* gkba_last_error(const gkba_ctx* c) {
     if (c) return c->err.c_str();
     std::lock_guard<std::mutex> g(g_err_mu);
@@ -798,6 +810,7 @@ void free_batch(gkba_batch* b) {
 // Collision integrals of every member of group g over its own history (L =
 // n + 1 points with T = T_a, or n + 2 points with T = T_b), into Ia or Ib.
 gkba_status batch_collision(gkba_batch* b, gkba_batch::Group& g, int which) {
+    NvtxRange nr("gkba batch collision");
     gkba_ctx* sh = g.sh;
     const int N = g.N;
     const long long NN = (long long)N * N;
@@ -1060,7 +1073,11 @@ gkba_status gkba_batch_step(gkba_batch* b, const double* E_n, const double* E_np
         saved[i] = b->ctx[i]->stream;
         b->ctx[i]->stream = b->stream;
     }
-    gkba_status st = batch_step(b, E_n, E_np1, rho_out, diag_out);
+    gkba_status st;
+    {
+        NvtxRange nr("gkba_batch_step");
+        st = batch_step(b, E_n, E_np1, rho_out, diag_out);
+    }
     const cudaError_t se = cudaStreamSynchronize(b->stream);
     for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->stream = saved[i];
     if (st != GKBA_OK) {

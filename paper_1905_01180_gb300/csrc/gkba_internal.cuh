@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gkba.h"
 
 namespace gkba {
@@ -30,6 +32,14 @@ enum KernelClass : int {
 };
 
 extern const char* kKernelClassNames[K_COUNT];
+
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct TimedLaunch {
     int cls;
@@ -240,6 +250,8 @@ gkba_status build_forms_tf32(gkba_ctx* c, int nb, const double2* G, const double
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
                                    const void* part, bool fp32, double2* S);
 size_t tf32_part_bytes(int Np, int ub, int kchunk);
+// Launch the bounded-wait self-test (a wait that must run out); elapsed_ms[2].
+gkba_status wait_selftest(gkba_ctx* c, double limit_ms, double* elapsed_ms);
 
 // Workspace sizing: make sure the workspace holds ub units (returns actual ub).
 gkba_status ensure_workspace(gkba_ctx* c, int want_units);

@@ -177,14 +177,15 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v
 // Bounded wait of the CTA-pair kernel; on timeout it raises this CTA's and the
 // peer CTA's abort flags (peer_abort: shared::cluster address).
 __device__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                             uint32_t peer_abort, int* err, int code) {
+                             uint32_t peer_abort, int* err, int code,
+                             unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*abort_flag) return false;
-            if (gtimer() - t0 > kWaitLimitNs) {
+            if (gtimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 st_cluster_u32(peer_abort, 1u);
                 atomicCAS(err, 0, code);
@@ -961,6 +962,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Self-test of the bounded waits (failure detection without a GPU fault): a
+// 2-CTA cluster whose even CTA waits, with the waits of the contraction
+// kernels (mbar_wait_cl) and a short limit, on an mbarrier that nothing
+// arrives at.  Its wait runs out, records `code` in the error word and
+// raises both CTAs' abort flags; the odd CTA, waiting on its own barrier with
+// a 100x longer limit, must leave on its peer's flag.  No TMA, no tensor
+// memory; every loop is bounded.
+// ---------------------------------------------------------------------------
+__global__ void __cluster_dims__(2, 1, 1) k_wait_selftest(int* err, unsigned long long limit_ns,
+                                                          unsigned long long* elapsed_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_s;
+    volatile int* abort_flag = &abort_s;
+    const uint32_t rank = cluster_rank();
+    const uint32_t peer_abort = mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    cluster_sync_all();
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = gtimer();
+        const unsigned long long lim = rank == 0 ? limit_ns : 100ull * limit_ns;
+        (void)mbar_wait_cl(smem_u32(&bar), 0, abort_flag, peer_abort, err, 90 + (int)rank, lim);
+        elapsed_ns[rank] = gtimer() - t0;
+    }
+    __syncthreads();
+    cluster_sync_all();  // no remote store is in flight when either CTA leaves
+}
+
+// ---------------------------------------------------------------------------
 // Operand preparation kernels
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
@@ -1308,6 +1342,25 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         GKBA_TRY(launch_end(c, t));
     }
     return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
+}
+
+gkba_status wait_selftest(gkba_ctx* c, double limit_ms, double* elapsed_ms) {
+    unsigned long long* el = nullptr;
+    GKBA_CUDA(c, cudaMalloc(&el, 2 * sizeof(unsigned long long)));
+    GKBA_CUDA(c, cudaMemsetAsync(el, 0, 2 * sizeof(unsigned long long), c->stream));
+    k_wait_selftest<<<2, 32, 0, c->stream>>>(c->dint + 1, (unsigned long long)(limit_ms * 1e6), el);
+    const cudaError_t le = cudaGetLastError();
+    unsigned long long h[2] = {0, 0};
+    const cudaError_t ce = cudaMemcpyAsync(h, el, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(el);
+    if (le != cudaSuccess || ce != cudaSuccess)
+        return fail(c, GKBA_ECUDA, "wait self-test: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
+    if (elapsed_ms) {
+        elapsed_ms[0] = h[0] * 1e-6;
+        elapsed_ms[1] = h[1] * 1e-6;
+    }
+    return GKBA_OK;
 }
 
 size_t tf32_part_bytes(int Np, int ub, int kchunk) {

@@ -30,7 +30,8 @@ _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIME
 EXPORTED = ["gkba_init", "gkba_sigma", "gkba_collision", "gkba_step", "gkba_set_history",
             "gkba_get_history", "gkba_get_state", "gkba_mean_field", "gkba_adjoint",
             "gkba_get_stats", "gkba_last_error", "gkba_destroy", "gkba_sigma_noalloc",
-            "gkba_batch_create", "gkba_batch_step", "gkba_batch_last_error", "gkba_batch_destroy"]
+            "gkba_batch_create", "gkba_batch_step", "gkba_batch_last_error", "gkba_batch_destroy",
+            "gkba_selftest_timeout"]
 
 
 class GKBAError(RuntimeError):
@@ -82,6 +83,7 @@ def load():
     L.gkba_destroy.restype = None
     L.gkba_sigma_noalloc.argtypes = [I, I, P, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
     L.gkba_batch_create.argtypes = [ctypes.POINTER(P), P, I, ctypes.c_size_t]
+    L.gkba_selftest_timeout.argtypes = [P, D, P]
     L.gkba_batch_step.argtypes = [P, P, P, P, P]
     L.gkba_batch_last_error.argtypes = [P]
     L.gkba_batch_last_error.restype = ctypes.c_char_p
@@ -256,6 +258,12 @@ class Context:
                                           flops=arr[i].flops, bytes=arr[i].bytes)
                for i in range(n.value)}
         return out, tot.value
+
+    def selftest_timeout(self, limit_ms=50.0):
+        """Run the bounded-wait self-test; returns (status, elapsed_ms of both CTAs)."""
+        el = np.zeros(2, np.float64)
+        st = load().gkba_selftest_timeout(self._h, float(limit_ms), el.ctypes.data)
+        return st, el
 
     def adjoint(self, *a, **k):
         st = load().gkba_adjoint(self._h, None, 0, 0, None, None, None)

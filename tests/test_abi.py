@@ -116,6 +116,7 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert b"NULL" in lib.gkba_batch_last_error(None)
     assert lib.gkba_batch_step(None, None, None, None, None) == gkba.EINVAL
     lib.gkba_batch_destroy(None)
+    assert lib.gkba_selftest_timeout(None, 10.0, None) == gkba.EINVAL
 
 
 def test_null_context_calls_fail_cleanly(lib):
