@@ -247,6 +247,30 @@ gkba_status gkba_sigma_noalloc(int N, int n_units, const double* v, const double
                                size_t err_len);
 
 /*
+ * gkba_sigma3 - the trilinear form behind Eq. (2bse) with its two G slots
+ * separated: S3(A, B, C)_ij = sum v_irpn w_mqsj A_nm B_sr C_pq, so that
+ * S(G, Gb) = S3(G, Gb, G).  n_units triples of N*N complex matrices; runs on
+ * the context's precision path (general interaction only: GKBA_EUNSUPPORTED
+ * otherwise).  Used by the adjoint: every derivative of S is an S3 value.
+ */
+gkba_status gkba_sigma3(gkba_ctx* ctx, int n_units, const double* A, const double* B,
+                        const double* C, double* S_out, int on_device);
+
+/*
+ * gkba_collision_vjp - adjoint (vector-Jacobian product) of gkba_collision:
+ * for a real loss L(I) and I_bar = dL/dRe I + i dL/dIm I (N*N complex),
+ * returns rho_bar and T_bar (L*N*N complex each, same convention) for the
+ * same history and weights (NULL: trapezoid).  The derivative of each slot of
+ * Eq. (2bse) is evaluated as an S3 value on the context's precision path,
+ * chained through P_k = T_k rho_k, Q_k = T_k - P_k and the products with
+ * P_k^+ / Q_k^+ in FP64.  General interaction only (GKBA_EUNSUPPORTED
+ * otherwise).  Costs about four collision integrals.
+ */
+gkba_status gkba_collision_vjp(gkba_ctx* ctx, int L, const double* rho_hist, const double* T_hist,
+                               const double* weights, const double* I_bar, double* rho_bar,
+                               double* T_bar, int on_device);
+
+/*
  * Stacked batches of systems: many systems of uneven basis size and history
  * length advanced together.  The (t_k, component) units of all systems of the
  * same N share each launch of the contraction kernels (per system only the w

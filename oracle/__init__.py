@@ -39,6 +39,7 @@ __all__ = [
     "sigma_bruteforce",
     "sigma_paper",
     "sigma_independent",
+    "sigma3",
     "sigma_hubbard",
     "sigma_symmetric",
     "sigma_bubble",
@@ -47,6 +48,7 @@ __all__ = [
     "self_energies",
     "trapezoid_weights",
     "collision",
+    "collision_vjp",
     "hf_self_energy",
     "expm_hermitian",
     "Propagation",
@@ -146,6 +148,25 @@ def sigma_independent(v, G, Gb):
     return S if batched else S[0]
 
 
+def sigma3(v, A, B, C):
+    """Eq. (2bse) with its two G slots given separate matrices:
+
+    S3(A, B, C)_ij = sum_{mnpqrs} v_irpn w_mqsj A_nm B_sr C_pq,
+
+    so that S(G, Gbar) = S3(G, Gbar, G).  The same four-step ordering as
+    ``sigma_independent``.  Batched over a leading axis.
+    """
+    batched = A.ndim == 3
+    if not batched:
+        A, B, C = A[None], B[None], C[None]
+    w = exchange_folded(v)
+    W1 = np.einsum("mqsj,bsr->bmqrj", w, B, optimize=True)
+    W2 = np.einsum("bpq,bmqrj->bmprj", C, W1, optimize=True)
+    W3 = np.einsum("bnm,bmprj->bnprj", A, W2, optimize=True)
+    S = np.einsum("irpn,bnprj->bij", v, W3, optimize=True)
+    return S if batched else S[0]
+
+
 def sigma_hubbard(U, G, Gb):
     """Diagonal basis, Eq. (2b-diag): Sigma_ij = U_i U_j G_ij Gb_ji G_ij
     for v_ijkl = U_i delta_ij delta_ik delta_il."""
@@ -237,6 +258,53 @@ def collision(v, rho_hist, T_hist, weights, route="independent", chunk=256):
         terms = Sg @ Gl_kt - Sl @ Gg_kt
         I += np.einsum("k,kij->ij", c, terms)
     return I
+
+
+def collision_vjp(v, rho_hist, T_hist, weights, Ibar):
+    """Reverse-mode derivative of ``collision`` (first line of Eq. collint).
+
+    For a real loss L(I) and gradients written as real pairs (Xbar =
+    dL/dRe X + i dL/dIm X, so that dL = Re sum conj(Xbar) dX), returns
+    (rho_bar, T_bar), each L x N x N, for a given Ibar.  It is the chain rule
+    through
+        I   = sum_k c_k [S(Q_k, P_k^+) P_k^+ - S(P_k, Q_k^+) Q_k^+],
+        P_k = T_k rho_k,  Q_k = T_k - P_k,
+    where Y = S Gbar gives Sbar = Ybar Gbar^+ and Gbar-bar = S^+ Ybar, a
+    conjugate transpose Gbar = X^+ gives Xbar = (Gbar-bar)^+, and each slot of
+    Eq. (2bse), S_ij = sum v_irpn w_mqsj G_nm Gb_sr G_pq (holomorphic in G and
+    Gb, v and w real), is differentiated by writing out its sum with the
+    differentiated factor left open and the others conjugated.
+    """
+    L, N, _ = rho_hist.shape
+    w = exchange_folded(v)
+    eye = np.eye(N)
+    rho_bar = np.zeros((L, N, N), np.complex128)
+    T_bar = np.zeros((L, N, N), np.complex128)
+    for k in range(L):
+        T, rho, c = T_hist[k], rho_hist[k], weights[k]
+        P = T @ rho
+        Q = T - P
+        Pbar = np.zeros((N, N), np.complex128)
+        Qbar = np.zeros((N, N), np.complex128)
+        # unit 0: -c S(P, Q^+) Q^+ ; unit 1: +c S(Q, P^+) P^+
+        for G, Gb, coef, first in ((P, Q.conj().T, -c, True), (Q, P.conj().T, c, False)):
+            S = sigma_independent(v, G, Gb)
+            Ybar = coef * Ibar
+            Sbar = Ybar @ Gb.conj().T
+            Gb_bar = S.conj().T @ Ybar
+            Gc, Gbc = G.conj(), Gb.conj()
+            Gb_bar = Gb_bar + np.einsum("irpn,mqsj,nm,pq,ij->sr", v, w, Gc, Gc, Sbar, optimize=True)
+            G_bar = (np.einsum("irpn,mqsj,sr,pq,ij->nm", v, w, Gbc, Gc, Sbar, optimize=True)
+                     + np.einsum("irpn,mqsj,nm,sr,ij->pq", v, w, Gc, Gbc, Sbar, optimize=True))
+            if first:
+                Pbar += G_bar
+                Qbar += Gb_bar.conj().T
+            else:
+                Qbar += G_bar
+                Pbar += Gb_bar.conj().T
+        rho_bar[k] = T.conj().T @ (Pbar - Qbar)
+        T_bar[k] = Pbar @ rho.conj().T + Qbar @ (eye - rho).conj().T
+    return rho_bar, T_bar
 
 
 def hf_self_energy(v, rho):

@@ -384,11 +384,13 @@ __global__ void k_forms64(int N, int nb, const double2* __restrict__ G, const do
     const int u = (int)(e / NN);
     const int rr = (int)(e % NN);
     const int a = rr / N, b = rr % N;
-    // stage-1 operand: entry (s = a, r = b)
-    const double2 gb = Gb[u * NN + rr];  // Gb[s][r]
-    double* b1 = B1 + (long long)u * 2 * NN;
-    b1[(long long)(0 * N + b) * N + a] = gb.x;
-    b1[(long long)(1 * N + b) * N + a] = gb.y;
+    // stage-1 operand: entry (s = a, r = b); skipped when only the G forms are wanted
+    if (B1 != nullptr) {
+        const double2 gb = Gb[u * NN + rr];  // Gb[s][r]
+        double* b1 = B1 + (long long)u * 2 * NN;
+        b1[(long long)(0 * N + b) * N + a] = gb.x;
+        b1[(long long)(1 * N + b) * N + a] = gb.y;
+    }
     // stage-2/3 operand: entry (p = a, q = b)
     const double2 g = G[u * NN + rr];
     double* gr = Gr + (long long)u * 4 * NN;
@@ -678,6 +680,58 @@ __global__ void __launch_bounds__(256) k_sigma_symm_small(int N, const double* _
     }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the collision integral: per-unit elementwise steps.
+// ---------------------------------------------------------------------------
+// out_u = op(in_u) for N x N units: conjugate and/or transpose.
+__global__ void k_unit_xform(int N, long long n_el, const double2* __restrict__ in,
+                             double2* __restrict__ out, int conj, int transpose) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const long long NN = (long long)N * N, u = e / NN;
+    const int rr = (int)(e % NN), i = rr / N, j = rr % N;
+    double2 x = in[u * NN + (transpose ? (long long)j * N + i : rr)];
+    if (conj) x.y = -x.y;
+    out[e] = x;
+}
+// y_u += x_u (or x_u^T)
+__global__ void k_unit_acc(int N, long long n_el, double2* __restrict__ y,
+                           const double2* __restrict__ x, int transpose) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    const long long NN = (long long)N * N, u = e / NN;
+    const int rr = (int)(e % NN), i = rr / N, j = rr % N;
+    const double2 a = x[u * NN + (transpose ? (long long)j * N + i : rr)];
+    y[e].x += a.x;
+    y[e].y += a.y;
+}
+// Ybar_u = coef_u Ibar (I = sum_u coef_u Y_u with real coefficients)
+__global__ void k_scale_units(int N, int nb, const double* __restrict__ coef,
+                              const double2* __restrict__ Ibar, double2* __restrict__ Y) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)N * N;
+    if (e >= NN * nb) return;
+    const double c = coef[e / NN];
+    const double2 b = Ibar[e % NN];
+    Y[e] = make_double2(c * b.x, c * b.y);
+}
+// Per history point k (units 2k: G = P, Gb = Q^+; 2k+1: G = Q, Gb = P^+):
+//   Pbar = Gbar_(2k) + (Gbbar_(2k+1))^+,  Qbar = Gbar_(2k+1) + (Gbbar_(2k))^+
+__global__ void k_vjp_points(int N, int nk, const double2* __restrict__ Gbar,
+                             const double2* __restrict__ Gbbar, double2* __restrict__ Pbar,
+                             double2* __restrict__ Qbar) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)N * N;
+    if (e >= NN * nk) return;
+    const long long k = e / NN;
+    const int rr = (int)(e % NN), i = rr / N, j = rr % N;
+    const long long tr = (long long)j * N + i;
+    const double2 g0 = Gbar[(2 * k) * NN + rr], g1 = Gbar[(2 * k + 1) * NN + rr];
+    const double2 b0 = Gbbar[(2 * k) * NN + tr], b1 = Gbbar[(2 * k + 1) * NN + tr];
+    Pbar[e] = make_double2(g0.x + b1.x, g0.y - b1.y);
+    Qbar[e] = make_double2(g1.x + b0.x, g1.y - b0.y);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -886,11 +940,46 @@ gkba_status weighted_sum_units(gkba_ctx* c, int N, int nb, const double* coef, c
     return launch_end(c, t);
 }
 
+gkba_status unit_xform(gkba_ctx* c, int nb, const double2* in, double2* out, int conj, int transpose) {
+    const long long n = (long long)nb * c->N * c->N;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_unit_xform<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, n, in, out, conj, transpose);
+    return launch_end(c, t);
+}
+gkba_status unit_acc(gkba_ctx* c, int nb, double2* y, const double2* x, int transpose) {
+    const long long n = (long long)nb * c->N * c->N;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_unit_acc<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, n, y, x, transpose);
+    return launch_end(c, t);
+}
+gkba_status scale_units(gkba_ctx* c, int nb, const double* coef, const double2* Ibar, double2* Y) {
+    const long long n = (long long)nb * c->N * c->N;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_scale_units<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, nb, coef, Ibar, Y);
+    return launch_end(c, t);
+}
+gkba_status vjp_points(gkba_ctx* c, int nk, const double2* Gbar, const double2* Gbbar, double2* Pbar,
+                       double2* Qbar) {
+    const long long n = (long long)nk * c->N * c->N;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_vjp_points<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, nk, Gbar, Gbbar, Pbar, Qbar);
+    return launch_end(c, t);
+}
+
 gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
     const long long NN = (long long)c->N * c->N;
     auto t = launch_begin(c, K_PREP, 0.0, 0.0);
     k_forms64<<<grid1(nb * NN, 256), 256, 0, c->stream>>>(c->N, nb, G, Gb, (double*)c->formsB1,
                                                           (double*)c->formsG);
+    return launch_end(c, t);
+}
+
+// G forms of stage S3 from a separate matrix A (trilinear S3(A, B, C)).
+gkba_status build_forms3_fp64(gkba_ctx* c, int nb, const double2* A) {
+    const long long NN = (long long)c->N * c->N;
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_forms64<<<grid1(nb * NN, 256), 256, 0, c->stream>>>(c->N, nb, A, nullptr, nullptr,
+                                                          (double*)c->formsG3);
     return launch_end(c, t);
 }
 
@@ -965,7 +1054,8 @@ gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
     }
     {
         StageMap m{N3, N, 1, N4, N2, N, N, N};
-        GKBA_TRY(gemm64_stage(c, K_W3, X2, 2 * N, 2 * N4, (const double*)c->formsG, 2 * N, 4 * N2,
+        GKBA_TRY(gemm64_stage(c, K_W3, X2, 2 * N, 2 * N4,
+                              (const double*)(c->sep_A ? c->formsG3 : c->formsG), 2 * N, 4 * N2,
                               X13, 2 * N4, (int)N3, 2 * N, 2 * N, nb, 0, 0, m, fl_cc * nb,
                               8.0 * 4 * N4 * nb));
     }

@@ -145,6 +145,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const size_t oPart = cv.take(part_bytes);
     const size_t oB1 = cv.take(!gen ? 0 : tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(2LL * NN * ub * 8));
     const size_t oG = cv.take(!gen ? 0 : tc ? (size_t)(2LL * 4 * Np * Np * ub * 4) : (size_t)(4LL * NN * ub * 8));
+    const size_t oG3 = cv.take(!gen ? 0 : tc ? (size_t)(2LL * 4 * Np * Np * ub * 4) : (size_t)(4LL * NN * ub * 8));
     const size_t oPQ = cv.take((size_t)(ub * NN * 16));
     const size_t oMb = cv.take((size_t)(ub * NN * 16));
     const size_t oCoef = cv.take((size_t)ub * 8);
@@ -168,6 +169,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     c->part_bytes = part_bytes;
     c->formsB1 = b + oB1;
     c->formsG = b + oG;
+    c->formsG3 = b + oG3;
     c->PQ = (double2*)(b + oPQ);
     c->Mb = (double2*)(b + oMb);
     c->coef = (double*)(b + oCoef);
@@ -224,6 +226,97 @@ gkba_status sigma_dev(gkba_ctx* c, int n_units, const double2* G, const double2*
         GKBA_TRY(build_forms(c, nb, G + u0 * NN, NN, Gb + u0 * NN, NN, 0));
         GKBA_TRY(contract(c, nb, G + u0 * NN, Gb + u0 * NN));
         GKBA_TRY(reduce_batch(c, nb, nullptr, S_out + u0 * NN));
+    }
+    return GKBA_OK;
+}
+
+// S3(A_u, B_u, C_u) of nb units (device, stride N*N) into c->Su: the
+// contraction chain with B in stage S1's slot, C in S2's and A in S3's.
+static gkba_status contract3(gkba_ctx* c, int nb, const double2* A, const double2* B,
+                             const double2* C) {
+    const long long NN = (long long)c->N * c->N;
+    GKBA_TRY(build_forms(c, nb, C, NN, B, NN, 0));
+    if (A != C) {
+        GKBA_TRY(tensor_core_path(c) ? build_forms3_tf32(c, nb, A) : build_forms3_fp64(c, nb, A));
+        c->sep_A = true;
+    }
+    const gkba_status st = contract(c, nb, C, B);
+    c->sep_A = false;
+    return st;
+}
+
+gkba_status sigma3_dev(gkba_ctx* c, int n_units, const double2* A, const double2* B,
+                       const double2* C, double2* S_out) {
+    const long long NN = (long long)c->N * c->N;
+    GKBA_TRY(ensure_workspace(c, n_units));
+    for (int u0 = 0; u0 < n_units; u0 += c->ub) {
+        const int nb = std::min(c->ub, n_units - u0);
+        GKBA_TRY(contract3(c, nb, A + u0 * NN, B + u0 * NN, C + u0 * NN));
+        GKBA_CUDA(c, cudaMemcpyAsync(S_out + u0 * NN, c->Su, nb * NN * sizeof(double2),
+                                     cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return GKBA_OK;
+}
+
+// Reverse mode of collision_dev: given Ibar (device, N*N), rho_bar and
+// T_bar (device, L*N*N) for the L history points.  Gradients are real pairs
+// (dL/dRe + i dL/dIm).  Per batch of units (G_u, Gb_u) with coefficient c_u:
+//   Ybar = c_u Ibar;  Sbar = Ybar Gb^+;  Gbbar = S^+ Ybar (from Y = S Gb)
+//   Gbbar += S3(G*, Sbar^T, G*)^T                      (S's Gb slot)
+//   Gbar   = S3(Sbar, G*^T, Gb*^T) + S3(Gb*^T, G*^T, Sbar)  (its two G slots)
+// (the slot derivatives of Eq. (2bse) written as S3 evaluations, valid for
+// w = 2v - v_exch with v 8-fold symmetric); then
+//   Pbar = Gbar(P slot) + Gbbar(P^+ slot)^+,  Qbar likewise,
+//   rho_bar = T^+ (Pbar - Qbar),  T_bar = (Pbar - Qbar) rho^+ + Qbar.
+gkba_status collision_vjp_dev(gkba_ctx* c, int L, const double2* rho, const double2* T,
+                              const double* w, const double2* Ibar, double2* rho_bar,
+                              double2* T_bar) {
+    const int N = c->N;
+    const long long NN = (long long)N * N;
+    GKBA_TRY(ensure_workspace(c, 2 * L));
+    if (c->vjp_units < c->ub) {
+        if (c->vjp) cudaFree(c->vjp);
+        c->vjp = nullptr;
+        c->vjp_units = 0;
+        if (cudaMalloc(&c->vjp, 10ull * c->ub * NN * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GKBA_ENOMEM, "adjoint scratch of %d units does not fit", c->ub);
+        }
+        c->vjp_units = c->ub;
+    }
+    const long long blk = (long long)c->vjp_units * NN;
+    double2 *Gv = c->vjp, *Gbv = Gv + blk, *Sv = Gv + 2 * blk, *Sbv = Gv + 3 * blk,
+            *Gbb = Gv + 4 * blk, *Gbr = Gv + 5 * blk, *tA = Gv + 6 * blk, *tB = Gv + 7 * blk,
+            *tC = Gv + 8 * blk, *D = Gv + 9 * blk;
+    const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+    const int nk_per = c->ub / 2;
+    for (int k0 = 0; k0 < L; k0 += nk_per) {
+        const int nk = std::min(nk_per, L - k0), nb = 2 * nk;
+        GKBA_TRY(units_from_history(c, N, k0, nk, L, c->dt, rho, T, w, Gv, Gbv, c->coef));
+        GKBA_TRY(contract3(c, nb, Gv, Gbv, Gv));  // S_u
+        GKBA_CUDA(c, cudaMemcpyAsync(Sv, c->Su, nb * NN * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                     c->stream));
+        GKBA_TRY(scale_units(c, nb, c->coef, Ibar, tC));  // Ybar
+        GKBA_TRY(zgemm_batched(c, K_RED, N, 'N', 'C', one, tC, NN, Gbv, NN, zero, Sbv, NN, nb, 0));
+        GKBA_TRY(zgemm_batched(c, K_RED, N, 'C', 'N', one, Sv, NN, tC, NN, zero, Gbb, NN, nb, 0));
+        GKBA_TRY(unit_xform(c, nb, Gv, tA, 1, 0));   // G*
+        GKBA_TRY(unit_xform(c, nb, Sbv, tB, 0, 1));  // Sbar^T
+        GKBA_TRY(contract3(c, nb, tA, tB, tA));
+        GKBA_TRY(unit_acc(c, nb, Gbb, c->Su, 1));
+        GKBA_TRY(unit_xform(c, nb, Gv, tB, 1, 1));   // G*^T
+        GKBA_TRY(unit_xform(c, nb, Gbv, tC, 1, 1));  // Gb*^T
+        GKBA_TRY(contract3(c, nb, Sbv, tB, tC));
+        GKBA_CUDA(c, cudaMemcpyAsync(Gbr, c->Su, nb * NN * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                     c->stream));
+        GKBA_TRY(contract3(c, nb, tC, tB, Sbv));
+        GKBA_TRY(unit_acc(c, nb, Gbr, c->Su, 0));
+        GKBA_TRY(vjp_points(c, nk, Gbr, Gbb, tA, tB));  // Pbar, Qbar
+        GKBA_TRY(axpy_c(c, D, tA, tB, 1.0, -1.0, (int)(nk * NN)));
+        GKBA_TRY(zgemm_batched(c, K_RED, N, 'C', 'N', one, T + k0 * NN, NN, D, NN, zero,
+                               rho_bar + k0 * NN, NN, nk, 0));
+        GKBA_TRY(zgemm_batched(c, K_RED, N, 'N', 'C', one, D, NN, rho + k0 * NN, NN, zero,
+                               T_bar + k0 * NN, NN, nk, 0));
+        GKBA_TRY(axpy_c(c, T_bar + k0 * NN, T_bar + k0 * NN, tB, 1.0, 1.0, (int)(nk * NN)));
     }
     return GKBA_OK;
 }
@@ -308,7 +401,7 @@ void free_ctx(gkba_ctx* c) {
     if (!c) return;
     if (c->device >= 0) cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
+    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->vjp, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
                     c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
                     c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
                     c->stage};
@@ -598,6 +691,90 @@ gkba_status gkba_collision(gkba_ctx* c, int L, const double* rho_hist, const dou
     GKBA_TRY(collision_dev(c, L, dR, dT, dW, dI));
     if (!on_device)
         GKBA_CUDA(c, cudaMemcpyAsync(I_out, dI, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+    return finish(c);
+}
+
+gkba_status gkba_sigma3(gkba_ctx* c, int n_units, const double* A, const double* B,
+                        const double* C, double* S_out, int on_device) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_sigma3: NULL context");
+    if (n_units < 0 || (n_units > 0 && (!A || !B || !C || !S_out)))
+        return fail(c, GKBA_EINVAL, "gkba_sigma3: bad arguments");
+    if (c->kind != GKBA_V_GENERAL)
+        return fail(c, GKBA_EUNSUPPORTED, "gkba_sigma3: general interaction only");
+    if (n_units == 0) return GKBA_OK;
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    const size_t NN = (size_t)c->N * c->N, bytes = NN * 16 * (size_t)n_units;
+    const double2 *dA, *dB, *dC;
+    double2* dS;
+    if (on_device) {
+        dA = (const double2*)A;
+        dB = (const double2*)B;
+        dC = (const double2*)C;
+        dS = (double2*)S_out;
+    } else {
+        GKBA_TRY(ensure_stage(c, 4 * bytes));
+        char* st = (char*)c->stage;
+        dA = (double2*)st;
+        dB = (double2*)(st + bytes);
+        dC = (double2*)(st + 2 * bytes);
+        dS = (double2*)(st + 3 * bytes);
+        GKBA_TRY(copy_in(c, (void*)dA, A, bytes, 0));
+        GKBA_TRY(copy_in(c, (void*)dB, B, bytes, 0));
+        GKBA_TRY(copy_in(c, (void*)dC, C, bytes, 0));
+    }
+    GKBA_TRY(sigma3_dev(c, n_units, dA, dB, dC, dS));
+    if (!on_device)
+        GKBA_CUDA(c, cudaMemcpyAsync(S_out, dS, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return finish(c);
+}
+
+gkba_status gkba_collision_vjp(gkba_ctx* c, int L, const double* rho_hist, const double* T_hist,
+                               const double* weights, const double* I_bar, double* rho_bar,
+                               double* T_bar, int on_device) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_collision_vjp: NULL context");
+    if (L < 1 || !rho_hist || !T_hist || !I_bar || !rho_bar || !T_bar)
+        return fail(c, GKBA_EINVAL, "gkba_collision_vjp: need L >= 1 and non-NULL arrays");
+    if (c->kind != GKBA_V_GENERAL)
+        return fail(c, GKBA_EUNSUPPORTED, "gkba_collision_vjp: general interaction only");
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    const size_t NN = (size_t)c->N * c->N, hb = NN * 16 * (size_t)L;
+    const size_t wb = ((size_t)L * 8 + 255) & ~(size_t)255;
+    const double2 *dR, *dT, *dIb;
+    const double* dW = nullptr;
+    double2 *dRb, *dTb;
+    if (on_device) {
+        dR = (const double2*)rho_hist;
+        dT = (const double2*)T_hist;
+        dW = weights;
+        dIb = (const double2*)I_bar;
+        dRb = (double2*)rho_bar;
+        dTb = (double2*)T_bar;
+    } else {
+        if (weights)
+            for (int k = 0; k < L; ++k)
+                if (!std::isfinite(weights[k]))
+                    return fail(c, GKBA_EINVAL, "gkba_collision_vjp: non-finite weight");
+        GKBA_TRY(ensure_stage(c, 4 * hb + wb + NN * 16));
+        char* s = (char*)c->stage;
+        dR = (double2*)s;
+        dT = (double2*)(s + hb);
+        dRb = (double2*)(s + 2 * hb);
+        dTb = (double2*)(s + 3 * hb);
+        double* w = (double*)(s + 4 * hb);
+        dIb = (double2*)(s + 4 * hb + wb);
+        GKBA_TRY(copy_in(c, (void*)dR, rho_hist, hb, 0));
+        GKBA_TRY(copy_in(c, (void*)dT, T_hist, hb, 0));
+        GKBA_TRY(copy_in(c, (void*)dIb, I_bar, NN * 16, 0));
+        if (weights) {
+            GKBA_TRY(copy_in(c, w, weights, (size_t)L * 8, 0));
+            dW = w;
+        }
+    }
+    GKBA_TRY(collision_vjp_dev(c, L, dR, dT, dW, dIb, dRb, dTb));
+    if (!on_device) {
+        GKBA_CUDA(c, cudaMemcpyAsync(rho_bar, dRb, hb, cudaMemcpyDeviceToHost, c->stream));
+        GKBA_CUDA(c, cudaMemcpyAsync(T_bar, dTb, hb, cudaMemcpyDeviceToHost, c->stream));
+    }
     return finish(c);
 }
 

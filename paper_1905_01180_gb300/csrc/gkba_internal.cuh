@@ -123,6 +123,10 @@ struct gkba_ctx {
     double2* PQ = nullptr;       // P and Q for ub/2 history points: 2 * (ub/2) * N*N
     void* formsB1 = nullptr;     // per-unit B operand of S1
     void* formsG = nullptr;      // per-unit B operand of S2/S3
+    void* formsG3 = nullptr;     // per-unit B operand of S3 when its slot differs (sep_A)
+    double2* vjp = nullptr;      // adjoint scratch: 10 blocks of vjp_units N*N units
+    int vjp_units = 0;
+    bool sep_A = false;          // contraction of S3(A, B, C): S3 reads formsG3
     double2* Mb = nullptr;       // per-unit Gbar (= the right factor of S.Gbar), ub * N*N
     double* coef = nullptr;      // per-unit weight (+-c_k), ub
     double2* Su = nullptr;       // per-unit S, ub * N*N
@@ -247,6 +251,14 @@ gkba_status weighted_sum_units(gkba_ctx* c, int N, int nb, const double* coef, c
                                double2* I);
 gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
 gkba_status build_forms_tf32(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
+gkba_status build_forms3_fp64(gkba_ctx* c, int nb, const double2* A);
+// adjoint of the collision integral: per-unit elementwise steps (N x N units)
+gkba_status unit_xform(gkba_ctx* c, int nb, const double2* in, double2* out, int conj, int transpose);
+gkba_status unit_acc(gkba_ctx* c, int nb, double2* y, const double2* x, int transpose);
+gkba_status scale_units(gkba_ctx* c, int nb, const double* coef, const double2* Ibar, double2* Y);
+gkba_status vjp_points(gkba_ctx* c, int nk, const double2* Gbar, const double2* Gbbar, double2* Pbar,
+                       double2* Qbar);
+gkba_status build_forms3_tf32(gkba_ctx* c, int nb, const double2* A);
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
                                    const void* part, bool fp32, double2* S);
 size_t tf32_part_bytes(int Np, int ub, int kchunk);

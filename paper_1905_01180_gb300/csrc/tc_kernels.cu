@@ -1056,13 +1056,17 @@ __global__ void k_forms_tf32(int N, int Np, int nb, int ub, const double2* __res
     const long long NN = (long long)N * N;
     float bh = 0.f, bl = 0.f, gh = 0.f, gl = 0.f;
     if (idx < N && k < N) {
-        const double2 gb = Gb[u * NN + (long long)k * N + idx];  // Gb[s = k][r = idx]
-        split_f64(comp ? gb.y : gb.x, bh, bl);
+        if (B1 != nullptr) {
+            const double2 gb = Gb[u * NN + (long long)k * N + idx];  // Gb[s = k][r = idx]
+            split_f64(comp ? gb.y : gb.x, bh, bl);
+        }
         const double2 g = G[u * NN + (long long)idx * N + k];    // G[p = idx][q = k]
         split_f64(comp ? g.y : g.x, gh, gl);
     }
-    B1[e] = bh;
-    B1[per * ub + e] = bl;
+    if (B1 != nullptr) {  // null: only the G forms (stage S3's slot of S3(A, B, C))
+        B1[e] = bh;
+        B1[per * ub + e] = bl;
+    }
     // Gs: Re G -> blocks 0 and 3, Im G -> block 1 and (negated) block 2
     const long long pg = 2 * per;
     const long long g0 = (long long)u * pg + rr;
@@ -1176,6 +1180,14 @@ gkba_status build_forms_tf32(gkba_ctx* c, int nb, const double2* G, const double
     return launch_end(c, t);
 }
 
+gkba_status build_forms3_tf32(gkba_ctx* c, int nb, const double2* A) {
+    const long long per = 2LL * c->Np * c->Np;
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_forms_tf32<<<grid1(per * nb, 256), 256, 0, c->stream>>>(c->N, c->Np, nb, c->ub_cap, A, nullptr,
+                                                              nullptr, (float*)c->formsG3);
+    return launch_end(c, t);
+}
+
 gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG, const double2* Gb,
                         long long sGb, int) {
     (void)sG;
@@ -1198,13 +1210,15 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     float* B1lo = B1hi + per * c->ub_cap;
     float* Gshi = (float*)c->formsG;
     float* Gslo = Gshi + 2 * per * c->ub_cap;
+    float* G3hi = (float*)(c->sep_A ? c->formsG3 : c->formsG);  // stage S3's slot
+    float* G3lo = G3hi + 2 * per * c->ub_cap;
     int* err = c->dint + 1;
     // Flops below are the algorithmic counts of the N-basis problem (padding excluded).
     const double Nr = c->N;
     const double fl_cr = 4.0 * Nr * Nr * Nr * Nr * Nr, fl_cc = 2.0 * fl_cr;
     const double N4r = Nr * Nr * Nr * Nr;
 
-    CUtensorMap mA1, mA23_in1, mA23_in2, mB1h, mB1l, mGh, mGl, mAf, mVh, mVl;
+    CUtensorMap mA1, mA23_in1, mA23_in2, mB1h, mB1l, mGh, mGl, mG3h, mG3l, mAf, mVh, mVl;
     const bool multi = c->unit_sys != nullptr;  // several systems: w and v per system
     if (multi) {
         cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)N3, (cuuint64_t)c->nsys};
@@ -1235,6 +1249,8 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         cuuint64_t sg[2] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * per * 4};
         GKBA_TRY(make_map(c, &mGh, Gshi, 3, dg, sg, b));
         GKBA_TRY(make_map(c, &mGl, Gslo, 3, dg, sg, b));
+        GKBA_TRY(make_map(c, &mG3h, G3hi, 3, dg, sg, b));
+        GKBA_TRY(make_map(c, &mG3l, G3lo, 3, dg, sg, b));
     }
     if ((Np % 32) == 0) {
         const long long Rl = ((2LL * Np * nb + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
@@ -1313,7 +1329,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     }
     {
         auto t = launch_begin(c, K_W3, fl_cc * nb, 4.0 * 4 * N4r * nb);
-        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in2, mGh, mGl, sp);
+        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in2, mG3h, mG3l, sp);
         GKBA_TRY(launch_end(c, t));
     }
     // S4: split-K over (n,r,p)

@@ -31,7 +31,7 @@ EXPORTED = ["gkba_init", "gkba_sigma", "gkba_collision", "gkba_step", "gkba_set_
             "gkba_get_history", "gkba_get_state", "gkba_mean_field", "gkba_adjoint",
             "gkba_get_stats", "gkba_last_error", "gkba_destroy", "gkba_sigma_noalloc",
             "gkba_batch_create", "gkba_batch_step", "gkba_batch_last_error", "gkba_batch_destroy",
-            "gkba_selftest_timeout"]
+            "gkba_selftest_timeout", "gkba_sigma3", "gkba_collision_vjp"]
 
 
 class GKBAError(RuntimeError):
@@ -84,6 +84,8 @@ def load():
     L.gkba_sigma_noalloc.argtypes = [I, I, P, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
     L.gkba_batch_create.argtypes = [ctypes.POINTER(P), P, I, ctypes.c_size_t]
     L.gkba_selftest_timeout.argtypes = [P, D, P]
+    L.gkba_sigma3.argtypes = [P, I, P, P, P, P, I]
+    L.gkba_collision_vjp.argtypes = [P, I, P, P, P, P, P, P, I]
     L.gkba_batch_step.argtypes = [P, P, P, P, P]
     L.gkba_batch_last_error.argtypes = [P]
     L.gkba_batch_last_error.restype = ctypes.c_char_p
@@ -211,6 +213,41 @@ class Context:
         self._check(load().gkba_collision(self._h, Lh, rp, tp, wp, out.ctypes.data, 0))
         return out
 
+    def sigma3(self, A, B, C):
+        """S3(A, B, C)_ij = sum v_irpn w_mqsj A_nm B_sr C_pq for (U, N, N) batches."""
+        a, ap = _host(A, np.complex128); b, bp = _host(B, np.complex128)
+        c, cp = _host(C, np.complex128)
+        n = 1 if a.ndim == 2 else int(a.shape[0])
+        out = np.empty_like(a)
+        self._check(load().gkba_sigma3(self._h, n, ap, bp, cp, out.ctypes.data, 0))
+        return out
+
+    def collision_vjp(self, rho_hist, T_hist, I_bar, weights=None):
+        """Adjoint of ``collision``: (rho_bar, T_bar) for I_bar = dL/dRe I + i dL/dIm I."""
+        Lh = int(rho_hist.shape[0])
+        if _is_torch(rho_hist):
+            import torch
+            r, rp = _dev(rho_hist, "c16"); t, tp = _dev(T_hist, "c16")
+            ib, ibp = _dev(I_bar, "c16")
+            wp = None
+            if weights is not None:
+                w, wp = _dev(weights, "f64")
+            rb = torch.empty_like(r)
+            tb = torch.empty_like(t)
+            self._check(load().gkba_collision_vjp(self._h, Lh, rp, tp, wp, ibp, rb.data_ptr(),
+                                                  tb.data_ptr(), 1))
+            return rb, tb
+        r, rp = _host(rho_hist, np.complex128); t, tp = _host(T_hist, np.complex128)
+        ib, ibp = _host(I_bar, np.complex128)
+        wp = None
+        if weights is not None:
+            w, wp = _host(weights, np.float64)
+        rb = np.empty_like(r)
+        tb = np.empty_like(t)
+        self._check(load().gkba_collision_vjp(self._h, Lh, rp, tp, wp, ibp, rb.ctypes.data,
+                                              tb.ctypes.data, 0))
+        return rb, tb
+
     def step(self, E_n, E_np1):
         """One Heun step; returns (rho_{n+1}, I(t_n), diag(t_n))."""
         rho = np.empty((self.N, self.N), np.complex128)
@@ -318,3 +355,24 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def collision_autograd(ctx, rho_hist, T_hist, weights=None):
+    """I = ctx.collision(rho_hist, T_hist) as a differentiable torch op on CUDA
+    complex128 tensors: the backward pass is gkba_collision_vjp (PyTorch's
+    complex gradient convention, dL/dRe + i dL/dIm, is the library's)."""
+    import torch
+
+    class _Collision(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, rho, T):
+            fctx.save_for_backward(rho, T)
+            return ctx.collision(rho, T, weights)
+
+        @staticmethod
+        def backward(fctx, I_bar):
+            rho, T = fctx.saved_tensors
+            rb, tb = ctx.collision_vjp(rho, T, I_bar.contiguous(), weights)
+            return rb, tb
+
+    return _Collision.apply(rho_hist, T_hist)

@@ -24,7 +24,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "gkba.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gkba_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(gkba_[a-z_0-9]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
