@@ -202,12 +202,24 @@ gkba_status gkba_get_state(const gkba_ctx* ctx, int* n, double* rho);
 gkba_status gkba_mean_field(gkba_ctx* ctx, const double* rho, double* sigma_hf, int on_device);
 
 /*
- * gkba_adjoint - reverse-mode gradient of L = Tr[d rho(t_T)] through the
- * Heun stepper and the collision integral.  Not implemented in this build:
- * returns GKBA_EUNSUPPORTED and writes nothing.
+ * gkba_adjoint - reverse-mode gradient through the Heun stepper and the
+ * collision integrals of the n steps taken since gkba_init (or
+ * gkba_set_history(0, ...)): the discrete adjoint of gkba_step as
+ * implemented, for a loss L(rho(t_n)) of the final state.
+ *   rho_bar_final N*N complex (host): dL/dRe rho(t_n) + i dL/dIm rho(t_n)
+ *                 (for L = Tr[d rho(t_n)], d Hermitian: rho_bar_final = d)
+ *   E_bar         n+1 doubles (host): dL/dE_k for the field samples of the
+ *                 steps (E(t_k) as passed to step k and to step k-1 as E_np1)
+ *   rho0_bar      N*N complex (host, may be NULL): dL/drho(t_0), same convention
+ * gkba_step records the predictor state and the propagator of every step;
+ * the backward pass un-propagates the T(t, t_k) rows with U_n^+ (U_n unitary),
+ * so no checkpoints are needed.  Each step costs two collision-integral
+ * adjoints (about eight collision integrals) plus N^3 work, including the
+ * Frechet derivative of the exponential (a 2N x 2N exponential).
+ * Gradients with respect to v are not provided.  GKBA_EUNSUPPORTED for a
+ * structured interaction or a trajectory started by gkba_set_history(n > 0).
  */
-gkba_status gkba_adjoint(gkba_ctx* ctx, const double* E_samples, int n_steps, int ckpt_every,
-                         const double* dL_drho_T, double* dL_dE, double* dL_dv);
+gkba_status gkba_adjoint(gkba_ctx* ctx, const double* rho_bar_final, double* E_bar, double* rho0_bar);
 
 /*
  * gkba_get_stats - kernel counters since the last reset: fills up to

@@ -732,6 +732,155 @@ __global__ void k_vjp_points(int N, int nk, const double2* __restrict__ Gbar,
     Qbar[e] = make_double2(g1.x + b0.x, g1.y - b0.y);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the Heun step: small N x N helpers.
+// ---------------------------------------------------------------------------
+// y += i s (a - b)
+__global__ void k_add_i_diff(long long n, double2* __restrict__ y, const double2* __restrict__ a,
+                             const double2* __restrict__ b, double s) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double re = a[e].x - b[e].x, im = a[e].y - b[e].y;
+    y[e].x += -s * im;
+    y[e].y += s * re;
+}
+// Ibar = -(kbar + kbar^+)   (k = ... - (I + I^+))
+__global__ void k_ibar_from_kbar(int N, const double2* __restrict__ kb, double2* __restrict__ Ib) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * N) return;
+    const int i = e / N, j = e % N;
+    const double2 a = kb[e], b = kb[j * N + i];
+    Ib[e] = make_double2(-(a.x + b.x), -(a.y - b.y));
+}
+// rho_bar[l][k] += sum_ij hfK[(i,j)][(l,k)] hbar[i][j]  (adjoint of the mean field, hfK real)
+__global__ void k_mean_field_adj(int N, const double* __restrict__ hfK, const double2* __restrict__ hb,
+                                 double2* __restrict__ rb) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int NN = N * N;
+    if (warp >= NN) return;
+    double re = 0.0, im = 0.0;
+    for (int e = lane; e < NN; e += 32) {
+        const double kv = hfK[(long long)e * NN + warp];
+        re = fma(kv, hb[e].x, re);
+        im = fma(kv, hb[e].y, im);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        rb[warp].x += re;
+        rb[warp].y += im;
+    }
+}
+// out += Re sum_ij conj(hbar_ij) d_ij   (dL/dE for h = ... + E d, E real); one block
+__global__ void k_field_grad(int N, const double2* __restrict__ hb, const double2* __restrict__ d,
+                             double* __restrict__ out) {
+    __shared__ double part[256];
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) acc += hb[e].x * d[e].x + hb[e].y * d[e].y;
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out += part[0];
+}
+// Fréchet block for the adjoint of U = exp(X), X = -i dt (hA + hB)/2:
+//   Z = [[X^+, Ubar / nu], [0, X^+]] (2N x 2N), nu = max(1, ||Ubar||_1) so that
+// the scaling of the exponential stays small; the top-right block of exp(Z)
+// times nu is L_exp(X^+, Ubar) = Xbar.  One block.
+__global__ void k_frechet_block(int N, double dt, const double2* __restrict__ hA,
+                                const double2* __restrict__ hB, const double2* __restrict__ Ub,
+                                double2* __restrict__ Z, double* __restrict__ nu_out) {
+    __shared__ double colmax[256];
+    double best = 0.0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double sum = 0.0;
+        for (int i = 0; i < N; ++i) sum += hypot(Ub[i * N + j].x, Ub[i * N + j].y);
+        best = fmax(best, sum);
+    }
+    colmax[threadIdx.x] = best;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) colmax[threadIdx.x] = fmax(colmax[threadIdx.x], colmax[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double nu = fmax(1.0, colmax[0]);
+    const int M = 2 * N;
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+        const int r = e / M, c = e % M;
+        double2 z = make_double2(0.0, 0.0);
+        if ((r < N && c < N) || (r >= N && c >= N)) {
+            // X^+ with X = -i dt h, h = (hA + hB)/2 Hermitian: X^+ = i dt h
+            const int i = r % N, j = c % N;
+            const double hr = 0.5 * (hA[i * N + j].x + hB[i * N + j].x);
+            const double hi = 0.5 * (hA[i * N + j].y + hB[i * N + j].y);
+            z = make_double2(-dt * hi, dt * hr);
+        } else if (r < N && c >= N) {
+            const double2 u = Ub[r * N + (c - N)];
+            z = make_double2(u.x / nu, u.y / nu);
+        }
+        Z[e] = z;
+    }
+    if (threadIdx.x == 0) *nu_out = nu;
+}
+// hbar_A += (i dt / 2) nu W[0:N, N:2N];  hbar_B += same  (X = -i dt (hA + hB)/2)
+__global__ void k_frechet_apply(int N, double dt, const double2* __restrict__ W,
+                                const double* __restrict__ nu, double2* __restrict__ hA_b,
+                                double2* __restrict__ hB_b) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * N) return;
+    const int i = e / N, j = e % N;
+    const double2 w = W[i * (2 * N) + N + j];
+    const double s = 0.5 * dt * (*nu);
+    const double2 a = make_double2(-s * w.y, s * w.x);  // i s w
+    hA_b[e].x += a.x;
+    hA_b[e].y += a.y;
+    hB_b[e].x += a.x;
+    hB_b[e].y += a.y;
+}
+// exp(Z) for a general complex n x n matrix: scaling set-up (1-norm, number of
+// squarings s with ||Z||_1 / 2^s <= 1/2, Z scaled by 2^-s into X).  One block.
+__global__ void k_expm_setup_general(int n, const double2* __restrict__ Z, double2* __restrict__ X,
+                                     int* __restrict__ s_out) {
+    __shared__ double colmax[256];
+    double best = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) sum += hypot(Z[i * n + j].x, Z[i * n + j].y);
+        best = fmax(best, sum);
+    }
+    colmax[threadIdx.x] = best;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) colmax[threadIdx.x] = fmax(colmax[threadIdx.x], colmax[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double nrm = colmax[0];
+    int s = 0;
+    while (s < 16 && ldexp(nrm, -s) > 0.5) ++s;
+    const double scale = ldexp(1.0, -s);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+        X[e] = make_double2(scale * Z[e].x, scale * Z[e].y);
+    if (threadIdx.x == 0) *s_out = s;
+}
+
+// dst = sum_u src_u over nb N x N units (fixed order)
+__global__ void k_sum_units(long long NN, int nb, const double2* __restrict__ src,
+                            double2* __restrict__ dst) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NN) return;
+    double re = 0.0, im = 0.0;
+    for (int u = 0; u < nb; ++u) {
+        re += src[u * NN + e].x;
+        im += src[u * NN + e].y;
+    }
+    dst[e] = make_double2(re, im);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -963,6 +1112,82 @@ gkba_status vjp_points(gkba_ctx* c, int nk, const double2* Gbar, const double2* 
     const long long n = (long long)nk * c->N * c->N;
     auto t = launch_begin(c, K_RED, 0.0, 0.0);
     k_vjp_points<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, nk, Gbar, Gbbar, Pbar, Qbar);
+    return launch_end(c, t);
+}
+
+gkba_status add_i_diff(gkba_ctx* c, double2* y, const double2* a, const double2* b, double s) {
+    const long long n = (long long)c->N * c->N;
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_add_i_diff<<<grid1(n, 256), 256, 0, c->stream>>>(n, y, a, b, s);
+    return launch_end(c, t);
+}
+gkba_status ibar_from_kbar(gkba_ctx* c, const double2* kb, double2* Ib) {
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_ibar_from_kbar<<<grid1((long long)c->N * c->N, 256), 256, 0, c->stream>>>(c->N, kb, Ib);
+    return launch_end(c, t);
+}
+gkba_status mean_field_adj(gkba_ctx* c, const double2* hb, double2* rb) {
+    const int NN = c->N * c->N;
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_mean_field_adj<<<grid1((long long)NN * 32, 256), 256, 0, c->stream>>>(c->N, c->hfK, hb, rb);
+    return launch_end(c, t);
+}
+gkba_status field_grad(gkba_ctx* c, const double2* hb, double* out) {
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_field_grad<<<1, 256, 0, c->stream>>>(c->N, hb, c->d, out);
+    return launch_end(c, t);
+}
+// exp(Z) of a general complex n x n matrix (Taylor degree 18 by Horner after
+// scaling, then the squarings); X, Y, W: n x n scratch, result in W.
+static gkba_status expm_general(gkba_ctx* c, int n, const double2* Z, double2* X, double2* Y,
+                                double2* W) {
+    {
+        auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+        k_expm_setup_general<<<1, 256, 0, c->stream>>>(n, Z, X, c->dint + 0);
+        GKBA_TRY(launch_end(c, t));
+        t = launch_begin(c, K_STEP, 0.0, 0.0);
+        k_set_identity<<<grid1((long long)n * n, 256), 256, 0, c->stream>>>(n, 1, Y);
+        GKBA_TRY(launch_end(c, t));
+    }
+    double2 *y = Y, *z = W;
+    for (int k = 18; k >= 1; --k) {
+        GKBA_TRY(zgemm_batched(c, K_STEP, n, 'N', 'N', make_double2(1.0 / k, 0.0), X, 0, y, 0,
+                               make_double2(0.0, 0.0), z, 0, 1, 1));
+        std::swap(y, z);
+    }
+    for (int i = 0; i < 16; ++i) {
+        GKBA_TRY(zgemm_impl(c, K_STEP, n, 'N', 'N', make_double2(1.0, 0.0), y, 0, y, 0,
+                            make_double2(0.0, 0.0), z, 0, 1, 0, c->dint + 0, i));
+        std::swap(y, z);
+    }
+    if (y != W)
+        GKBA_CUDA(c, cudaMemcpyAsync(W, y, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                     c->stream));
+    return GKBA_OK;
+}
+// Adjoint of U = exp(-i dt (hA + hB)/2): hA_bar, hB_bar += (i dt / 2) L_exp(X^+, Ubar).
+// scratch: 4 blocks of (2N)^2 entries.
+gkba_status expm_adj(gkba_ctx* c, const double2* hA, const double2* hB, const double2* Ubar,
+                     double2* hA_bar, double2* hB_bar, double2* scratch) {
+    const int N = c->N, M = 2 * N;
+    const long long MM = (long long)M * M;
+    double2 *Z = scratch, *X = scratch + MM, *Y = scratch + 2 * MM, *W = scratch + 3 * MM;
+    {
+        auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+        k_frechet_block<<<1, 256, 0, c->stream>>>(N, c->dt, hA, hB, Ubar, Z, c->dscal + 12);
+        GKBA_TRY(launch_end(c, t));
+    }
+    GKBA_TRY(expm_general(c, M, Z, X, Y, W));
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_frechet_apply<<<grid1((long long)N * N, 256), 256, 0, c->stream>>>(N, c->dt, W, c->dscal + 12,
+                                                                         hA_bar, hB_bar);
+    return launch_end(c, t);
+}
+
+gkba_status sum_units(gkba_ctx* c, int nb, const double2* src, double2* dst) {
+    const long long NN = (long long)c->N * c->N;
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_sum_units<<<grid1(NN, 256), 256, 0, c->stream>>>(NN, nb, src, dst);
     return launch_end(c, t);
 }
 

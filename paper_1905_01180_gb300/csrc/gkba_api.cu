@@ -401,7 +401,7 @@ void free_ctx(gkba_ctx* c) {
     if (!c) return;
     if (c->device >= 0) cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->vjp, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
+    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->vjp, c->rhot_hist, c->U_hist, c->adj_ws, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
                     c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
                     c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
                     c->stage};
@@ -574,6 +574,8 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     ALLOC(c->rho_hist, cap * NN * 16);
     ALLOC(c->T_a, cap * NN * 16);
     ALLOC(c->T_b, cap * NN * 16);
+    ALLOC(c->rhot_hist, cap * NN * 16);
+    ALLOC(c->U_hist, cap * NN * 16);
     ALLOC(c->hhf_n, NN * 16);
     ALLOC(c->hhf_t, NN * 16);
     ALLOC(c->k1, NN * 16);
@@ -622,6 +624,9 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         return bail(GKBA_ECUDA);
     }
     c->n = 0;
+    c->adj_from = 0;
+    c->E_a.assign(cap, 0.0);
+    c->E_b.assign(cap, 0.0);
     *out = c;
     return GKBA_OK;
 }
@@ -818,9 +823,13 @@ gkba_status gkba_step(gkba_ctx* c, double E_n, double E_np1, double* rho_out, do
     GKBA_TRY(diagnostics(c, E_n, rho_n, c->Ia, c->dscal));
     GKBA_TRY(rhs(c, c->hhf_n, rho_n, c->Ia, c->k1));
     GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k1, 1.0, c->dt, (int)NN));
+    GKBA_CUDA(c, cudaMemcpyAsync(c->rhot_hist + n * NN, rho_t, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
     GKBA_TRY(h_hf(c, E_np1, rho_t, c->hhf_t));
     // propagator recursion T(t_{n+1}, t_k) = U_n T(t_n, t_k); T(t_{n+1}, t_{n+1}) = 1
     GKBA_TRY(expm_step(c, c->hhf_n, c->hhf_t, c->U));
+    GKBA_CUDA(c, cudaMemcpyAsync(c->U_hist + n * NN, c->U, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
+    c->E_a[n] = E_n;
+    c->E_b[n] = E_np1;
     GKBA_TRY(zgemm_batched(c, K_STEP, c->N, 'N', 'N', make_double2(1.0, 0.0), c->U, 0, c->T_a, NN,
                            make_double2(0.0, 0.0), c->T_b, NN, n + 1, 0));
     GKBA_TRY(set_identity(c, c->T_b + (n + 1) * NN, 1));
@@ -851,6 +860,7 @@ gkba_status gkba_set_history(gkba_ctx* c, int n, const double* rho_hist, const d
     GKBA_TRY(copy_in(c, c->rho_hist, rho_hist, bytes, on_device));
     GKBA_TRY(copy_in(c, c->T_a, T_hist, bytes, on_device));
     c->n = n;
+    c->adj_from = n;  // steps before n were not recorded
     return finish(c);
 }
 
@@ -879,8 +889,114 @@ gkba_status gkba_get_state(const gkba_ctx* cc, int* n, double* rho) {
     return GKBA_OK;
 }
 
-gkba_status gkba_adjoint(gkba_ctx* c, const double*, int, int, const double*, double*, double*) {
-    return fail(c, GKBA_EUNSUPPORTED, "gkba_adjoint is not implemented in this build");
+gkba_status gkba_adjoint(gkba_ctx* c, const double* rho_bar_final, double* E_bar, double* rho0_bar) {
+    if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_adjoint: NULL context");
+    if (!rho_bar_final || !E_bar) return fail(c, GKBA_EINVAL, "gkba_adjoint: NULL argument");
+    if (c->kind != GKBA_V_GENERAL)
+        return fail(c, GKBA_EUNSUPPORTED, "gkba_adjoint: general interaction only");
+    if (c->adj_from != 0)
+        return fail(c, GKBA_EUNSUPPORTED,
+                    "gkba_adjoint: the trajectory must start at gkba_init or gkba_set_history(0, ...)");
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    NvtxRange nr("gkba_adjoint");
+    const int M = c->n, N = c->N;
+    const long long NN = (long long)N * N;
+    const size_t H = (size_t)(M + 2) * NN;  // one history-sized block
+    const size_t need = (7 * H + 12 * NN + 16 * NN) * sizeof(double2) + (size_t)(M + 1) * 8 + 256;
+    if (c->adj_ws_bytes < need) {
+        if (c->adj_ws) cudaFree(c->adj_ws);
+        c->adj_ws = nullptr;
+        c->adj_ws_bytes = 0;
+        if (cudaMalloc(&c->adj_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GKBA_ENOMEM, "gkba_adjoint: %zu bytes of backward buffers do not fit", need);
+        }
+        c->adj_ws_bytes = need;
+    }
+    double2* base = c->adj_ws;
+    double2 *Rb = base, *Tcur = base + H, *Tprv = base + 2 * H, *Tb = base + 3 * H,
+            *srho = base + 4 * H, *sT = base + 5 * H, *prod = base + 6 * H;
+    double2* sm = base + 7 * H;
+    double2 *kb = sm, *kb1 = sm + NN, *hA = sm + 2 * NN, *hB = sm + 3 * NN, *hAb = sm + 4 * NN,
+            *hBb = sm + 5 * NN, *rtb = sm + 6 * NN, *Ib = sm + 7 * NN, *P1 = sm + 8 * NN,
+            *P2 = sm + 9 * NN, *Ub = sm + 10 * NN, *save = sm + 11 * NN;
+    double2* fre = sm + 12 * NN;  // 4 (2N)^2 blocks = 16 NN
+    double* Eb = (double*)(fre + 16 * NN);
+    const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+    const double dt = c->dt;
+    GKBA_CUDA(c, cudaMemsetAsync(Rb, 0, H * sizeof(double2), c->stream));
+    GKBA_CUDA(c, cudaMemsetAsync(Tb, 0, H * sizeof(double2), c->stream));
+    GKBA_CUDA(c, cudaMemsetAsync(Eb, 0, (size_t)(M + 1) * 8, c->stream));
+    GKBA_TRY(copy_in(c, Rb + (size_t)M * NN, rho_bar_final, NN * 16, 0));
+    GKBA_CUDA(c, cudaMemcpyAsync(Tcur, c->T_a, (size_t)(M + 1) * NN * 16, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    for (int n = M - 1; n >= 0; --n) {
+        const double2* rho_n = c->rho_hist + (size_t)n * NN;
+        const double2* rho_t = c->rhot_hist + (size_t)n * NN;
+        const double2* U = c->U_hist + (size_t)n * NN;
+        double2* Rn = Rb + (size_t)n * NN;
+        double2* Rn1 = Rb + (size_t)(n + 1) * NN;
+        GKBA_TRY(h_hf(c, c->E_a[n], rho_n, hA));
+        GKBA_TRY(h_hf(c, c->E_b[n], rho_t, hB));
+        // T(t_n, t_k) = U^+ T(t_{n+1}, t_k), k <= n (U unitary)
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'C', 'N', one, U, 0, Tcur, NN, zero, Tprv, NN, n + 1, 0));
+        // rho_{n+1} = rho_n + dt/2 (k1 + k2)
+        GKBA_TRY(axpy_c(c, kb, Rn1, Rn1, 0.5 * dt, 0.0, (int)NN));
+        GKBA_TRY(axpy_c(c, Rn, Rn, Rn1, 1.0, 1.0, (int)NN));
+        // k2 = -i[hB, rho~] - (I~ + I~^+)
+        GKBA_CUDA(c, cudaMemsetAsync(hAb, 0, 4 * NN * sizeof(double2), c->stream));  // hAb hBb rtb Ib
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'C', one, kb, 0, rho_t, 0, zero, P1, 0, 1, 0));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'C', 'N', one, rho_t, 0, kb, 0, zero, P2, 0, 1, 0));
+        GKBA_TRY(add_i_diff(c, hBb, P1, P2, 1.0));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', one, hB, 0, kb, 0, zero, P1, 0, 1, 0));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', one, kb, 0, hB, 0, zero, P2, 0, 1, 0));
+        GKBA_TRY(add_i_diff(c, rtb, P1, P2, 1.0));
+        GKBA_TRY(ibar_from_kbar(c, kb, Ib));
+        // corrector collision over rho_0 .. rho_n, rho~ with T(t_{n+1}, .)
+        double2* slot = c->rho_hist + (size_t)(n + 1) * NN;
+        GKBA_CUDA(c, cudaMemcpyAsync(save, slot, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
+        GKBA_CUDA(c, cudaMemcpyAsync(slot, rho_t, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
+        gkba_status st = collision_vjp_dev(c, n + 2, c->rho_hist, Tcur, nullptr, Ib, srho, sT);
+        GKBA_CUDA(c, cudaMemcpyAsync(slot, save, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
+        GKBA_TRY(st);
+        GKBA_TRY(axpy_c(c, Rb, Rb, srho, 1.0, 1.0, (int)((n + 1) * NN)));
+        GKBA_TRY(axpy_c(c, rtb, rtb, srho + (size_t)(n + 1) * NN, 1.0, 1.0, (int)NN));
+        GKBA_TRY(axpy_c(c, Tb, Tb, sT, 1.0, 1.0, (int)((n + 2) * NN)));
+        // T(t_{n+1}, t_k) = U T(t_n, t_k): Ubar = sum_k Tbar_k T(t_n, t_k)^+, Tbar_k <- U^+ Tbar_k
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'C', one, Tb, NN, Tprv, NN, zero, prod, NN, n + 1, 0));
+        GKBA_TRY(sum_units(c, n + 1, prod, Ub));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'C', 'N', one, U, 0, Tb, NN, zero, prod, NN, n + 1, 0));
+        GKBA_CUDA(c, cudaMemcpyAsync(Tb, prod, (size_t)(n + 1) * NN * 16, cudaMemcpyDeviceToDevice, c->stream));
+        GKBA_CUDA(c, cudaMemsetAsync(Tb + (size_t)(n + 1) * NN, 0, NN * 16, c->stream));
+        // U = exp(-i dt (hA + hB)/2)
+        GKBA_TRY(expm_adj(c, hA, hB, Ub, hAb, hBb, fre));
+        // hB = h + E_{n+1} d + Sigma_HF(rho~)
+        GKBA_TRY(field_grad(c, hBb, Eb + n + 1));
+        GKBA_TRY(mean_field_adj(c, hBb, rtb));
+        // rho~ = rho_n + dt k1
+        GKBA_TRY(axpy_c(c, Rn, Rn, rtb, 1.0, 1.0, (int)NN));
+        GKBA_TRY(axpy_c(c, kb1, kb, rtb, 1.0, dt, (int)NN));
+        // k1 = -i[hA, rho_n] - (I_n + I_n^+)
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'C', one, kb1, 0, rho_n, 0, zero, P1, 0, 1, 0));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'C', 'N', one, rho_n, 0, kb1, 0, zero, P2, 0, 1, 0));
+        GKBA_TRY(add_i_diff(c, hAb, P1, P2, 1.0));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', one, hA, 0, kb1, 0, zero, P1, 0, 1, 0));
+        GKBA_TRY(zgemm_batched(c, K_STEP, N, 'N', 'N', one, kb1, 0, hA, 0, zero, P2, 0, 1, 0));
+        GKBA_TRY(add_i_diff(c, Rn, P1, P2, 1.0));
+        GKBA_TRY(ibar_from_kbar(c, kb1, Ib));
+        // collision over rho_0 .. rho_n with T(t_n, .)
+        GKBA_TRY(collision_vjp_dev(c, n + 1, c->rho_hist, Tprv, nullptr, Ib, srho, sT));
+        GKBA_TRY(axpy_c(c, Rb, Rb, srho, 1.0, 1.0, (int)((n + 1) * NN)));
+        GKBA_TRY(axpy_c(c, Tb, Tb, sT, 1.0, 1.0, (int)((n + 1) * NN)));
+        // hA = h + E_n d + Sigma_HF(rho_n)
+        GKBA_TRY(field_grad(c, hAb, Eb + n));
+        GKBA_TRY(mean_field_adj(c, hAb, Rn));
+        std::swap(Tcur, Tprv);
+    }
+    GKBA_CUDA(c, cudaMemcpyAsync(E_bar, Eb, (size_t)(M + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (rho0_bar)
+        GKBA_CUDA(c, cudaMemcpyAsync(rho0_bar, Rb, NN * 16, cudaMemcpyDeviceToHost, c->stream));
+    return finish(c);
 }
 
 gkba_status gkba_get_stats(gkba_ctx* c, gkba_kernel_stat* stats, int max_stats, int* n_stats,
@@ -1096,8 +1212,14 @@ gkba_status batch_step(gkba_batch* b, const double* E_n, const double* E_np1,
         GKBA_TRY(diagnostics(c, E_n[i], rho_n, c->Ia, c->dscal));
         GKBA_TRY(rhs(c, c->hhf_n, rho_n, c->Ia, c->k1));
         GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k1, 1.0, c->dt, (int)NN));
+        GKBA_CUDA(c, cudaMemcpyAsync(c->rhot_hist + n * NN, rho_t, NN * 16, cudaMemcpyDeviceToDevice,
+                                     c->stream));
         GKBA_TRY(h_hf(c, E_np1[i], rho_t, c->hhf_t));
         GKBA_TRY(expm_step(c, c->hhf_n, c->hhf_t, c->U));
+        GKBA_CUDA(c, cudaMemcpyAsync(c->U_hist + n * NN, c->U, NN * 16, cudaMemcpyDeviceToDevice,
+                                     c->stream));
+        c->E_a[n] = E_n[i];
+        c->E_b[n] = E_np1[i];
         GKBA_TRY(zgemm_batched(c, K_STEP, c->N, 'N', 'N', make_double2(1.0, 0.0), c->U, 0, c->T_a,
                                NN, make_double2(0.0, 0.0), c->T_b, NN, n + 1, 0));
         GKBA_TRY(set_identity(c, c->T_b + (n + 1) * NN, 1));

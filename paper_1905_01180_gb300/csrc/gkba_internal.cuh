@@ -126,6 +126,13 @@ struct gkba_ctx {
     void* formsG3 = nullptr;     // per-unit B operand of S3 when its slot differs (sep_A)
     double2* vjp = nullptr;      // adjoint scratch: 10 blocks of vjp_units N*N units
     int vjp_units = 0;
+    // trajectory record of gkba_step for the adjoint (steps adj_from .. n-1)
+    double2* rhot_hist = nullptr;  // rho~ (predictor) of each step
+    double2* U_hist = nullptr;     // U_n of each step
+    std::vector<double> E_a, E_b;  // E(t_n), E(t_{n+1}) passed to each step
+    int adj_from = 0;              // first recorded step (0 after gkba_init)
+    double2* adj_ws = nullptr;     // backward-pass buffers
+    size_t adj_ws_bytes = 0;
     bool sep_A = false;          // contraction of S3(A, B, C): S3 reads formsG3
     double2* Mb = nullptr;       // per-unit Gbar (= the right factor of S.Gbar), ub * N*N
     double* coef = nullptr;      // per-unit weight (+-c_k), ub
@@ -258,6 +265,17 @@ gkba_status unit_acc(gkba_ctx* c, int nb, double2* y, const double2* x, int tran
 gkba_status scale_units(gkba_ctx* c, int nb, const double* coef, const double2* Ibar, double2* Y);
 gkba_status vjp_points(gkba_ctx* c, int nk, const double2* Gbar, const double2* Gbbar, double2* Pbar,
                        double2* Qbar);
+// adjoint of the Heun step (N x N helpers)
+gkba_status add_i_diff(gkba_ctx* c, double2* y, const double2* a, const double2* b, double s);
+gkba_status ibar_from_kbar(gkba_ctx* c, const double2* kb, double2* Ib);
+gkba_status mean_field_adj(gkba_ctx* c, const double2* hb, double2* rb);
+gkba_status field_grad(gkba_ctx* c, const double2* hb, double* out);
+gkba_status expm_adj(gkba_ctx* c, const double2* hA, const double2* hB, const double2* Ubar,
+                     double2* hA_bar, double2* hB_bar, double2* scratch);
+gkba_status sum_units(gkba_ctx* c, int nb, const double2* src, double2* dst);
+gkba_status collision_vjp_dev(gkba_ctx* c, int L, const double2* rho, const double2* T,
+                              const double* w, const double2* Ibar, double2* rho_bar,
+                              double2* T_bar);
 gkba_status build_forms3_tf32(gkba_ctx* c, int nb, const double2* A);
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
                                    const void* part, bool fp32, double2* S);

@@ -74,7 +74,7 @@ def load():
     L.gkba_get_history.argtypes = [P, ctypes.POINTER(I), P, P]
     L.gkba_get_state.argtypes = [P, ctypes.POINTER(I), P]
     L.gkba_mean_field.argtypes = [P, P, P, I]
-    L.gkba_adjoint.argtypes = [P, P, I, I, P, P, P]
+    L.gkba_adjoint.argtypes = [P, P, P, P]
     L.gkba_get_stats.argtypes = [P, ctypes.POINTER(KernelStat), I, ctypes.POINTER(I),
                                  ctypes.POINTER(ctypes.c_longlong), I]
     L.gkba_last_error.argtypes = [P]
@@ -302,9 +302,17 @@ class Context:
         st = load().gkba_selftest_timeout(self._h, float(limit_ms), el.ctypes.data)
         return st, el
 
-    def adjoint(self, *a, **k):
-        st = load().gkba_adjoint(self._h, None, 0, 0, None, None, None)
-        self._check(st)
+    def adjoint(self, rho_bar_final):
+        """Gradients of L(rho(t_n)) w.r.t. the field samples E(t_0 .. t_n) and
+        rho(t_0) through the steps taken since gkba_init; rho_bar_final =
+        dL/dRe rho(t_n) + i dL/dIm rho(t_n).  Returns (E_bar, rho0_bar)."""
+        rb, rbp = _host(rho_bar_final, np.complex128)
+        n = ctypes.c_int()
+        self._check(load().gkba_get_state(self._h, ctypes.byref(n), None))
+        E_bar = np.zeros(n.value + 1, np.float64)
+        r0 = np.empty((self.N, self.N), np.complex128)
+        self._check(load().gkba_adjoint(self._h, rbp, E_bar.ctypes.data, r0.ctypes.data))
+        return E_bar, r0
 
 
 class Batch:

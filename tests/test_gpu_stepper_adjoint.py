@@ -1,0 +1,114 @@
+"""Adjoint of the Heun stepper (gkba_adjoint): gradients of the final dipole
+L = Re Tr[d rho(t_n)] with respect to the field samples E(t_k) and the
+initial state rho(t_0), through every collision integral of the trajectory.
+
+Pins: central finite differences of the library's own forward propagation
+(FP64), and finite differences of the oracle's propagation (an independent
+forward), at small N.
+"""
+import numpy as np
+import pytest
+
+import gkba_inputs as gi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as p
+    return p
+
+
+def run(P, s, dt, E, rho0=None, precision="fp64"):
+    n = len(E) - 1
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"] if rho0 is None else rho0, dt,
+                    max_steps=n, precision=precision)
+    for k in range(n):
+        rho, _, _ = ctx.step(E[k], E[k + 1])
+    return ctx, float(np.real(np.trace(s["d"] @ rho)))
+
+
+def setup(N=6, n=12, dt=0.05):
+    s = gi.system(N, 8, seed=3)
+    E = 0.2 * np.sin(0.7 * np.arange(n + 1) * dt * 10)
+    return s, dt, E
+
+
+def test_field_gradient_matches_library_finite_differences(P):
+    s, dt, E = setup()
+    ctx, L0 = run(P, s, dt, E)
+    E_bar, rho0_bar = ctx.adjoint(s["d"])
+    ctx.close()
+    eps = 1e-5
+    for k in (0, 3, 7, len(E) - 1):
+        Ep, Em = E.copy(), E.copy()
+        Ep[k] += eps
+        Em[k] -= eps
+        cp, Lp = run(P, s, dt, Ep)
+        cm, Lm = run(P, s, dt, Em)
+        cp.close()
+        cm.close()
+        fd = (Lp - Lm) / (2 * eps)
+        print(f"dL/dE_{k}: adjoint {E_bar[k]:+.10e}  finite differences {fd:+.10e}")
+        assert abs(E_bar[k] - fd) < 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_initial_state_gradient_matches_finite_differences(P):
+    s, dt, E = setup()
+    ctx, L0 = run(P, s, dt, E)
+    _, rho0_bar = ctx.adjoint(s["d"])
+    ctx.close()
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(6, 6)) + 1j * rng.normal(size=(6, 6))
+    D = 0.5 * (X + X.conj().T)  # Hermitian direction (gkba_init checks rho0)
+    eps = 1e-5
+    cp, Lp = run(P, s, dt, E, s["rho0"] + eps * D)
+    cm, Lm = run(P, s, dt, E, s["rho0"] - eps * D)
+    cp.close()
+    cm.close()
+    fd = (Lp - Lm) / (2 * eps)
+    ad = float(np.real(np.sum(np.conj(rho0_bar) * D)))
+    print(f"dL/drho0 along D: adjoint {ad:+.10e}  finite differences {fd:+.10e}")
+    assert abs(ad - fd) < 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_field_gradient_matches_oracle_finite_differences(P):
+    # the independent forward: the oracle's Heun propagation
+    N, n, dt = 4, 8, 0.05
+    s = gi.system(N, 4, seed=5)
+    E = 0.3 * np.cos(np.arange(n + 1) * 0.4)
+    ctx, _ = run(P, s, dt, E)
+    E_bar, _ = ctx.adjoint(s["d"])
+    ctx.close()
+
+    def loss(Ev):
+        pr = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, Ev)
+        return float(np.real(np.trace(s["d"] @ pr.rho[n])))
+
+    eps = 1e-5
+    for k in range(n + 1):
+        Ep, Em = E.copy(), E.copy()
+        Ep[k] += eps
+        Em[k] -= eps
+        fd = (loss(Ep) - loss(Em)) / (2 * eps)
+        assert abs(E_bar[k] - fd) < 1e-6 * max(abs(fd), 1e-3), (k, E_bar[k], fd)
+
+
+def test_split_tf32_gradient_close_to_fp64(P):
+    s, dt, E = setup(N=16, n=10)
+    c64, _ = run(P, s, dt, E)
+    g64, _ = c64.adjoint(s["d"])
+    c64.close()
+    ctf, _ = run(P, s, dt, E, precision="tf32acc")
+    gtf, _ = ctf.adjoint(s["d"])
+    ctf.close()
+    e = np.linalg.norm(gtf - g64) / np.linalg.norm(g64)
+    print(f"split-TF32 (accurate) field gradient vs FP64: rel {e:.2e}")
+    assert e < 1e-3
