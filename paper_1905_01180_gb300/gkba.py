@@ -384,3 +384,34 @@ def collision_autograd(ctx, rho_hist, T_hist, weights=None):
             return rb, tb
 
     return _Collision.apply(rho_hist, T_hist)
+
+
+def dipole_autograd(make_context, E, d=None):
+    """L = Re Tr[d rho(t_n)] after len(E) - 1 Heun steps of a fresh context
+    (``make_context()`` returns a Context at step 0; d defaults to the dipole
+    the context was built with, passed explicitly here) as a torch op of the
+    field samples E (float64 tensor): the backward pass is gkba_adjoint."""
+    import torch
+
+    class _Dipole(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, Ev):
+            e = Ev.detach().cpu().numpy().astype(np.float64)
+            ctx = make_context()
+            rho = None
+            for k in range(len(e) - 1):
+                rho, _, _ = ctx.step(e[k], e[k + 1])
+            fctx.gkba = ctx
+            return torch.tensor(float(np.real(np.trace(d @ rho))), dtype=torch.float64,
+                                device=Ev.device)
+
+        @staticmethod
+        def backward(fctx, gL):
+            ctx = fctx.gkba
+            E_bar, _ = ctx.adjoint(np.asarray(d, np.complex128).conj().T)
+            ctx.close()
+            return gL * torch.as_tensor(E_bar, dtype=torch.float64, device=gL.device)
+
+    if d is None:
+        raise ValueError("pass the dipole matrix d of the loss")
+    return _Dipole.apply(E)

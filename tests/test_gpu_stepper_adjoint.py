@@ -112,3 +112,19 @@ def test_split_tf32_gradient_close_to_fp64(P):
     e = np.linalg.norm(gtf - g64) / np.linalg.norm(g64)
     print(f"split-TF32 (accurate) field gradient vs FP64: rel {e:.2e}")
     assert e < 1e-3
+
+
+def test_dipole_autograd(P):
+    # torch autograd of the final dipole w.r.t. the pulse samples
+    import torch
+    from paper_1905_01180_gb300 import gkba
+    s, dt, E = setup(N=6, n=8)
+    make = lambda: P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=len(E) - 1)
+    Et = torch.tensor(E, dtype=torch.float64, requires_grad=True)
+    L = gkba.dipole_autograd(make, Et, s["d"])
+    L.backward()
+    ctx, L0 = run(P, s, dt, E)
+    E_bar, _ = ctx.adjoint(s["d"])
+    ctx.close()
+    assert abs(L.item() - L0) < 1e-12
+    assert np.allclose(Et.grad.numpy(), E_bar, rtol=1e-12, atol=1e-15)
