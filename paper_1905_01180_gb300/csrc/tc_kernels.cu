@@ -543,6 +543,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 tc_fence_after();
                 const uint32_t dacc = tmem + (uint32_t)(ab * 256);
                 const uint32_t dcor = SPLIT_ACC ? tmem + 256u : dacc;
+                // the last chunk of a plane holds Np % 32 = 16 valid K when Np is an odd
+                // multiple of 16 (the rest is the TMA's zero fill): its zero K steps are
+                // skipped.  kc counts chunks within the plane (no division in this loop:
+                // this thread's issue rate bounds the kernel).
+                const int ktail = (Np & (kKC - 1)) ? (Np & (kKC - 1)) / 8 : 4;
+                int kc = 0;
                 for (int c = 0; c < nchunk; ++c, ++it) {
                     const int slot = (int)(it & 1);
                     const uint32_t sph = (uint32_t)((it >> 1) & 1);
@@ -552,10 +558,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     const uint32_t ahi = tmem + (slot ? 448u : 192u);
                     const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
                     const unsigned long long dl = dBlo0 + ((unsigned long long)(c * chunkB) >> 4);
-                    // the last chunk of a plane holds Np % 32 = 16 valid K when Np is an odd
-                    // multiple of 16 (the rest is the TMA's zero fill): skip its zero K steps
-                    const int kvalid = Np - (c % p.kch) * kKC;
-                    const int ksteps = kvalid >= kKC ? 4 : kvalid / 8;
+                    const int ksteps = kc == p.kch - 1 ? ktail : 4;
+                    if (++kc == p.kch) kc = 0;
 #pragma unroll 1
                     for (int kk = 0; kk < ksteps; ++kk) {
                         const uint32_t ah = ahi + kk * 8, al = ah + 32;
