@@ -54,7 +54,7 @@ def test_sigma3_vs_oracle(P, precision, N):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "tf32"])
-@pytest.mark.parametrize("N,L", [(8, 4), (16, 3)])
+@pytest.mark.parametrize("N,L", [(8, 4), (16, 3), (13, 3), (40, 2)])
 def test_collision_vjp_vs_oracle(P, precision, N, L):
     s = gi.system(N, 8, seed=1)
     rho, T = gi.history(N, L, 0.02, seed=2)

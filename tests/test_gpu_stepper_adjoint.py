@@ -128,3 +128,24 @@ def test_dipole_autograd(P):
     ctx.close()
     assert abs(L.item() - L0) < 1e-12
     assert np.allclose(Et.grad.numpy(), E_bar, rtol=1e-12, atol=1e-15)
+
+
+def test_adjoint_after_batched_steps(P):
+    # gkba_batch_step records the trajectory like gkba_step: the adjoint of a
+    # member equals the adjoint of the same system stepped on its own
+    s, dt, E = setup(N=8, n=6)
+    n = len(E) - 1
+    make = lambda: P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision="tf32")
+    other = gi.system(12, 8, seed=7)
+    a, b = make(), make()
+    c = P.Context(other["h"], other["v"], other["d"], other["rho0"], dt, max_steps=n, precision="tf32")
+    with P.Batch([a, c]) as bt:
+        for k in range(n):
+            bt.step([E[k], 0.0], [E[k + 1], 0.0])
+    for k in range(n):
+        b.step(E[k], E[k + 1])
+    ga, ra = a.adjoint(s["d"])
+    gb, rb = b.adjoint(s["d"])
+    for x in (a, b, c):
+        x.close()
+    assert np.array_equal(ga, gb) and np.array_equal(ra, rb)
