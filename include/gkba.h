@@ -216,10 +216,14 @@ gkba_status gkba_mean_field(gkba_ctx* ctx, const double* rho, double* sigma_hf, 
  * so no checkpoints are needed.  Each step costs two collision-integral
  * adjoints (about eight collision integrals) plus N^3 work, including the
  * Frechet derivative of the exponential (a 2N x 2N exponential).
- * Gradients with respect to v are not provided.  GKBA_EUNSUPPORTED for a
- * structured interaction or a trajectory started by gkba_set_history(n > 0).
+ *   v_bar         N^4 doubles (host, may be NULL): dL/dv_abcd through every
+ *                 collision integral and mean field of the trajectory (each
+ *                 entry an independent real variable); FP64 contexts only.
+ * GKBA_EUNSUPPORTED for a structured interaction, a trajectory started by
+ * gkba_set_history(n > 0), or v_bar on a split-TF32 context.
  */
-gkba_status gkba_adjoint(gkba_ctx* ctx, const double* rho_bar_final, double* E_bar, double* rho0_bar);
+gkba_status gkba_adjoint(gkba_ctx* ctx, const double* rho_bar_final, double* E_bar, double* rho0_bar,
+                         double* v_bar);
 
 /*
  * gkba_get_stats - kernel counters since the last reset: fills up to
@@ -277,10 +281,14 @@ gkba_status gkba_sigma3(gkba_ctx* ctx, int n_units, const double* A, const doubl
  * chained through P_k = T_k rho_k, Q_k = T_k - P_k and the products with
  * P_k^+ / Q_k^+ in FP64.  General interaction only (GKBA_EUNSUPPORTED
  * otherwise).  Costs about four collision integrals.
+ *   v_bar  N^4 doubles or NULL: dL/dv_abcd, every entry an independent real
+ *          variable (chain it to a parametrization of v, e.g. Coulomb
+ *          factors, on the caller's side); FP64 contexts only
+ *          (GKBA_EUNSUPPORTED otherwise); two more chains per unit.
  */
 gkba_status gkba_collision_vjp(gkba_ctx* ctx, int L, const double* rho_hist, const double* T_hist,
                                const double* weights, const double* I_bar, double* rho_bar,
-                               double* T_bar, int on_device);
+                               double* T_bar, double* v_bar, int on_device);
 
 /*
  * Stacked batches of systems: many systems of uneven basis size and history

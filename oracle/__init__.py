@@ -49,6 +49,7 @@ __all__ = [
     "trapezoid_weights",
     "collision",
     "collision_vjp",
+    "collision_vjp_v",
     "hf_self_energy",
     "expm_hermitian",
     "Propagation",
@@ -305,6 +306,31 @@ def collision_vjp(v, rho_hist, T_hist, weights, Ibar):
         rho_bar[k] = T.conj().T @ (Pbar - Qbar)
         T_bar[k] = Pbar @ rho.conj().T + Qbar @ (eye - rho).conj().T
     return rho_bar, T_bar
+
+
+def collision_vjp_v(v, rho_hist, T_hist, weights, Ibar):
+    """Derivative of Re sum conj(Ibar) I with respect to the Coulomb
+    integrals v_abcd (each entry an independent real variable) through the
+    collision integral (first line of Eq. collint).  Per unit (G, Gb) with
+    adjoint Sbar of S (as in ``collision_vjp``), v enters Eq. (2bse) twice:
+      v-slot:  vbar_irpn += Re sum_j conj(Sbar_ij) sum_mqs w_mqsj G_nm Gb_sr G_pq
+      w-slot:  wbar_mqsj += Re sum_i conj(Sbar_ij) sum_rpn v_irpn G_nm Gb_sr G_pq
+    and w_mqsj = 2 v_mqsj - v_qmsj gives vbar_abcd += 2 wbar_abcd - wbar_bacd.
+    """
+    L, N, _ = rho_hist.shape
+    w = exchange_folded(v)
+    vbar = np.zeros((N,) * 4)
+    wbar = np.zeros((N,) * 4)
+    for k in range(L):
+        T, rho, c = T_hist[k], rho_hist[k], weights[k]
+        P = T @ rho
+        Q = T - P
+        for G, Gb, coef in ((P, Q.conj().T, -c), (Q, P.conj().T, c)):
+            Sbar = (coef * Ibar) @ Gb.conj().T
+            Sc = Sbar.conj()
+            vbar += np.real(np.einsum("ij,mqsj,nm,sr,pq->irpn", Sc, w, G, Gb, G, optimize=True))
+            wbar += np.real(np.einsum("ij,irpn,nm,sr,pq->mqsj", Sc, v, G, Gb, G, optimize=True))
+    return vbar + 2.0 * wbar - wbar.transpose(1, 0, 2, 3)
 
 
 def hf_self_energy(v, rho):

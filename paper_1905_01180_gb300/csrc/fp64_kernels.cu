@@ -881,6 +881,68 @@ __global__ void k_sum_units(long long NN, int nb, const double2* __restrict__ sr
     dst[e] = make_double2(re, im);
 }
 
+// ---------------------------------------------------------------------------
+// Gradient with respect to the Coulomb integrals (FP64 path).
+// ---------------------------------------------------------------------------
+// out[a][K] += sum_{u, c, b} S_c(u, a, b) X[u][c][b][K]   (K < N^3)
+// with S_c the real (c = 0) / imaginary (c = 1) part of Sbar_u[a][b], or of
+// Sbar_u[b][a] when transposeS; X planar complex [u][c][N][N^3] (unit stride
+// 2 N^4), i.e. out = Re sum conj(Sbar) X over the contracted index.
+__global__ void k_vbar_slot(int N, int nb, const double2* __restrict__ Sbar, int transposeS,
+                            const double* __restrict__ X, double* __restrict__ out) {
+    const long long N3 = (long long)N * N * N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N3 * N) return;
+    const int a = (int)(e / N3);
+    const long long K = e % N3;
+    const long long NN = (long long)N * N;
+    double acc = 0.0;
+    for (int u = 0; u < nb; ++u) {
+        const double* xu = X + (long long)u * 2 * N * N3;
+        const double2* su = Sbar + (long long)u * NN;
+        for (int b = 0; b < N; ++b) {
+            const double2 sv = transposeS ? su[(long long)b * N + a] : su[(long long)a * N + b];
+            acc = fma(sv.x, xu[(long long)b * N3 + K], acc);
+            acc = fma(sv.y, xu[N3 * N + (long long)b * N3 + K], acc);
+        }
+    }
+    out[e] += acc;
+}
+// vbar[a][b][c][d] += vslot[a][(d, b, c)] + 2 wslot[d][(a, c, b)] - wslot[d][(b, c, a)]
+// (vslot[i][(n,r,p)] = dL/dv_irpn; wslot[j][(m,s,q)] = dL/dw_mqsj, w_mqsj = 2 v_mqsj - v_qmsj)
+__global__ void k_fold_vbar(int N, const double* __restrict__ vslot, const double* __restrict__ wslot,
+                            double* __restrict__ vbar) {
+    const long long n = N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n * n * n) return;
+    const long long d = e % n, c = (e / n) % n, b = (e / n / n) % n, a = e / n / n / n;
+    const long long N3 = n * n * n;
+    double x = vslot[a * N3 + (d * n + b) * n + c];
+    x += 2.0 * wslot[d * N3 + (a * n + c) * n + b];
+    x -= wslot[d * N3 + (b * n + c) * n + a];
+    vbar[e] += x;
+}
+// Mean-field part, for h = ... + Sigma_HF(rho), Sigma_HF_ij = sum_kl (2 v_iklj - v_ikjl) rho_lk:
+// vbar[a][b][c][d] += 2 Re(conj(hbar_ad) rho_cb) - Re(conj(hbar_ac) rho_db)
+__global__ void k_vbar_mean_field(int N, const double2* __restrict__ hb, const double2* __restrict__ rho,
+                                  double* __restrict__ vbar) {
+    const long long n = N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n * n * n) return;
+    const long long d = e % n, c = (e / n) % n, b = (e / n / n) % n, a = e / n / n / n;
+    const double2 h1 = hb[a * n + d], r1 = rho[c * n + b];
+    const double2 h2 = hb[a * n + c], r2 = rho[d * n + b];
+    vbar[e] += 2.0 * (h1.x * r1.x + h1.y * r1.y) - (h2.x * r2.x + h2.y * r2.y);
+}
+// omega layout for the w-slot chain: wO[i][n][p][r] = v_irpn
+__global__ void k_build_vomega64(int N, const double* __restrict__ v, double* __restrict__ out) {
+    const long long n = N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n * n * n) return;
+    const long long r = e % n, p = (e / n) % n, nn = (e / n / n) % n, i = e / n / n / n;
+    out[e] = v[((i * n + r) * n + p) * n + nn];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1191,6 +1253,32 @@ gkba_status sum_units(gkba_ctx* c, int nb, const double2* src, double2* dst) {
     return launch_end(c, t);
 }
 
+gkba_status vbar_slot(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, const double* X,
+                      double* out) {
+    const long long n = (long long)c->N * c->N * c->N * c->N;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_vbar_slot<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, nb, Sbar, transposeS, X, out);
+    return launch_end(c, t);
+}
+gkba_status fold_vbar(gkba_ctx* c, const double* vslot, const double* wslot, double* vbar) {
+    const long long n = (long long)c->N * c->N * c->N * c->N;
+    auto t = launch_begin(c, K_RED, 0.0, 0.0);
+    k_fold_vbar<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, vslot, wslot, vbar);
+    return launch_end(c, t);
+}
+gkba_status vbar_mean_field(gkba_ctx* c, const double2* hb, const double2* rho, double* vbar) {
+    const long long n = (long long)c->N * c->N * c->N * c->N;
+    auto t = launch_begin(c, K_STEP, 0.0, 0.0);
+    k_vbar_mean_field<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, hb, rho, vbar);
+    return launch_end(c, t);
+}
+gkba_status build_vomega64(gkba_ctx* c, double* out) {
+    const long long n = (long long)c->N * c->N * c->N * c->N;
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_build_vomega64<<<grid1(n, 256), 256, 0, c->stream>>>(c->N, c->v, out);
+    return launch_end(c, t);
+}
+
 gkba_status build_forms_fp64(gkba_ctx* c, int nb, const double2* G, const double2* Gb) {
     const long long NN = (long long)c->N * c->N;
     auto t = launch_begin(c, K_PREP, 0.0, 0.0);
@@ -1258,7 +1346,9 @@ gkba_status reduce_batch(gkba_ctx* c, int nb, double2* I_acc, double2* S_out) {
 //   S3  X3[c'][j][n][r][p] = sum_(c,m) X2[(j,r,p)][(c,m)] Gr[(c',n)][(c,m)]
 //   S4  D[(u,c,j)][i] = sum_(n,r,p) X3[u][(c,j)][(n,r,p)] vK[i][(n,r,p)], split-K
 // i.e. W1 = w x_s Gb, W2 = G x_q W1, W3 = G x_m W2, Sigma = v . W3.
-gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
+// Stages S1-S3 of the FP64 chain into X13 = X3[u][c'][j][n][r][p], with A1
+// the stage-S1 operand (w in the [j][m][q][s] layout, or any tensor in it).
+gkba_status fp64_chain_x3(gkba_ctx* c, int nb, const double* A1) {
     const int N = c->N;
     const long long N2 = (long long)N * N, N3 = N2 * N, N4 = N3 * N;
     double* X13 = (double*)c->X13;
@@ -1267,7 +1357,7 @@ gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
     const double fl_cc = 8.0 * (double)N4 * N;   // complex x complex stage, per unit
     {
         StageMap m{2 * N3, 2 * N, 1, N, 2 * N2, N, N, N};
-        GKBA_TRY(gemm64_stage(c, K_W1, c->wS64, N, 0, (const double*)c->formsB1, N, 2 * N2, X13,
+        GKBA_TRY(gemm64_stage(c, K_W1, A1, N, 0, (const double*)c->formsB1, N, 2 * N2, X13,
                               2 * N4, (int)N3, 2 * N, N, nb, 0, 0, m, fl_cr * nb,
                               8.0 * (N4 + 2 * N4 * nb)));
     }
@@ -1284,6 +1374,15 @@ gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
                               X13, 2 * N4, (int)N3, 2 * N, 2 * N, nb, 0, 0, m, fl_cc * nb,
                               8.0 * 4 * N4 * nb));
     }
+    return GKBA_OK;
+}
+
+gkba_status contract_batch_fp64(gkba_ctx* c, int nb) {
+    const int N = c->N;
+    const long long N2 = (long long)N * N, N3 = N2 * N, N4 = N3 * N;
+    double* X13 = (double*)c->X13;
+    const double fl_cr = 4.0 * (double)N4 * N;
+    GKBA_TRY(fp64_chain_x3(c, nb, c->wS64));
     const long long R = 2LL * N * nb;
     const long long Kc = 8192;
     const int nz = (int)((N3 + Kc - 1) / Kc);

@@ -270,7 +270,7 @@ gkba_status sigma3_dev(gkba_ctx* c, int n_units, const double2* A, const double2
 //   rho_bar = T^+ (Pbar - Qbar),  T_bar = (Pbar - Qbar) rho^+ + Qbar.
 gkba_status collision_vjp_dev(gkba_ctx* c, int L, const double2* rho, const double2* T,
                               const double* w, const double2* Ibar, double2* rho_bar,
-                              double2* T_bar) {
+                              double2* T_bar, double* vslot, double* wslot) {
     const int N = c->N;
     const long long NN = (long long)N * N;
     GKBA_TRY(ensure_workspace(c, 2 * L));
@@ -299,6 +299,16 @@ gkba_status collision_vjp_dev(gkba_ctx* c, int L, const double2* rho, const doub
         GKBA_TRY(scale_units(c, nb, c->coef, Ibar, tC));  // Ybar
         GKBA_TRY(zgemm_batched(c, K_RED, N, 'N', 'C', one, tC, NN, Gbv, NN, zero, Sbv, NN, nb, 0));
         GKBA_TRY(zgemm_batched(c, K_RED, N, 'C', 'N', one, Sv, NN, tC, NN, zero, Gbb, NN, nb, 0));
+        if (vslot) {
+            // dL/dv (FP64 path): the v slot against X3 = W3 still in X13 from S above
+            GKBA_TRY(vbar_slot(c, nb, Sbv, 0, (const double*)c->X13, vslot));
+            // the w slot against the same chain run on v in the omega layout with G^T, Gb^T
+            GKBA_TRY(unit_xform(c, nb, Gv, tA, 0, 1));
+            GKBA_TRY(unit_xform(c, nb, Gbv, tB, 0, 1));
+            GKBA_TRY(build_forms(c, nb, tA, NN, tB, NN, 0));
+            GKBA_TRY(fp64_chain_x3(c, nb, c->vomega));
+            GKBA_TRY(vbar_slot(c, nb, Sbv, 1, (const double*)c->X13, wslot));
+        }
         GKBA_TRY(unit_xform(c, nb, Gv, tA, 1, 0));   // G*
         GKBA_TRY(unit_xform(c, nb, Sbv, tB, 0, 1));  // Sbar^T
         GKBA_TRY(contract3(c, nb, tA, tB, tA));
@@ -401,7 +411,8 @@ void free_ctx(gkba_ctx* c) {
     if (!c) return;
     if (c->device >= 0) cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->vjp, c->rhot_hist, c->U_hist, c->adj_ws, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
+    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->vjp, c->rhot_hist, c->U_hist, c->adj_ws, c->vomega,
+                    c->vgrad, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
                     c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
                     c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
                     c->stage};
@@ -699,6 +710,21 @@ gkba_status gkba_collision(gkba_ctx* c, int L, const double* rho_hist, const dou
     return finish(c);
 }
 
+// Buffers of dL/dv (FP64 path): the omega layout of v and three accumulators
+// (v slot N x N^3, w slot N x N^3, natural N^4), zeroed.
+static gkba_status prepare_vgrad(gkba_ctx* c) {
+    if (c->prec != GKBA_FP64)
+        return fail(c, GKBA_EUNSUPPORTED, "dL/dv is computed on the FP64 path only");
+    const size_t N4 = (size_t)c->N * c->N * c->N * c->N;
+    if (!c->vomega) {
+        GKBA_TRY(alloc(c, (void**)&c->vomega, N4 * 8));
+        GKBA_TRY(build_vomega64(c, c->vomega));
+    }
+    if (!c->vgrad) GKBA_TRY(alloc(c, (void**)&c->vgrad, 3 * N4 * 8));
+    GKBA_CUDA(c, cudaMemsetAsync(c->vgrad, 0, 3 * N4 * 8, c->stream));
+    return GKBA_OK;
+}
+
 gkba_status gkba_sigma3(gkba_ctx* c, int n_units, const double* A, const double* B,
                         const double* C, double* S_out, int on_device) {
     if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_sigma3: NULL context");
@@ -735,7 +761,7 @@ gkba_status gkba_sigma3(gkba_ctx* c, int n_units, const double* A, const double*
 
 gkba_status gkba_collision_vjp(gkba_ctx* c, int L, const double* rho_hist, const double* T_hist,
                                const double* weights, const double* I_bar, double* rho_bar,
-                               double* T_bar, int on_device) {
+                               double* T_bar, double* v_bar, int on_device) {
     if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_collision_vjp: NULL context");
     if (L < 1 || !rho_hist || !T_hist || !I_bar || !rho_bar || !T_bar)
         return fail(c, GKBA_EINVAL, "gkba_collision_vjp: need L >= 1 and non-NULL arrays");
@@ -775,7 +801,20 @@ gkba_status gkba_collision_vjp(gkba_ctx* c, int L, const double* rho_hist, const
             dW = w;
         }
     }
-    GKBA_TRY(collision_vjp_dev(c, L, dR, dT, dW, dIb, dRb, dTb));
+    const size_t N4 = NN * NN;
+    double *vs = nullptr, *ws = nullptr;
+    if (v_bar) {
+        GKBA_TRY(prepare_vgrad(c));
+        vs = c->vgrad;
+        ws = c->vgrad + N4;
+    }
+    GKBA_TRY(collision_vjp_dev(c, L, dR, dT, dW, dIb, dRb, dTb, vs, ws));
+    if (v_bar) {
+        GKBA_TRY(fold_vbar(c, vs, ws, c->vgrad + 2 * N4));
+        GKBA_CUDA(c, cudaMemcpyAsync(v_bar, c->vgrad + 2 * N4, N4 * 8,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                     c->stream));
+    }
     if (!on_device) {
         GKBA_CUDA(c, cudaMemcpyAsync(rho_bar, dRb, hb, cudaMemcpyDeviceToHost, c->stream));
         GKBA_CUDA(c, cudaMemcpyAsync(T_bar, dTb, hb, cudaMemcpyDeviceToHost, c->stream));
@@ -889,7 +928,8 @@ gkba_status gkba_get_state(const gkba_ctx* cc, int* n, double* rho) {
     return GKBA_OK;
 }
 
-gkba_status gkba_adjoint(gkba_ctx* c, const double* rho_bar_final, double* E_bar, double* rho0_bar) {
+gkba_status gkba_adjoint(gkba_ctx* c, const double* rho_bar_final, double* E_bar, double* rho0_bar,
+                         double* v_bar) {
     if (!c) return fail(nullptr, GKBA_EINVAL, "gkba_adjoint: NULL context");
     if (!rho_bar_final || !E_bar) return fail(c, GKBA_EINVAL, "gkba_adjoint: NULL argument");
     if (c->kind != GKBA_V_GENERAL)
@@ -928,6 +968,14 @@ gkba_status gkba_adjoint(gkba_ctx* c, const double* rho_bar_final, double* E_bar
     GKBA_CUDA(c, cudaMemsetAsync(Tb, 0, H * sizeof(double2), c->stream));
     GKBA_CUDA(c, cudaMemsetAsync(Eb, 0, (size_t)(M + 1) * 8, c->stream));
     GKBA_TRY(copy_in(c, Rb + (size_t)M * NN, rho_bar_final, NN * 16, 0));
+    const size_t N4 = (size_t)NN * NN;
+    double *vs = nullptr, *ws = nullptr, *vn = nullptr;
+    if (v_bar) {
+        GKBA_TRY(prepare_vgrad(c));
+        vs = c->vgrad;
+        ws = c->vgrad + N4;
+        vn = c->vgrad + 2 * N4;
+    }
     GKBA_CUDA(c, cudaMemcpyAsync(Tcur, c->T_a, (size_t)(M + 1) * NN * 16, cudaMemcpyDeviceToDevice,
                                  c->stream));
     for (int n = M - 1; n >= 0; --n) {
@@ -956,7 +1004,7 @@ gkba_status gkba_adjoint(gkba_ctx* c, const double* rho_bar_final, double* E_bar
         double2* slot = c->rho_hist + (size_t)(n + 1) * NN;
         GKBA_CUDA(c, cudaMemcpyAsync(save, slot, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
         GKBA_CUDA(c, cudaMemcpyAsync(slot, rho_t, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
-        gkba_status st = collision_vjp_dev(c, n + 2, c->rho_hist, Tcur, nullptr, Ib, srho, sT);
+        gkba_status st = collision_vjp_dev(c, n + 2, c->rho_hist, Tcur, nullptr, Ib, srho, sT, vs, ws);
         GKBA_CUDA(c, cudaMemcpyAsync(slot, save, NN * 16, cudaMemcpyDeviceToDevice, c->stream));
         GKBA_TRY(st);
         GKBA_TRY(axpy_c(c, Rb, Rb, srho, 1.0, 1.0, (int)((n + 1) * NN)));
@@ -972,6 +1020,7 @@ gkba_status gkba_adjoint(gkba_ctx* c, const double* rho_bar_final, double* E_bar
         GKBA_TRY(expm_adj(c, hA, hB, Ub, hAb, hBb, fre));
         // hB = h + E_{n+1} d + Sigma_HF(rho~)
         GKBA_TRY(field_grad(c, hBb, Eb + n + 1));
+        if (vn) GKBA_TRY(vbar_mean_field(c, hBb, rho_t, vn));
         GKBA_TRY(mean_field_adj(c, hBb, rtb));
         // rho~ = rho_n + dt k1
         GKBA_TRY(axpy_c(c, Rn, Rn, rtb, 1.0, 1.0, (int)NN));
@@ -985,15 +1034,20 @@ gkba_status gkba_adjoint(gkba_ctx* c, const double* rho_bar_final, double* E_bar
         GKBA_TRY(add_i_diff(c, Rn, P1, P2, 1.0));
         GKBA_TRY(ibar_from_kbar(c, kb1, Ib));
         // collision over rho_0 .. rho_n with T(t_n, .)
-        GKBA_TRY(collision_vjp_dev(c, n + 1, c->rho_hist, Tprv, nullptr, Ib, srho, sT));
+        GKBA_TRY(collision_vjp_dev(c, n + 1, c->rho_hist, Tprv, nullptr, Ib, srho, sT, vs, ws));
         GKBA_TRY(axpy_c(c, Rb, Rb, srho, 1.0, 1.0, (int)((n + 1) * NN)));
         GKBA_TRY(axpy_c(c, Tb, Tb, sT, 1.0, 1.0, (int)((n + 1) * NN)));
         // hA = h + E_n d + Sigma_HF(rho_n)
         GKBA_TRY(field_grad(c, hAb, Eb + n));
+        if (vn) GKBA_TRY(vbar_mean_field(c, hAb, rho_n, vn));
         GKBA_TRY(mean_field_adj(c, hAb, Rn));
         std::swap(Tcur, Tprv);
     }
     GKBA_CUDA(c, cudaMemcpyAsync(E_bar, Eb, (size_t)(M + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (v_bar) {
+        GKBA_TRY(fold_vbar(c, vs, ws, vn));
+        GKBA_CUDA(c, cudaMemcpyAsync(v_bar, vn, N4 * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
     if (rho0_bar)
         GKBA_CUDA(c, cudaMemcpyAsync(rho0_bar, Rb, NN * 16, cudaMemcpyDeviceToHost, c->stream));
     return finish(c);

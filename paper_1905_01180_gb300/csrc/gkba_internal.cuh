@@ -133,6 +133,8 @@ struct gkba_ctx {
     int adj_from = 0;              // first recorded step (0 after gkba_init)
     double2* adj_ws = nullptr;     // backward-pass buffers
     size_t adj_ws_bytes = 0;
+    double* vomega = nullptr;      // v in the [i][n][p][r] layout (w-slot chain of dL/dv)
+    double* vgrad = nullptr;       // dL/dv accumulators: vslot, wslot (N x N^3 each), natural N^4
     bool sep_A = false;          // contraction of S3(A, B, C): S3 reads formsG3
     double2* Mb = nullptr;       // per-unit Gbar (= the right factor of S.Gbar), ub * N*N
     double* coef = nullptr;      // per-unit weight (+-c_k), ub
@@ -273,9 +275,16 @@ gkba_status field_grad(gkba_ctx* c, const double2* hb, double* out);
 gkba_status expm_adj(gkba_ctx* c, const double2* hA, const double2* hB, const double2* Ubar,
                      double2* hA_bar, double2* hB_bar, double2* scratch);
 gkba_status sum_units(gkba_ctx* c, int nb, const double2* src, double2* dst);
+// gradient with respect to v (FP64 path)
+gkba_status fp64_chain_x3(gkba_ctx* c, int nb, const double* A1);
+gkba_status vbar_slot(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, const double* X,
+                      double* out);
+gkba_status fold_vbar(gkba_ctx* c, const double* vslot, const double* wslot, double* vbar);
+gkba_status vbar_mean_field(gkba_ctx* c, const double2* hb, const double2* rho, double* vbar);
+gkba_status build_vomega64(gkba_ctx* c, double* out);
 gkba_status collision_vjp_dev(gkba_ctx* c, int L, const double2* rho, const double2* T,
                               const double* w, const double2* Ibar, double2* rho_bar,
-                              double2* T_bar);
+                              double2* T_bar, double* vslot = nullptr, double* wslot = nullptr);
 gkba_status build_forms3_tf32(gkba_ctx* c, int nb, const double2* A);
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
                                    const void* part, bool fp32, double2* S);

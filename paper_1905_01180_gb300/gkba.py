@@ -74,7 +74,7 @@ def load():
     L.gkba_get_history.argtypes = [P, ctypes.POINTER(I), P, P]
     L.gkba_get_state.argtypes = [P, ctypes.POINTER(I), P]
     L.gkba_mean_field.argtypes = [P, P, P, I]
-    L.gkba_adjoint.argtypes = [P, P, P, P]
+    L.gkba_adjoint.argtypes = [P, P, P, P, P]
     L.gkba_get_stats.argtypes = [P, ctypes.POINTER(KernelStat), I, ctypes.POINTER(I),
                                  ctypes.POINTER(ctypes.c_longlong), I]
     L.gkba_last_error.argtypes = [P]
@@ -85,7 +85,7 @@ def load():
     L.gkba_batch_create.argtypes = [ctypes.POINTER(P), P, I, ctypes.c_size_t]
     L.gkba_selftest_timeout.argtypes = [P, D, P]
     L.gkba_sigma3.argtypes = [P, I, P, P, P, P, I]
-    L.gkba_collision_vjp.argtypes = [P, I, P, P, P, P, P, P, I]
+    L.gkba_collision_vjp.argtypes = [P, I, P, P, P, P, P, P, P, I]
     L.gkba_batch_step.argtypes = [P, P, P, P, P]
     L.gkba_batch_last_error.argtypes = [P]
     L.gkba_batch_last_error.restype = ctypes.c_char_p
@@ -222,8 +222,9 @@ class Context:
         self._check(load().gkba_sigma3(self._h, n, ap, bp, cp, out.ctypes.data, 0))
         return out
 
-    def collision_vjp(self, rho_hist, T_hist, I_bar, weights=None):
-        """Adjoint of ``collision``: (rho_bar, T_bar) for I_bar = dL/dRe I + i dL/dIm I."""
+    def collision_vjp(self, rho_hist, T_hist, I_bar, weights=None, want_v=False):
+        """Adjoint of ``collision``: (rho_bar, T_bar[, v_bar]) for
+        I_bar = dL/dRe I + i dL/dIm I (v_bar: FP64 contexts, host arrays)."""
         Lh = int(rho_hist.shape[0])
         if _is_torch(rho_hist):
             import torch
@@ -235,7 +236,7 @@ class Context:
             rb = torch.empty_like(r)
             tb = torch.empty_like(t)
             self._check(load().gkba_collision_vjp(self._h, Lh, rp, tp, wp, ibp, rb.data_ptr(),
-                                                  tb.data_ptr(), 1))
+                                                  tb.data_ptr(), None, 1))
             return rb, tb
         r, rp = _host(rho_hist, np.complex128); t, tp = _host(T_hist, np.complex128)
         ib, ibp = _host(I_bar, np.complex128)
@@ -244,9 +245,10 @@ class Context:
             w, wp = _host(weights, np.float64)
         rb = np.empty_like(r)
         tb = np.empty_like(t)
+        vb = np.empty((self.N,) * 4, np.float64) if want_v else None
         self._check(load().gkba_collision_vjp(self._h, Lh, rp, tp, wp, ibp, rb.ctypes.data,
-                                              tb.ctypes.data, 0))
-        return rb, tb
+                                              tb.ctypes.data, vb.ctypes.data if want_v else None, 0))
+        return (rb, tb, vb) if want_v else (rb, tb)
 
     def step(self, E_n, E_np1):
         """One Heun step; returns (rho_{n+1}, I(t_n), diag(t_n))."""
@@ -302,17 +304,20 @@ class Context:
         st = load().gkba_selftest_timeout(self._h, float(limit_ms), el.ctypes.data)
         return st, el
 
-    def adjoint(self, rho_bar_final):
-        """Gradients of L(rho(t_n)) w.r.t. the field samples E(t_0 .. t_n) and
-        rho(t_0) through the steps taken since gkba_init; rho_bar_final =
-        dL/dRe rho(t_n) + i dL/dIm rho(t_n).  Returns (E_bar, rho0_bar)."""
+    def adjoint(self, rho_bar_final, want_v=False):
+        """Gradients of L(rho(t_n)) w.r.t. the field samples E(t_0 .. t_n),
+        rho(t_0) [and v, FP64 contexts] through the steps taken since
+        gkba_init; rho_bar_final = dL/dRe rho(t_n) + i dL/dIm rho(t_n).
+        Returns (E_bar, rho0_bar[, v_bar])."""
         rb, rbp = _host(rho_bar_final, np.complex128)
         n = ctypes.c_int()
         self._check(load().gkba_get_state(self._h, ctypes.byref(n), None))
         E_bar = np.zeros(n.value + 1, np.float64)
         r0 = np.empty((self.N, self.N), np.complex128)
-        self._check(load().gkba_adjoint(self._h, rbp, E_bar.ctypes.data, r0.ctypes.data))
-        return E_bar, r0
+        vb = np.empty((self.N,) * 4, np.float64) if want_v else None
+        self._check(load().gkba_adjoint(self._h, rbp, E_bar.ctypes.data, r0.ctypes.data,
+                                        vb.ctypes.data if want_v else None))
+        return (E_bar, r0, vb) if want_v else (E_bar, r0)
 
 
 class Batch:

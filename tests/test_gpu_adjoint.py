@@ -91,3 +91,32 @@ def test_collision_autograd(P):
     ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.02))
     assert rel(I.detach().cpu().numpy(), ref) < 1e-10
     ctx.close()
+
+
+def test_collision_vjp_v_vs_oracle(P):
+    # dL/dv through the collision integral (FP64 path) against the oracle's
+    # slot-by-slot einsum derivative (pinned by finite differences)
+    N, L = 5, 3
+    s = gi.system(N, 8, seed=6)
+    rho, T = gi.history(N, L, 0.02, seed=7)
+    Ibar = cplx(np.random.default_rng(8), N, N)
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.02)
+    rb, tb, vb = ctx.collision_vjp(rho, T, Ibar, want_v=True)
+    ctx.close()
+    ref = O.collision_vjp_v(s["v"], rho, T, O.trapezoid_weights(L, 0.02), Ibar)
+    e = rel(vb, ref)
+    print(f"N={N} L={L} collision dL/dv rel err {e:.2e}")
+    assert e < 1e-10
+    rr, tr = O.collision_vjp(s["v"], rho, T, O.trapezoid_weights(L, 0.02), Ibar)
+    assert rel(rb, rr) < 1e-10 and rel(tb, tr) < 1e-10
+
+
+def test_v_gradient_needs_fp64(P):
+    N = 4
+    s = gi.system(N, 4, seed=1)
+    rho, T = gi.history(N, 2, 0.02, seed=2)
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.02, precision="tf32")
+    with pytest.raises(P.GKBAError) as ei:
+        ctx.collision_vjp(rho, T, np.eye(N, dtype=complex), want_v=True)
+    assert ei.value.status == P.gkba.EUNSUPPORTED
+    ctx.close()

@@ -149,3 +149,34 @@ def test_adjoint_after_batched_steps(P):
     for x in (a, b, c):
         x.close()
     assert np.array_equal(ga, gb) and np.array_equal(ra, rb)
+
+
+def symmetrize8(x):
+    perms = [(0, 1, 2, 3), (1, 0, 3, 2), (3, 2, 1, 0), (2, 3, 0, 1),
+             (3, 1, 2, 0), (1, 3, 0, 2), (0, 2, 1, 3), (2, 0, 3, 1)]
+    return sum(x.transpose(p) for p in perms) / 8.0
+
+
+def test_coulomb_gradient_matches_finite_differences(P):
+    # dL/dv through every collision integral and mean field of the trajectory,
+    # along an 8-fold symmetric direction (gkba_init accepts v +- eps dv)
+    N, n, dt = 5, 8, 0.05
+    s = gi.system(N, 6, seed=8)
+    E = 0.2 * np.sin(np.arange(n + 1) * 0.5)
+    ctx, _ = run(P, s, dt, E)
+    _, _, vbar = ctx.adjoint(s["d"], want_v=True)
+    ctx.close()
+    dv = symmetrize8(np.random.default_rng(10).normal(size=(N,) * 4))
+    eps = 1e-6
+
+    def loss(vv):
+        s2 = dict(s)
+        s2["v"] = vv
+        c, L = run(P, s2, dt, E)
+        c.close()
+        return L
+
+    fd = (loss(s["v"] + eps * dv) - loss(s["v"] - eps * dv)) / (2 * eps)
+    ad = float(np.sum(vbar * dv))
+    print(f"dL/dv along dv: adjoint {ad:+.10e}  finite differences {fd:+.10e}")
+    assert abs(ad - fd) < 1e-6 * max(abs(fd), 1e-3)

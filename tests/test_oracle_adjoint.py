@@ -90,3 +90,38 @@ def test_slot_derivatives_are_sigma3_evaluations():
                 + np.einsum("irpn,mqsj,nm,sr,ij->pq", v, w, Gc, Gbc, Sbar, optimize=True))
     assert rel(O.sigma3(v, Gc, Sbar.T, Gc).T, gb_direct) < 1e-13
     assert rel(O.sigma3(v, Sbar, Gc.T, Gbc.T) + O.sigma3(v, Gbc.T, Gc.T, Sbar), g_direct) < 1e-13
+
+
+def symmetrize8(x):
+    """Average over the 8-fold permutation group of Eq. (symmetries)."""
+    perms = [(0, 1, 2, 3), (1, 0, 3, 2), (3, 2, 1, 0), (2, 3, 0, 1),
+             (3, 1, 2, 0), (1, 3, 0, 2), (0, 2, 1, 3), (2, 0, 3, 1)]
+    return sum(x.transpose(p) for p in perms) / 8.0
+
+
+def test_collision_vjp_v_matches_finite_differences():
+    # L(v) = Re sum conj(Ibar) I(v) along an 8-fold symmetric direction
+    N, L = 4, 3
+    v = gi.random_symmetric_v(N, seed=11)
+    rng = np.random.default_rng(12)
+    rho, T = cplx(rng, L, N, N) * 0.3, cplx(rng, L, N, N) * 0.3
+    w = np.array([0.01, 0.02, 0.01])
+    Ibar = cplx(rng, N, N)
+    dv = symmetrize8(rng.normal(size=(N,) * 4))
+    assert np.allclose(dv, dv.transpose(1, 0, 3, 2)) and np.allclose(dv, dv.transpose(3, 2, 1, 0))
+    vbar = O.collision_vjp_v(v, rho, T, w, Ibar)
+    f = lambda e: np.real(np.sum(np.conj(Ibar) * O.collision(v + e * dv, rho, T, w)))
+    eps = 1e-5
+    fd = (f(eps) - f(-eps)) / (2 * eps)
+    ad = float(np.sum(vbar * dv))
+    assert abs(fd - ad) < 1e-7 * max(abs(fd), 1.0), (fd, ad)
+    # planted mistake: the v slot alone (the w = 2v - v_exch slot dropped)
+    wf = O.exchange_folded(v)
+    vslot = np.zeros((N,) * 4)
+    for k in range(L):
+        P = T[k] @ rho[k]
+        Q = T[k] - P
+        for G, Gb, coef in ((P, Q.conj().T, -w[k]), (Q, P.conj().T, w[k])):
+            Sc = ((coef * Ibar) @ Gb.conj().T).conj()
+            vslot += np.real(np.einsum("ij,mqsj,nm,sr,pq->irpn", Sc, wf, G, Gb, G, optimize=True))
+    assert abs(float(np.sum(vslot * dv)) - fd) > 1e-3 * abs(fd)
