@@ -420,3 +420,14 @@ def dipole_autograd(make_context, E, d=None):
     if d is None:
         raise ValueError("pass the dipole matrix d of the loss")
     return _Dipole.apply(E)
+
+
+def coulomb_factor_grad(B, v_bar):
+    """dL/dB^P for Coulomb integrals built from factors, v_ijkl = sum_P
+    B^P_il B^P_jk (B real, shape (n_P, N, N)), given dL/dv (every entry of v
+    an independent variable, as gkba_adjoint / gkba_collision_vjp return it):
+    dL/dB^P_ab = sum_jk vbar_ajkb B^P_jk + sum_il vbar_iabl B^P_il."""
+    B = np.asarray(B, np.float64)
+    vb = np.asarray(v_bar, np.float64)
+    return (np.einsum("ajkb,pjk->pab", vb, B, optimize=True)
+            + np.einsum("iabl,pil->pab", vb, B, optimize=True))

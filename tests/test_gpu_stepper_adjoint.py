@@ -180,3 +180,37 @@ def test_coulomb_gradient_matches_finite_differences(P):
     ad = float(np.sum(vbar * dv))
     print(f"dL/dv along dv: adjoint {ad:+.10e}  finite differences {fd:+.10e}")
     assert abs(ad - fd) < 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_coulomb_factor_gradient(P):
+    # gradients of the final dipole w.r.t. the Coulomb factors B^P of
+    # v = sum_P B^P (x) B^P, along a direction that keeps every B^P symmetric
+    from paper_1905_01180_gb300 import gkba
+    N, nP, n, dt = 4, 3, 6, 0.05
+    s = gi.system(N, 4, seed=12)
+    rng = np.random.default_rng(13)
+    B = rng.normal(size=(nP, N, N)) * 0.4
+    B = 0.5 * (B + B.transpose(0, 2, 1))
+    vofB = lambda b: np.einsum("pil,pjk->ijkl", b, b)
+    E = 0.2 * np.cos(np.arange(n + 1) * 0.3)
+
+    def forward(b):
+        s2 = dict(s)
+        s2["v"] = vofB(b)
+        return run(P, s2, dt, E)
+
+    ctx, _ = forward(B)
+    _, _, vbar = ctx.adjoint(s["d"], want_v=True)
+    ctx.close()
+    gB = gkba.coulomb_factor_grad(B, vbar)
+    dB = rng.normal(size=B.shape)
+    dB = 0.5 * (dB + dB.transpose(0, 2, 1))
+    eps = 1e-6
+    cp, Lp = forward(B + eps * dB)
+    cm, Lm = forward(B - eps * dB)
+    cp.close()
+    cm.close()
+    fd = (Lp - Lm) / (2 * eps)
+    ad = float(np.sum(gB * dB))
+    print(f"dL/dB along dB: adjoint {ad:+.10e}  finite differences {fd:+.10e}")
+    assert abs(ad - fd) < 1e-6 * max(abs(fd), 1e-3)
