@@ -117,6 +117,10 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert lib.gkba_batch_step(None, None, None, None, None) == gkba.EINVAL
     lib.gkba_batch_destroy(None)
     assert lib.gkba_selftest_timeout(None, 10.0, None) == gkba.EINVAL
+    # gradients and the trilinear form: NULL context or arrays are refused on the host
+    assert lib.gkba_sigma3(None, 1, None, None, None, None, 0) == gkba.EINVAL
+    assert lib.gkba_collision_vjp(None, 1, None, None, None, None, None, None, None, 0) == gkba.EINVAL
+    assert lib.gkba_adjoint(None, None, None, None, None) == gkba.EINVAL
 
 
 def test_null_context_calls_fail_cleanly(lib):

@@ -214,3 +214,33 @@ def test_coulomb_factor_gradient(P):
     ad = float(np.sum(gB * dB))
     print(f"dL/dB along dB: adjoint {ad:+.10e}  finite differences {fd:+.10e}")
     assert abs(ad - fd) < 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_adjoint_refusals(P):
+    # a trajectory that did not start at step 0, a structured interaction and
+    # dL/dv on a split-TF32 context are refused (no partial results)
+    N, dt = 6, 0.05
+    s = gi.system(N, 4, seed=2)
+    rho, T = gi.history(N, 3, dt, seed=3)
+    c = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=4)
+    c.set_history(2, rho, T)
+    c.step(0.0, 0.0)
+    with pytest.raises(P.GKBAError) as ei:
+        c.adjoint(s["d"])
+    assert ei.value.status == P.gkba.EUNSUPPORTED
+    c.close()
+    ch = gi.chain(6, "diagonal")
+    c = P.Context(ch["h"], ch["v"], ch["d"], ch["rho0"], dt, max_steps=2, interaction="diagonal")
+    c.step(0.0, 0.0)
+    with pytest.raises(P.GKBAError) as ei:
+        c.adjoint(ch["d"])
+    assert ei.value.status == P.gkba.EUNSUPPORTED
+    c.close()
+    c = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=2, precision="tf32")
+    c.step(0.0, 0.0)
+    with pytest.raises(P.GKBAError) as ei:
+        c.adjoint(s["d"], want_v=True)
+    assert ei.value.status == P.gkba.EUNSUPPORTED
+    E_bar, _ = c.adjoint(s["d"])  # field gradients work on the split-TF32 path
+    assert np.isfinite(E_bar).all()
+    c.close()
