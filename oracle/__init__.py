@@ -55,6 +55,11 @@ __all__ = [
     "Propagation",
     "propagate",
     "energy",
+    "time_linear_factors",
+    "time_linear_term",
+    "time_linear_apply",
+    "collision_time_linear",
+    "propagate_time_linear",
 ]
 
 # --------------------------------------------------------------------------
@@ -333,6 +338,75 @@ def collision_vjp_v(v, rho_hist, T_hist, weights, Ibar):
     return vbar + 2.0 * wbar - wbar.transpose(1, 0, 2, 3)
 
 
+
+# --------------------------------------------------------------------------
+# Time-linear form of the history sum (an extension; not in the paper)
+#
+# With the HF propagator of Eq. (prop) as a product of one-step unitaries,
+# T(t_n, t_k) = Ucal_n Ucal_k^dag (Ucal_0 = 1, Ucal_{k+1} = U_k Ucal_k), the
+# GKBA pieces of history point k factor as
+#   P_k = T rho_k = Ucal_n X_k,          X_k    = Ucal_k^dag rho_k
+#   Q_k = T - P_k = Ucal_n Xb_k,         Xb_k   = Ucal_k^dag (1 - rho_k)
+#   P_k^dag = X_k^dag Ucal_n^dag,        Q_k^dag = Xb_k^dag Ucal_n^dag.
+# Substituting into Eq. (2bse) moves every Ucal_n onto the indices that v
+# carries (n, p with Ucal, r with conj(Ucal)) and onto the right factor of the
+# first line of Eq. (collint), so that
+#   I(t_n) = [sum_{npr} v_irpn (Ucal x_n Ucal x_p conj(Ucal) x_r Lambda_n)] Ucal_n^dag,
+#   Lambda_n = sum_k c_k [Z(Xb_k, X_k) x_j X_k^dag - Z(X_k, Xb_k) x_j Xb_k^dag],
+#   Z(A, B)_{a b c j} = sum_{mqs} w_mqsj A_am A_bq conj(B)_cs.
+# Lambda_n is an N^4 tensor that changes only by the terms of new history
+# points (and the trapezoid end weights), so a step costs O(N^5) whatever the
+# history length.  The result equals ``collision`` up to rounding.
+# --------------------------------------------------------------------------
+
+
+def time_linear_factors(Ucal_k, rho_k):
+    """X_k = Ucal_k^dag rho_k and Xb_k = Ucal_k^dag (1 - rho_k) (batched)."""
+    Uh = np.conj(np.swapaxes(Ucal_k, -1, -2))
+    X = Uh @ rho_k
+    return X, Uh - X
+
+
+def _z_tensor(w, A, B):
+    """Z(A, B)_{abcj} = sum_{mqs} w_mqsj A_am A_bq conj(B)_cs, one index at a time."""
+    y1 = np.einsum("mqsj,cs->mqcj", w, np.conj(B))
+    y2 = np.einsum("bq,mqcj->mbcj", A, y1)
+    return np.einsum("am,mbcj->abcj", A, y2)
+
+
+def time_linear_term(v, X, Xb):
+    """The t-independent contribution of one history point (weight 1):
+    Z(Xb, X) x_j X^dag - Z(X, Xb) x_j Xb^dag, as Lambda[a][b][c][j']."""
+    w = exchange_folded(v)
+    Xh, Xbh = np.conj(X.T), np.conj(Xb.T)
+    greater = np.einsum("abcj,jk->abck", _z_tensor(w, Xb, X), Xh)
+    lesser = np.einsum("abcj,jk->abck", _z_tensor(w, X, Xb), Xbh)
+    return greater - lesser
+
+
+def time_linear_apply(v, Lam, Ucal_n):
+    """I(t_n) from the accumulated tensor: move Ucal_n back onto the three v
+    indices, contract with v as in Eq. (2bse), multiply by Ucal_n^dag."""
+    l1 = np.einsum("na,abcd->nbcd", Ucal_n, Lam)
+    l2 = np.einsum("pb,nbcd->npcd", Ucal_n, l1)
+    l3 = np.einsum("rc,npcd->nprd", np.conj(Ucal_n), l2)
+    S = np.einsum("irpn,nprd->id", v, l3)
+    return S @ np.conj(Ucal_n.T)
+
+
+def collision_time_linear(v, rho_hist, Ucal_hist, Ucal_n, weights):
+    """First line of Eq. (collint) for T(t_n, t_k) = Ucal_n Ucal_k^dag via the
+    accumulated tensor: Lambda = sum_k c_k term_k, I = apply(Lambda, Ucal_n)."""
+    N = rho_hist.shape[-1]
+    Lam = np.zeros((N,) * 4, np.complex128)
+    for k in range(rho_hist.shape[0]):
+        if weights[k] == 0.0:
+            continue
+        X, Xb = time_linear_factors(Ucal_hist[k], rho_hist[k])
+        Lam += weights[k] * time_linear_term(v, X, Xb)
+    return time_linear_apply(v, Lam, Ucal_n)
+
+
 def hf_self_energy(v, rho):
     """(Sigma_HF)_ij = sum_kl (2 v_iklj - v_ikjl) rho_lk (Sec. II)."""
     return 2.0 * np.einsum("iklj,lk->ij", v, rho) - np.einsum("ikjl,lk->ij", v, rho)
@@ -417,6 +491,53 @@ def propagate(h, v, d, rho0, dt, n_steps, E_samples, route="independent"):
         U = expm_hermitian(0.5 * (hhf_n + hhf_t), dt)
         T_row = [U @ T for T in T_row] + [np.eye(N, dtype=np.complex128)]
         I_t = coll(rho_hist + [rho_t], T_row)
+        k2 = _rhs(hhf_t, rho_t, I_t)
+        rho_hist.append(rho_n + 0.5 * dt * (k1 + k2))
+
+    return Propagation(np.array(rho_hist), np.array(Is), np.asarray(E_samples[: n_steps + 1]),
+                       np.array(energies), np.array(ecs))
+
+
+def propagate_time_linear(h, v, d, rho0, dt, n_steps, E_samples):
+    """``propagate`` with the collision integrals taken from the accumulated
+    tensor of ``collision_time_linear`` instead of the history sum.
+
+    Ucal_0 = 1 and Ucal_{n+1} = U_n Ucal_n with the same U_n as ``propagate``.
+    Lambda_acc holds the history points t_0 .. t_{n-1} with the weights they
+    keep from then on (dt/2 for t_0, dt after it); the point t_n (k1) or the
+    predicted point t_{n+1} (k2, rho~) enters with the trapezoid end weight
+    dt/2, and rho_n is added to Lambda_acc once it is final.
+    """
+    N = rho0.shape[0]
+    eye = np.eye(N, dtype=np.complex128)
+    rho_hist = [rho0.copy()]
+    Ucal = eye.copy()
+    lam_acc = np.zeros((N,) * 4, np.complex128)
+    Is, energies, ecs = [], [], []
+
+    def term(rho, Uc):
+        X, Xb = time_linear_factors(Uc, rho)
+        return time_linear_term(v, X, Xb)
+
+    for n in range(n_steps + 1):
+        rho_n = rho_hist[n]
+        hhf_n = h + E_samples[n] * d + hf_self_energy(v, rho_n)
+        t_n = term(rho_n, Ucal)
+        I_n = np.zeros((N, N), np.complex128) if n == 0 else \
+            time_linear_apply(v, lam_acc + 0.5 * dt * t_n, Ucal)
+        Is.append(I_n)
+        et, ec = energy(h, d, E_samples[n], v, rho_n, I_n)
+        energies.append(et)
+        ecs.append(ec)
+        if n == n_steps:
+            break
+        k1 = _rhs(hhf_n, rho_n, I_n)
+        rho_t = rho_n + dt * k1
+        hhf_t = h + E_samples[n + 1] * d + hf_self_energy(v, rho_t)
+        U = expm_hermitian(0.5 * (hhf_n + hhf_t), dt)
+        lam_acc = lam_acc + (0.5 * dt if n == 0 else dt) * t_n
+        Ucal = U @ Ucal
+        I_t = time_linear_apply(v, lam_acc + 0.5 * dt * term(rho_t, Ucal), Ucal)
         k2 = _rhs(hhf_t, rho_t, I_t)
         rho_hist.append(rho_n + 0.5 * dt * (k1 + k2))
 
