@@ -61,6 +61,8 @@ def parse():
                     help="time 32 systems of uneven N and L stacked in one batch vs one by one")
     ap.add_argument("--chains", action="store_true",
                     help="time the Sec. IV propagations at N_b = 10 (Table I context)")
+    ap.add_argument("--time-linear", action="store_true",
+                    help="time gkba_step with the time-linear history (FP64) at N and exit")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one split-TF32 collision over one history point at N "
                          "with a two-unit workspace (the small case for ncu captures) and exit")
@@ -266,6 +268,49 @@ def run_chains(a):
               flush=True)
 
 
+def run_time_linear(a):
+    """gkba_step with cfg.history = GKBA_HISTORY_TIME_LINEAR (FP64) at N: the
+    history sum kept as one N^4 accumulator, so a step's cost does not depend
+    on the history length.  W warm-up steps from the initial state, then K
+    timed steps (CUDA events on the context's stream); the per-step work is the
+    same at any step index."""
+    import torch
+    import gkba_inputs as gi
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as P
+    N, dt = a.N, a.dt
+    s = gi.system(N, a.nP, seed=0)
+    stream = torch.cuda.current_stream()
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=a.warmup + a.steps + 1,
+                    precision="fp64", stream=stream.cuda_stream, timing=True,
+                    history="time_linear")
+    for _ in range(a.warmup):
+        ctx.step(0.0, 0.0)
+    ctx.stats(reset=True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        _, _, diag = ctx.step(0.0, 0.0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    stats, launches = ctx.stats(reset=True)
+    ctx.close()
+    flops = sum(v["flops"] for v in stats.values()) / a.steps
+    kern_ms = sum(v["ms"] for v in stats.values()) / a.steps
+    print(json.dumps({"workload": f"gkba_time_linear_step_N{N}", "metric": "GKBA Heun step time",
+                      "value": ms / 1e3, "unit": "s", "higher_is_better": False,
+                      "precision": "fp64", "history": "time_linear", "N": N, "n_P": a.nP,
+                      "steps": a.steps, "warmup": a.warmup, "flops_per_step": flops,
+                      "fp64_tflops": flops / (ms * 1e-3) / 1e12, "timed_kernel_ms": kern_ms,
+                      "gpu_launches": launches,
+                      "classes": {k: {"ms": v["ms"] / a.steps, "launches": v["launches"] // a.steps}
+                                  for k, v in stats.items() if v["launches"]},
+                      "trace": float(diag[0])}), flush=True)
+
+
 def run_batch(a):
     """Many systems of uneven size and history length: 32 seeded systems with
     N in {8, 12, 16, 24, 32, 48} and L in U[500, 3000] (then U[20, 200]), one Heun step each
@@ -334,6 +379,9 @@ def main():
         return
     if a.chains:
         run_chains(a)
+        return
+    if a.time_linear:
+        run_time_linear(a)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

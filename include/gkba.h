@@ -79,6 +79,16 @@ typedef enum {
                              Eq. (2b-symm), bubble and exchange */
 } gkba_interaction;
 
+typedef enum {
+    GKBA_HISTORY_SUM = 0,        /* each collision integral of gkba_step sums Eq. (collint)
+                                    over the whole history: O(L N^5) per step */
+    GKBA_HISTORY_TIME_LINEAR = 1 /* gkba_step keeps the history sum as one N^4 accumulator
+                                    (T(t_n,t_k) = Ucal_n Ucal_k^+ factored out; an extension,
+                                    not in the paper): O(N^5) per step at any history
+                                    length, the same result up to rounding.  FP64 and a
+                                    general v only; 2 x 16 N^4 bytes more device memory */
+} gkba_history;
+
 typedef struct {
     int N;             /* basis size, 1 <= N <= 128 (tensor-core modes: N <= 96) */
     double dt;         /* time step delta (> 0) */
@@ -100,6 +110,9 @@ typedef struct {
                           tensor-core accumulation error. */
     int interaction;   /* gkba_interaction: form of the v argument of gkba_init;
                           GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC need precision GKBA_FP64 */
+    int history;       /* gkba_history: how gkba_step evaluates the history sum
+                          (GKBA_HISTORY_TIME_LINEAR needs GKBA_FP64 and
+                          GKBA_V_GENERAL, else GKBA_EUNSUPPORTED) */
 } gkba_config;
 
 /* Per-kernel-class counters (see gkba_get_stats). */
@@ -171,7 +184,12 @@ gkba_status gkba_collision(gkba_ctx* ctx, int L, const double* rho_hist, const d
  *   diag_out  4 doubles at t_n: {Tr rho_n, E_total, E_corr, Re Tr I_n} with
  *             E_total = Tr[(h+E_n d) rho_n] + 1/2 Tr[Sigma_HF rho_n] + E_corr,
  *             E_corr = 1/2 Im Tr I_n (per spin).
- * GKBA_ESTATE when the history is full (n == cfg.max_steps).
+ * With cfg.history = GKBA_HISTORY_TIME_LINEAR both collision integrals come
+ * from the accumulator (time_linear.cu): k1's adds rho_n's term with weight
+ * dt/2 to the points t_0..t_{n-1}, k2's rho~'s term; rho_n's term then joins
+ * the accumulator with its final weight.
+ * GKBA_ESTATE when the history is full (n == cfg.max_steps), or in the
+ * time-linear mode after a failed step (gkba_set_history restores a state).
  */
 gkba_status gkba_step(gkba_ctx* ctx, double E_n, double E_np1, double* rho_out, double* I_out,
                       double* diag_out);
@@ -180,7 +198,10 @@ gkba_status gkba_step(gkba_ctx* ctx, double E_n, double E_np1, double* rho_out, 
  * gkba_set_history - replace the stepper state (checkpoint restore): the
  * history t_0 .. t_n with rho_hist[k] = rho(t_k) and T_hist[k] = T(t_n, t_k),
  * k = 0..n (n + 1 points; T_hist[n] should be the identity).
- * GKBA_EINVAL when n > cfg.max_steps.
+ * GKBA_EINVAL when n > cfg.max_steps.  In the time-linear mode T_hist[n]
+ * must be the identity (max deviation 1e-12, else GKBA_EINVAL) and the
+ * accumulator is rebuilt from the n points before t_n with Ucal_k^+ =
+ * T_hist[k] (O(n N^5) once).
  */
 gkba_status gkba_set_history(gkba_ctx* ctx, int n, const double* rho_hist, const double* T_hist,
                              int on_device);

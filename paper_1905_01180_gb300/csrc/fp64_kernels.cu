@@ -1348,7 +1348,10 @@ gkba_status reduce_batch(gkba_ctx* c, int nb, double2* I_acc, double2* S_out) {
 // i.e. W1 = w x_s Gb, W2 = G x_q W1, W3 = G x_m W2, Sigma = v . W3.
 // Stages S1-S3 of the FP64 chain into X13 = X3[u][c'][j][n][r][p], with A1
 // the stage-S1 operand (w in the [j][m][q][s] layout, or any tensor in it).
-gkba_status fp64_chain_x3(gkba_ctx* c, int nb, const double* A1) {
+// m3 / sOz3, when given, replace the output scatter of S3 (rows (j, r, p),
+// columns (c', n), unit offset sOz3).
+gkba_status fp64_chain_x3(gkba_ctx* c, int nb, const double* A1, const StageMap* m3,
+                          long long sOz3) {
     const int N = c->N;
     const long long N2 = (long long)N * N, N3 = N2 * N, N4 = N3 * N;
     double* X13 = (double*)c->X13;
@@ -1368,11 +1371,11 @@ gkba_status fp64_chain_x3(gkba_ctx* c, int nb, const double* A1) {
                               8.0 * 4 * N4 * nb));
     }
     {
-        StageMap m{N3, N, 1, N4, N2, N, N, N};
+        const StageMap m = m3 ? *m3 : StageMap{N3, N, 1, N4, N2, N, N, N};
         GKBA_TRY(gemm64_stage(c, K_W3, X2, 2 * N, 2 * N4,
                               (const double*)(c->sep_A ? c->formsG3 : c->formsG), 2 * N, 4 * N2,
-                              X13, 2 * N4, (int)N3, 2 * N, 2 * N, nb, 0, 0, m, fl_cc * nb,
-                              8.0 * 4 * N4 * nb));
+                              X13, m3 ? sOz3 : 2 * N4, (int)N3, 2 * N, 2 * N, nb, 0, 0, m,
+                              fl_cc * nb, 8.0 * 4 * N4 * nb));
     }
     return GKBA_OK;
 }

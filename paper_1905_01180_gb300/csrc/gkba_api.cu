@@ -13,7 +13,7 @@
 namespace gkba {
 
 const char* kKernelClassNames[K_COUNT] = {"S1_w_x_Gbar", "S2_G_x_X1", "S3_G_x_X2", "S4_v_dot_X3",
-                                          "prep",        "reduce",    "stepper"};
+                                          "prep",        "reduce",    "stepper",   "time_linear"};
 
 static std::mutex g_err_mu;
 static std::string g_last_init_error;
@@ -411,7 +411,8 @@ void free_ctx(gkba_ctx* c) {
     if (!c) return;
     if (c->device >= 0) cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->h, c->d, c->v, c->vm, c->vjp, c->rhot_hist, c->U_hist, c->adj_ws, c->vomega,
+    void* ptrs[] = {c->tl_acc, c->tl_s, c->tl_W, c->tl_Wn, c->tl_uf,
+                    c->h, c->d, c->v, c->vm, c->vjp, c->rhot_hist, c->U_hist, c->adj_ws, c->vomega,
                     c->vgrad, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
                     c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
                     c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
@@ -460,6 +461,12 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         return fail(nullptr, GKBA_EINVAL,
                     "gkba_init: diagonal and symmetric interactions run in FP64 (precision %d)",
                     cfg->precision);
+    if (cfg->history != GKBA_HISTORY_SUM && cfg->history != GKBA_HISTORY_TIME_LINEAR)
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown history mode %d", cfg->history);
+    if (cfg->history == GKBA_HISTORY_TIME_LINEAR &&
+        (cfg->precision != GKBA_FP64 || kind != GKBA_V_GENERAL))
+        return fail(nullptr, GKBA_EUNSUPPORTED,
+                    "gkba_init: the time-linear history runs on the FP64 path with a general v");
     const int Np = ((N + 15) / 16) * 16;
     if (cfg->precision != GKBA_FP64 && Np > 96)
         return fail(nullptr, GKBA_EINVAL,
@@ -522,6 +529,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     c->max_steps = cfg->max_steps;
     c->prec = cfg->precision;
     c->kind = kind;
+    c->history = cfg->history;
     c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)64 << 30);
     c->timing = cfg->timing != 0;
     c->s4_kchunk = cfg->s4_kchunk > 0 ? cfg->s4_kchunk
@@ -606,6 +614,13 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     } else if (c->prec == GKBA_FP64) {
         ALLOC(c->wS64, N4 * 8);
         ALLOC(c->vK64, N4 * 8);
+        if (c->history == GKBA_HISTORY_TIME_LINEAR) {
+            ALLOC(c->tl_acc, 2 * N4 * 8);
+            ALLOC(c->tl_s, 2 * N4 * 8);
+            ALLOC(c->tl_W, NN * 16);
+            ALLOC(c->tl_Wn, NN * 16);
+            ALLOC(c->tl_uf, 8 * NN * 8);
+        }
     } else {
         const size_t Np4 = (size_t)Np * Np * Np * Np;
         ALLOC(c->wS32, Np4 * 4);
@@ -628,6 +643,13 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         return bail(GKBA_ECUDA);
     }
     if ((st = set_identity(c, c->T_a, 1)) != GKBA_OK) return bail(st);
+    if (c->tl_acc) {
+        if (cudaMemsetAsync(c->tl_acc, 0, 2 * N4 * 8, c->stream) != cudaSuccess) {
+            fail(c, GKBA_ECUDA, "gkba_init: memset failed");
+            return bail(GKBA_ECUDA);
+        }
+        if ((st = set_identity(c, c->tl_W, 1)) != GKBA_OK) return bail(st);
+    }
     if ((st = fp64_prepare_model(c)) != GKBA_OK) return bail(st);
     if (tensor_core_path(c) && (st = tf32_prepare_model(c)) != GKBA_OK) return bail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -850,6 +872,11 @@ gkba_status gkba_step(gkba_ctx* c, double E_n, double E_np1, double* rho_out, do
         return fail(c, GKBA_EINVAL, "gkba_step: non-finite field sample");
     if (c->n >= c->max_steps)
         return fail(c, GKBA_ESTATE, "gkba_step: history full (n=%d, max_steps=%d)", c->n, c->max_steps);
+    const bool tl = c->history == GKBA_HISTORY_TIME_LINEAR;
+    if (tl && c->tl_broken)
+        return fail(c, GKBA_ESTATE,
+                    "gkba_step: the time-linear accumulator was left inconsistent by a failed step; "
+                    "gkba_set_history rebuilds it");
     GKBA_CUDA(c, cudaSetDevice(c->device));
     NvtxRange r("gkba_step");
     const int n = c->n;
@@ -858,7 +885,20 @@ gkba_status gkba_step(gkba_ctx* c, double E_n, double E_np1, double* rho_out, do
     double2* rho_t = c->rho_hist + (n + 1) * NN;
     // predictor
     GKBA_TRY(h_hf(c, E_n, rho_n, c->hhf_n));
-    GKBA_TRY(collision_dev(c, n + 1, c->rho_hist, c->T_a, nullptr, c->Ia));
+    if (tl) {
+        // Lambda of t_n = Lambda_acc + dt/2 term_n; then term_n joins Lambda_acc
+        // with its final weight (dt/2 for t_0, dt after)
+        c->tl_broken = true;  // until the step completes
+        GKBA_TRY(ensure_workspace(c, 2));
+        GKBA_TRY(tl_terms(c, 1, rho_n, c->tl_W, 0, 0, 1.0, 1.0));
+        GKBA_TRY(tl_update(c, 0.5 * c->dt, n == 0 ? 0.5 * c->dt : c->dt, n > 0, true));
+        if (n == 0)
+            GKBA_CUDA(c, cudaMemsetAsync(c->Ia, 0, NN * sizeof(double2), c->stream));
+        else
+            GKBA_TRY(tl_apply(c, c->tl_W, c->Ia));
+    } else {
+        GKBA_TRY(collision_dev(c, n + 1, c->rho_hist, c->T_a, nullptr, c->Ia));
+    }
     GKBA_TRY(diagnostics(c, E_n, rho_n, c->Ia, c->dscal));
     GKBA_TRY(rhs(c, c->hhf_n, rho_n, c->Ia, c->k1));
     GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k1, 1.0, c->dt, (int)NN));
@@ -873,11 +913,21 @@ gkba_status gkba_step(gkba_ctx* c, double E_n, double E_np1, double* rho_out, do
                            make_double2(0.0, 0.0), c->T_b, NN, n + 1, 0));
     GKBA_TRY(set_identity(c, c->T_b + (n + 1) * NN, 1));
     // corrector
-    GKBA_TRY(collision_dev(c, n + 2, c->rho_hist, c->T_b, nullptr, c->Ib));
+    if (tl) {
+        // W_{n+1} = Ucal_{n+1}^+ = W_n U_n^+; Lambda = Lambda_acc + dt/2 term(rho~)
+        GKBA_TRY(zgemm_batched(c, K_STEP, c->N, 'N', 'C', make_double2(1.0, 0.0), c->tl_W, 0, c->U,
+                               0, make_double2(0.0, 0.0), c->tl_Wn, 0, 1, 0));
+        GKBA_TRY(tl_terms(c, 1, rho_t, c->tl_Wn, 0, 0, 1.0, 1.0));
+        GKBA_TRY(tl_update(c, 0.5 * c->dt, 0.0, true, false));
+        GKBA_TRY(tl_apply(c, c->tl_Wn, c->Ib));
+    } else {
+        GKBA_TRY(collision_dev(c, n + 2, c->rho_hist, c->T_b, nullptr, c->Ib));
+    }
     GKBA_TRY(rhs(c, c->hhf_t, rho_t, c->Ib, c->k2));
     GKBA_TRY(axpy_c(c, c->k2, c->k1, c->k2, 1.0, 1.0, (int)NN));
     GKBA_TRY(axpy_c(c, rho_t, rho_n, c->k2, 1.0, 0.5 * c->dt, (int)NN));
     std::swap(c->T_a, c->T_b);
+    if (tl) std::swap(c->tl_W, c->tl_Wn);
     c->n = n + 1;
     if (rho_out)
         GKBA_CUDA(c, cudaMemcpyAsync(rho_out, rho_t, NN * 16, cudaMemcpyDeviceToHost, c->stream));
@@ -885,6 +935,7 @@ gkba_status gkba_step(gkba_ctx* c, double E_n, double E_np1, double* rho_out, do
     if (diag_out) GKBA_CUDA(c, cudaMemcpyAsync(c->hdiag, c->dscal, 4 * 8, cudaMemcpyDeviceToHost, c->stream));
     GKBA_TRY(finish(c));
     if (diag_out) memcpy(diag_out, c->hdiag, 4 * 8);
+    c->tl_broken = false;
     return GKBA_OK;
 }
 
@@ -895,12 +946,44 @@ gkba_status gkba_set_history(gkba_ctx* c, int n, const double* rho_hist, const d
         return fail(c, GKBA_EINVAL, "gkba_set_history: n=%d outside [0, max_steps=%d] or NULL", n,
                     c->max_steps);
     GKBA_CUDA(c, cudaSetDevice(c->device));
-    const size_t bytes = (size_t)(n + 1) * c->N * c->N * 16;
+    const long long NN = (long long)c->N * c->N;
+    const size_t bytes = (size_t)(n + 1) * NN * 16;
     GKBA_TRY(copy_in(c, c->rho_hist, rho_hist, bytes, on_device));
     GKBA_TRY(copy_in(c, c->T_a, T_hist, bytes, on_device));
+    if (c->history == GKBA_HISTORY_TIME_LINEAR) {
+        // Ucal_n = 1 and Ucal_k^+ = T(t_n, t_k): needs T(t_n, t_n) = 1
+        std::vector<double> Tn(2 * NN);
+        GKBA_CUDA(c, cudaMemcpyAsync(Tn.data(), c->T_a + (size_t)n * NN, NN * 16,
+                                     cudaMemcpyDeviceToHost, c->stream));
+        GKBA_CUDA(c, cudaStreamSynchronize(c->stream));
+        double dev = 0.0;
+        for (long long e = 0; e < NN; ++e) {
+            const double re = Tn[2 * e] - ((e / c->N == e % c->N) ? 1.0 : 0.0);
+            dev = std::max(dev, std::hypot(re, Tn[2 * e + 1]));
+        }
+        if (!(dev <= 1e-12))
+            return fail(c, GKBA_EINVAL,
+                        "gkba_set_history: T(t_n, t_n) must be the identity (max deviation %.3g)", dev);
+        c->tl_broken = true;
+        GKBA_CUDA(c, cudaMemsetAsync(c->tl_acc, 0, 2 * (size_t)NN * NN * 8, c->stream));
+        GKBA_TRY(set_identity(c, c->tl_W, 1));
+        if (n > 0) {
+            // Lambda_acc = sum_{k < n} c_k term_k, c_0 = dt/2, c_k = dt
+            GKBA_TRY(ensure_workspace(c, 2 * n));
+            const int nk_per = c->ub / 2;
+            for (int k0 = 0; k0 < n; k0 += nk_per) {
+                const int nk = std::min(nk_per, n - k0);
+                GKBA_TRY(tl_terms(c, nk, c->rho_hist + (size_t)k0 * NN, c->T_a + (size_t)k0 * NN, NN,
+                                  k0, 0.5 * c->dt, c->dt));
+                GKBA_TRY(tl_update(c, 0.0, 1.0, false, true));
+            }
+        }
+    }
     c->n = n;
     c->adj_from = n;  // steps before n were not recorded
-    return finish(c);
+    GKBA_TRY(finish(c));
+    c->tl_broken = false;
+    return GKBA_OK;
 }
 
 gkba_status gkba_get_history(const gkba_ctx* cc, int* n, double* rho_hist, double* T_hist) {

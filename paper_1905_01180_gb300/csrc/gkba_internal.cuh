@@ -28,6 +28,7 @@ enum KernelClass : int {
     K_PREP,      // P/Q reconstruction and per-unit operand forms
     K_RED,       // split-K reduction, S.Gbar products, weighted history sum
     K_STEP,      // mean field, commutators, expm, T recursion, Heun update
+    K_TL,        // time-linear history: accumulator GEMM and update, back-transforms
     K_COUNT
 };
 
@@ -69,6 +70,7 @@ struct gkba_ctx {
     const int* unit_sys = nullptr;
     int nsys = 1;
     double* vm = nullptr;       // U (N) or V (N*N) of a structured interaction
+    int history = GKBA_HISTORY_SUM;  // gkba_history
     int s4_kchunk = 512;
 
     // model on the device
@@ -141,6 +143,14 @@ struct gkba_ctx {
     double2* Su = nullptr;       // per-unit S, ub * N*N
     double2* Yu = nullptr;       // per-unit coef * S . Gbar, ub * N*N
     double2* red_tmp = nullptr;  // split-K reduction scratch: kReduceSplit * ub * N*N
+
+    // time-linear history (GKBA_HISTORY_TIME_LINEAR): T(t_n, t_k) = Ucal_n Ucal_k^+
+    double* tl_acc = nullptr;    // Lambda_acc, 2 N^4 doubles, [j][n][r][c][p]
+    double* tl_s = nullptr;      // Lambda of one collision / back-transform scratch, same size
+    double2* tl_W = nullptr;     // W_n = Ucal_n^+ (N*N)
+    double2* tl_Wn = nullptr;    // W_{n+1} during a step
+    double* tl_uf = nullptr;     // real forms of Ucal and conj(Ucal), 2 x (2N)^2
+    bool tl_broken = false;      // a step failed after Lambda_acc changed
 
     // caller-buffer staging for host-pointer calls
     void* stage = nullptr;
@@ -276,7 +286,8 @@ gkba_status expm_adj(gkba_ctx* c, const double2* hA, const double2* hB, const do
                      double2* hA_bar, double2* hB_bar, double2* scratch);
 gkba_status sum_units(gkba_ctx* c, int nb, const double2* src, double2* dst);
 // gradient with respect to v (FP64 path)
-gkba_status fp64_chain_x3(gkba_ctx* c, int nb, const double* A1);
+gkba_status fp64_chain_x3(gkba_ctx* c, int nb, const double* A1, const StageMap* m3 = nullptr,
+                          long long sOz3 = 0);
 gkba_status vbar_slot(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, const double* X,
                       double* out);
 gkba_status fold_vbar(gkba_ctx* c, const double* vslot, const double* wslot, double* vbar);
@@ -291,6 +302,17 @@ gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstrid
 size_t tf32_part_bytes(int Np, int ub, int kchunk);
 // Launch the bounded-wait self-test (a wait that must run out); elapsed_ms[2].
 gkba_status wait_selftest(gkba_ctx* c, double limit_ms, double* elapsed_ms);
+
+// ---- time-linear history (time_linear.cu) ---------------------------------
+// Terms of nk history points (rho_k, W_k = Ucal_k^+ at stride sW) summed into
+// c->X2 as D[j][n][r][c][p], point k0 + i weighted (k0 + i == 0 ? w_first : w_rest).
+gkba_status tl_terms(gkba_ctx* c, int nk, const double2* rho, const double2* W, long long sW,
+                     int k0, double w_first, double w_rest);
+// tl_s = tl_acc + a D (when write_s) and tl_acc += b D (when add_acc), D = c->X2.
+gkba_status tl_update(gkba_ctx* c, double a, double b, bool write_s, bool add_acc);
+// I = [v . (Ucal x_n Ucal x_p conj(Ucal) x_r tl_s)] Ucal^+ with Ucal = W^+;
+// overwrites tl_s, X2 and X13.
+gkba_status tl_apply(gkba_ctx* c, const double2* W, double2* I_out);
 
 // Workspace sizing: make sure the workspace holds ub units (returns actual ub).
 gkba_status ensure_workspace(gkba_ctx* c, int want_units);

@@ -72,33 +72,6 @@ __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait for the phase with the given parity.  Returns false when the
-// CTA's abort flag is up or the limit ran out (then it raises the flag and
-// records `code` in the error word).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                          int code) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 63u) == 0) {
-            if (*abort_flag) return false;
-            if (gtimer() - t0 > kWaitLimitNs) {
-                *abort_flag = 1;
-                atomicCAS(err, 0, code);
-                return false;
-            }
-        }
-    }
-}
-// Warp-uniform bounded wait: every lane waits, and the warp leaves a loop
-// together when any lane's wait gives up (no lane is left at a later
-// __syncwarp or warp-collective tcgen05 instruction).
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int code) {
-    const bool r = mbar_wait(bar, parity, abort_flag, err, code);
-    return __all_sync(0xffffffffu, r);
-}
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -127,18 +100,6 @@ __device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* m, uint3
         "%4, %5, %6}], [%2];" ::"r"(dst),
         "l"((unsigned long long)m), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
         : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
-                 "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
 }
 // --- CTA-pair (cta_group::2) forms ---
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -241,21 +202,6 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// D[tmem] (+)= A[tmem] * B[smem desc], kind::tf32, M = 128.
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, unsigned long long bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
-        "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -305,13 +251,8 @@ __device__ __forceinline__ unsigned long long desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32, K-major,
-// M = 128, N = n, optional negation of B.
-__host__ __device__ constexpr uint32_t idesc_tf32(int n, int negB) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negB << 14) |
-           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
-// Same for the CTA-pair MMA: M = 256 (two 128-row halves), N = n.
+// Instruction descriptor of the CTA-pair MMA: kind::tf32, FP32 accumulator,
+// A and B TF32, K-major, M = 256 (two 128-row halves), N = n.
 __host__ __device__ constexpr uint32_t idesc_tf32_pair(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)((2 * kBM) >> 4) << 24);

@@ -22,6 +22,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgkba.so")
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC, EUNSUPPORTED = range(8)
 FP64, SPLIT_TF32, SPLIT_TF32_ACC = 0, 1, 2
 V_GENERAL, V_DIAGONAL, V_SYMMETRIC = 0, 1, 2
+HISTORY_SUM, HISTORY_TIME_LINEAR = 0, 1
+_HISTORY = {"sum": HISTORY_SUM, "time_linear": HISTORY_TIME_LINEAR,
+            HISTORY_SUM: HISTORY_SUM, HISTORY_TIME_LINEAR: HISTORY_TIME_LINEAR}
 _INTERACTION = {"general": V_GENERAL, "diagonal": V_DIAGONAL, "symmetric": V_SYMMETRIC,
                 V_GENERAL: V_GENERAL, V_DIAGONAL: V_DIAGONAL, V_SYMMETRIC: V_SYMMETRIC}
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT",
@@ -45,7 +48,7 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
                 ("timing", ctypes.c_int), ("s4_kchunk", ctypes.c_int),
-                ("interaction", ctypes.c_int)]
+                ("interaction", ctypes.c_int), ("history", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -123,7 +126,8 @@ class Context:
     """One GKBA system on one GPU (wraps a gkba_ctx)."""
 
     def __init__(self, h, v, d, rho0, dt, max_steps=0, precision="fp64", stream=None,
-                 workspace_bytes=0, device=-1, timing=False, s4_kchunk=0, interaction="general"):
+                 workspace_bytes=0, device=-1, timing=False, s4_kchunk=0, interaction="general",
+                 history="sum"):
         L = load()
         on_dev = _is_torch(h)
         N = int(h.shape[0])
@@ -142,7 +146,8 @@ class Context:
                 SPLIT_TF32: SPLIT_TF32, SPLIT_TF32_ACC: SPLIT_TF32_ACC}[precision]
         cfg = Config(N=N, dt=float(dt), max_steps=int(max_steps), precision=prec,
                      cuda_stream=stream, workspace_bytes=int(workspace_bytes), device=int(device),
-                     timing=1 if timing else 0, s4_kchunk=int(s4_kchunk), interaction=kind)
+                     timing=1 if timing else 0, s4_kchunk=int(s4_kchunk), interaction=kind,
+                     history=_HISTORY[history])
         handle = ctypes.c_void_p()
         st = L.gkba_init(ctypes.byref(handle), ctypes.byref(cfg), ph[1], pv[1], pd[1], pr[1],
                          1 if on_dev else 0)
@@ -154,6 +159,7 @@ class Context:
         self.max_steps = int(max_steps)
         self.precision = prec
         self.interaction = kind
+        self.history = _HISTORY[history]
 
     # -- helpers -------------------------------------------------------
     def _check(self, st):

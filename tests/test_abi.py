@@ -46,7 +46,8 @@ def test_config_struct_matches_header():
     assert members == [f[0] for f in gkba.Config._fields_]
 
 
-def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None, interaction=0):
+def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None, interaction=0,
+          history=0):
     from paper_1905_01180_gb300 import gkba
     s = gi.system(4, 4, seed=0)
     h = s["h"] if h is None else h
@@ -55,7 +56,7 @@ def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None, interacti
     rho = s["rho0"] if rho is None else rho
     cfg = gkba.Config(N=N, dt=dt, max_steps=1, precision=prec, cuda_stream=None,
                       workspace_bytes=0, device=-1, timing=0, s4_kchunk=0,
-                      interaction=interaction)
+                      interaction=interaction, history=history)
     out = ctypes.c_void_p()
     arrs = [np.ascontiguousarray(x) for x in (h, v, d, rho)]
     st = lib.gkba_init(ctypes.byref(out), ctypes.byref(cfg), *[a.ctypes.data for a in arrs], 0)
@@ -103,6 +104,20 @@ def test_init_rejects_bad_structured_interactions(lib):
     U = np.array([1.0, np.inf, 1.0, 1.0])
     st, _, msg = _init(lib, interaction=gkba.V_DIAGONAL, v=U)
     assert st == gkba.EINVAL and "non-finite" in msg
+
+
+def test_init_rejects_bad_history_modes(lib):
+    # the time-linear history runs on the FP64 path with a general v; other
+    # combinations and unknown modes are refused before device work
+    from paper_1905_01180_gb300 import gkba
+    st, _, msg = _init(lib, history=2)
+    assert st == gkba.EINVAL and "history" in msg
+    st, _, msg = _init(lib, history=gkba.HISTORY_TIME_LINEAR, prec=gkba.SPLIT_TF32)
+    assert st == gkba.EUNSUPPORTED and "time-linear" in msg
+    c = gi.chain(4, "symmetric")
+    st, _, msg = _init(lib, history=gkba.HISTORY_TIME_LINEAR, interaction=gkba.V_SYMMETRIC,
+                       v=c["v"])
+    assert st == gkba.EUNSUPPORTED and "time-linear" in msg
 
 
 def test_batch_create_rejects_bad_arguments(lib):

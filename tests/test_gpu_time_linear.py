@@ -1,0 +1,150 @@
+"""The time-linear history (gkba_config.history = GKBA_HISTORY_TIME_LINEAR):
+gkba_step with the history sum of Eq. (collint) kept as one N^4 accumulator.
+
+It is an exact rewrite of the history sum for T(t_n, t_k) = Ucal_n Ucal_k^+,
+so every step must reproduce the history-sum stepper (FP64 GPU path) and the
+oracle's propagation to rounding.  Tolerances: 1e-11 on rho and the energies
+against the history-sum stepper, 1e-10 against the oracle, 1e-9 on the
+collision integral (it carries the cancellation of Sigma^> G^< - Sigma^< G^>).
+"""
+import numpy as np
+import pytest
+
+import gkba_inputs as gi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as p
+    return p
+
+
+def field(n, dt):
+    return 0.2 * np.sin(0.7 * np.arange(n + 1) * dt * 10)
+
+
+@pytest.mark.parametrize("N,n,dt", [(8, 40, 0.05), (13, 25, 0.02), (1, 6, 0.1)])
+def test_time_linear_matches_history_sum_stepper(P, N, n, dt):
+    s = gi.system(N, 8, seed=N)
+    E = field(n, dt)
+    a = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
+    b = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear")
+    worst_rho = worst_I = worst_E = 0.0
+    for k in range(n):
+        ra, Ia, da = a.step(E[k], E[k + 1])
+        rb, Ib, db = b.step(E[k], E[k + 1])
+        worst_rho = max(worst_rho, rel(rb, ra))
+        if k > 0:
+            worst_I = max(worst_I, rel(Ib, Ia))
+        else:
+            assert np.abs(Ib).max() == 0.0
+        worst_E = max(worst_E, abs(db[1] - da[1]))
+    print(f"N={N}, {n} steps: time-linear vs history sum rho {worst_rho:.2e} "
+          f"I {worst_I:.2e} energy {worst_E:.2e}")
+    assert worst_rho < 1e-11 and worst_I < 1e-9 and worst_E < 1e-11
+    # the propagator history stays available in this mode
+    na, rha, Ta = a.get_history()
+    nb, rhb, Tb = b.get_history()
+    assert na == nb == n and rel(Tb, Ta) < 1e-13
+    a.close()
+    b.close()
+
+
+def test_time_linear_matches_oracle(P):
+    N, n, dt = 6, 15, 0.05
+    s = gi.system(N, 8, seed=2)
+    E = field(n, dt)
+    ref = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, E)
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear")
+    for k in range(n):
+        rho, I, diag = ctx.step(E[k], E[k + 1])
+        assert rel(rho, ref.rho[k + 1]) < 1e-10
+        if k > 0:
+            assert rel(I, ref.I[k]) < 1e-9
+        assert abs(diag[1] - ref.energy_total[k]) < 1e-10
+    ctx.close()
+
+
+def test_work_per_step_does_not_grow_with_history(P):
+    # two accumulator chains per step (t_n and the predicted t_{n+1}) at any n
+    N, n, dt = 8, 12, 0.05
+    s = gi.system(N, 8, seed=5)
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear")
+    per_step = []
+    for k in range(n):
+        ctx.stats(reset=True)
+        ctx.step(0.0, 0.0)
+        st, _ = ctx.stats()
+        per_step.append((st["S1_w_x_Gbar"]["launches"], st["S1_w_x_Gbar"]["flops"],
+                         st["time_linear"]["launches"]))
+    assert all(p[0] == 2 for p in per_step)
+    assert len(set(per_step[1:])) == 1
+    ctx.close()
+
+
+@pytest.mark.parametrize("ws_units", [0, 4])
+def test_set_history_rebuilds_the_accumulator(P, ws_units):
+    # restore a checkpoint of a history-sum run into a time-linear context
+    # (rebuild over 9 points, in chunks of 2 when the workspace holds 4 units)
+    N, n0, n1, dt = 8, 9, 6, 0.05
+    s = gi.system(N, 8, seed=7)
+    E = field(n0 + n1, dt)
+    a = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n0 + n1)
+    for k in range(n0):
+        a.step(E[k], E[k + 1])
+    n, rho_hist, T_hist = a.get_history()
+    N2 = N * N
+    per_unit = 2 * (2 * N2 * N2 * 8) + 6 * N2 * 8 + N * 2 * N * 8 + 20 * N2 * 16 + 8
+    ws = int(4.5 * per_unit) if ws_units else 0
+    b = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n0 + n1,
+                  workspace_bytes=ws, history="time_linear")
+    b.set_history(n, rho_hist, T_hist)
+    for k in range(n0, n0 + n1):
+        ra, Ia, _ = a.step(E[k], E[k + 1])
+        rb, Ib, _ = b.step(E[k], E[k + 1])
+        assert rel(rb, ra) < 1e-11
+        assert rel(Ib, Ia) < 1e-9
+    a.close()
+    b.close()
+
+
+def test_set_history_needs_identity_at_t_n(P):
+    N, dt = 5, 0.05
+    s = gi.system(N, 8, seed=1)
+    rho, T = gi.history(N, 4, dt, seed=2)
+    T = T.copy()
+    T[-1] = T[0]  # not the identity
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=6, history="time_linear")
+    with pytest.raises(P.GKBAError) as ei:
+        ctx.set_history(3, rho, T)
+    assert ei.value.status == P.gkba.EINVAL
+    ctx.close()
+
+
+def test_adjoint_of_a_time_linear_run(P):
+    # the trajectory is the history-sum one up to rounding, and so are the
+    # gradients gkba_adjoint takes through it
+    N, n, dt = 5, 8, 0.05
+    s = gi.system(N, 8, seed=3)
+    E = field(n, dt)
+    out = []
+    for mode in ("sum", "time_linear"):
+        ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history=mode)
+        for k in range(n):
+            ctx.step(E[k], E[k + 1])
+        out.append(ctx.adjoint(s["d"]))
+        ctx.close()
+    (Ea, ra), (Eb, rb) = out
+    assert rel(Eb, Ea) < 1e-10 and rel(rb, ra) < 1e-10
