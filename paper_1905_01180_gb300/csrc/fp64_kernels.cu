@@ -975,6 +975,20 @@ gkba_status gemm64_stage(gkba_ctx* c, int cls, const double* A, long long lda, l
     return launch_end(c, t);
 }
 
+long long gemm64_splitk_chunk(gkba_ctx* c, int M, int Nc, long long K, long long max_chunks) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm64_stage, 256, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long bpz = (long long)((Nc + G64_BN - 1) / G64_BN) * ((M + G64_BM - 1) / G64_BM);
+    long long nz = std::max(1LL, (long long)per_sm * c->num_sms / bpz);
+    nz = std::min(nz, std::max(1LL, max_chunks));
+    const long long Kc = (K + nz - 1) / nz;
+    return (Kc + G64_BK - 1) / G64_BK * G64_BK;
+}
+
 static gkba_status zgemm_impl(gkba_ctx* c, int cls, int n, char opA, char opB, double2 alpha,
                               const double2* A, long long sA, const double2* B, long long sB,
                               double2 beta, double2* C, long long sC, int batch, int add_identity,

@@ -141,6 +141,9 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     else {
         const long long nz = (long long)std::ceil(N3 / 8192.0);
         part_bytes = (size_t)(nz * N * 2LL * N * ub * 8);
+        // the time-linear collision splits one unit's K into up to 1024 chunks
+        if (c->history == GKBA_HISTORY_TIME_LINEAR)
+            part_bytes = std::max(part_bytes, (size_t)(1024LL * N * 2LL * N * 8));
     }
     const size_t oPart = cv.take(part_bytes);
     const size_t oB1 = cv.take(!gen ? 0 : tc ? (size_t)(2LL * 2 * Np * Np * ub * 4) : (size_t)(2LL * NN * ub * 8));

@@ -223,6 +223,10 @@ gkba_status gemm64_stage(gkba_ctx* c, int cls, const double* A, long long lda, l
 
 // Complex batched GEMM: C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] (+ I if add_identity),
 // op = 'N' or 'C' (conjugate transpose); square n x n matrices, per-batch strides in elements.
+// K chunk (a multiple of the stage GEMM's K slice) of a split-K stage GEMM of
+// M x Nc outputs so that its launch fills about one wave of resident blocks,
+// with at most max_chunks chunks.
+long long gemm64_splitk_chunk(gkba_ctx* c, int M, int Nc, long long K, long long max_chunks);
 gkba_status zgemm_batched(gkba_ctx* c, int cls, int n, char opA, char opB, double2 alpha,
                           const double2* A, long long sA, const double2* B, long long sB,
                           double2 beta, double2* C, long long sC, int batch, int add_identity);

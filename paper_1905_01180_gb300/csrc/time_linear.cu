@@ -172,9 +172,10 @@ gkba_status tl_apply(gkba_ctx* c, const double2* W, double2* I_out) {
     const StageMap mx3{N3, 1, N2, N4, N, N, N, N};
     GKBA_TRY(gemm64_stage(c, K_TL, c->tl_s, 2 * N, 0, Urc, 2 * N, 0, X13, 0, (int)N3, 2 * N, 2 * N,
                           1, 0, 0, mx3, fl, by));
-    // stage S4 on one unit: D[(c, j)][i] = sum_(n,r,p) X3[c][j][(n,r,p)] vK[i][(n,r,p)], split-K
+    // stage S4 on one unit: D[(c, j)][i] = sum_(n,r,p) X3[c][j][(n,r,p)] vK[i][(n,r,p)],
+    // split-K into chunks that fill one wave of blocks (one unit has few output tiles)
     const long long R = 2LL * N;
-    const long long Kc = 8192;
+    const long long Kc = gemm64_splitk_chunk(c, (int)R, N, N3, (long long)(c->part_bytes / (N * R * 8)));
     const int nz = (int)((N3 + Kc - 1) / Kc);
     const StageMap m4{0, 0, 1, 0, R, (int)R, 1, N};
     GKBA_TRY(gemm64_stage(c, K_FIN, X13, N3, 0, c->vK64, N3, 0, (double*)c->part, N * R, (int)R, N,
