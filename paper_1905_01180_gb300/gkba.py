@@ -123,7 +123,13 @@ def _dev(x, dtype_name):
 
 
 class Context:
-    """One GKBA system on one GPU (wraps a gkba_ctx)."""
+    """One GKBA system on one GPU (wraps a gkba_ctx).
+
+    precision: "fp64", "tf32" (split-TF32 on the tensor cores) or "tf32acc";
+    interaction: "general" (v_ijkl), "diagonal" (U_i) or "symmetric" (V_ij);
+    history: "sum" (each step sums the whole history) or "time_linear" (the
+    history sum kept as one N^4 accumulator; FP64 and a general v only).
+    """
 
     def __init__(self, h, v, d, rho0, dt, max_steps=0, precision="fp64", stream=None,
                  workspace_bytes=0, device=-1, timing=False, s4_kchunk=0, interaction="general",
