@@ -148,3 +148,17 @@ def test_adjoint_of_a_time_linear_run(P):
         ctx.close()
     (Ea, ra), (Eb, rb) = out
     assert rel(Eb, Ea) < 1e-10 and rel(rb, ra) < 1e-10
+
+
+def test_time_linear_runs_are_bitwise_reproducible(P):
+    # fixed-order FP64 GEMMs and reductions: two runs agree bit for bit
+    N, n, dt = 9, 6, 0.05
+    s = gi.system(N, 8, seed=4)
+    E = field(n, dt)
+    outs = []
+    for _ in range(2):
+        ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear")
+        outs.append([ctx.step(E[k], E[k + 1]) for k in range(n)])
+        ctx.close()
+    for (ra, Ia, da), (rb, Ib, db) in zip(*outs):
+        assert np.array_equal(ra, rb) and np.array_equal(Ia, Ib) and np.array_equal(da, db)
