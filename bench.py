@@ -230,22 +230,23 @@ def run_chains(a):
     N_t Heun steps through gkba_step (field-free, from the initial state):
     (1) Hubbard chain, diagonal basis, 5000 x 0.01; (2) Ohno chain, symmetric
     basis, 2000 x 0.025; (3) general basis (the seeded stand-in for the CH4
-    integrals, 2 occupied orbitals), 1000 x 0.05.  One JSON line per run; the
-    paper's single-core CPU times (Table I, tensor-contraction column) are
-    context, not a target."""
+    integrals, 2 occupied orbitals), 1000 x 0.05, also with the time-linear
+    history (FP64).  One JSON line per run; the paper's single-core CPU times
+    (Table I, tensor-contraction column) are context, not a target."""
     import torch
     import gkba_inputs as gi
     from paper_1905_01180_gb300 import build as b
     b.build()
     import paper_1905_01180_gb300 as P
-    cases = [("hubbard_chain_N10", "diagonal", 0.01, 5000, "fp64", 164.0),
-             ("ohno_chain_N10", "symmetric", 0.025, 2000, "fp64", 731.0),
-             ("general_basis_N10", "general", 0.05, 1000, "fp64", 1333.0),
-             ("general_basis_N10", "general", 0.05, 1000, "tf32acc", 1333.0)]
-    for name, kind, dt, n, prec, paper in cases:
+    cases = [("hubbard_chain_N10", "diagonal", 0.01, 5000, "fp64", "sum", 164.0),
+             ("ohno_chain_N10", "symmetric", 0.025, 2000, "fp64", "sum", 731.0),
+             ("general_basis_N10", "general", 0.05, 1000, "fp64", "sum", 1333.0),
+             ("general_basis_N10", "general", 0.05, 1000, "tf32acc", "sum", 1333.0),
+             ("general_basis_N10", "general", 0.05, 1000, "fp64", "time_linear", 1333.0)]
+    for name, kind, dt, n, prec, history, paper in cases:
         s = gi.system(10, 8, seed=0) if kind == "general" else gi.chain(10, kind)
         ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=prec,
-                        interaction=kind)
+                        interaction=kind, history=history)
         tr0 = float(np.trace(s["rho0"]).real)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -259,7 +260,8 @@ def run_chains(a):
         ctx.close()
         print(json.dumps({"workload": name, "metric": "GKBA propagation wall time (N_t steps)",
                           "value": wall, "unit": "s", "higher_is_better": False,
-                          "interaction": kind, "precision": prec, "N": 10, "steps": n, "dt": dt,
+                          "interaction": kind, "precision": prec, "history": history,
+                          "N": 10, "steps": n, "dt": dt,
                           "ms_per_step": 1e3 * wall / n, "gpu_launches": launches,
                           "trace_drift": float(np.abs(np.array(tr) - tr0).max()),
                           "energy_drift": float(np.abs(np.array(en) - en[0]).max()),
