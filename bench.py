@@ -21,6 +21,8 @@ Printed JSON line (rank 0):
   fp64_path    the FP64 CUDA path timed on a 3-point history and extrapolated
                (cost is linear in the number of units), with the split-TF32
                error against it
+  time_linear  the same Heun step with the time-linear history (FP64, the
+               history sum kept as one N^4 accumulator; cost independent of L)
 
 --impl reference times the CPU oracle (the reference arm of this build) on a
 bounded sample per step: one (t_k, component) unit at N = 96.
@@ -57,6 +59,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-time-linear", action="store_true")
     ap.add_argument("--batch", action="store_true",
                     help="time 32 systems of uneven N and L stacked in one batch vs one by one")
     ap.add_argument("--chains", action="store_true",
@@ -270,12 +273,39 @@ def run_chains(a):
               flush=True)
 
 
-def run_time_linear(a):
+def time_linear_sample(P, s, N, dt, stream, warmup, steps):
     """gkba_step with cfg.history = GKBA_HISTORY_TIME_LINEAR (FP64) at N: the
     history sum kept as one N^4 accumulator, so a step's cost does not depend
-    on the history length.  W warm-up steps from the initial state, then K
-    timed steps (CUDA events on the context's stream); the per-step work is the
-    same at any step index."""
+    on the history length.  `warmup` steps from the initial state, then
+    `steps` timed steps (CUDA events on the context's stream); the per-step
+    work is the same at any step index."""
+    import torch
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=warmup + steps + 1,
+                    precision="fp64", stream=stream.cuda_stream, timing=True,
+                    history="time_linear")
+    for _ in range(warmup):
+        ctx.step(0.0, 0.0)
+    ctx.stats(reset=True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        _, _, diag = ctx.step(0.0, 0.0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    stats, launches = ctx.stats(reset=True)
+    ctx.close()
+    flops = sum(v["flops"] for v in stats.values()) / steps
+    return {"ms_per_step": ms, "flops_per_step": flops,
+            "fp64_tflops": flops / (ms * 1e-3) / 1e12, "gpu_launches": launches,
+            "classes": {k: {"ms": v["ms"] / steps, "launches": v["launches"] // steps}
+                        for k, v in stats.items() if v["launches"]},
+            "trace": float(diag[0])}
+
+
+def run_time_linear(a):
+    """The time-linear step alone at N (see time_linear_sample)."""
     import torch
     import gkba_inputs as gi
     from paper_1905_01180_gb300 import build as b
@@ -283,34 +313,11 @@ def run_time_linear(a):
     import paper_1905_01180_gb300 as P
     N, dt = a.N, a.dt
     s = gi.system(N, a.nP, seed=0)
-    stream = torch.cuda.current_stream()
-    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=a.warmup + a.steps + 1,
-                    precision="fp64", stream=stream.cuda_stream, timing=True,
-                    history="time_linear")
-    for _ in range(a.warmup):
-        ctx.step(0.0, 0.0)
-    ctx.stats(reset=True)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(a.steps):
-        _, _, diag = ctx.step(0.0, 0.0)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    stats, launches = ctx.stats(reset=True)
-    ctx.close()
-    flops = sum(v["flops"] for v in stats.values()) / a.steps
-    kern_ms = sum(v["ms"] for v in stats.values()) / a.steps
+    r = time_linear_sample(P, s, N, dt, torch.cuda.current_stream(), a.warmup, a.steps)
     print(json.dumps({"workload": f"gkba_time_linear_step_N{N}", "metric": "GKBA Heun step time",
-                      "value": ms / 1e3, "unit": "s", "higher_is_better": False,
+                      "value": r["ms_per_step"] / 1e3, "unit": "s", "higher_is_better": False,
                       "precision": "fp64", "history": "time_linear", "N": N, "n_P": a.nP,
-                      "steps": a.steps, "warmup": a.warmup, "flops_per_step": flops,
-                      "fp64_tflops": flops / (ms * 1e-3) / 1e12, "timed_kernel_ms": kern_ms,
-                      "gpu_launches": launches,
-                      "classes": {k: {"ms": v["ms"] / a.steps, "launches": v["launches"] // a.steps}
-                                  for k, v in stats.items() if v["launches"]},
-                      "trace": float(diag[0])}), flush=True)
+                      "steps": a.steps, "warmup": a.warmup, **r}), flush=True)
 
 
 def run_batch(a):
@@ -515,6 +522,16 @@ def main():
                              "split_tf32_rel_err_I": err}
         c64.close()
         ctc.close()
+
+    if rank == 0 and not a.no_time_linear:
+        # the same Heun step with the history sum kept as one N^4 accumulator
+        # (FP64; its cost does not depend on L)
+        r = time_linear_sample(P, s, N, dt, stream, 1, 2)
+        line["time_linear"] = {"ms_per_step": r["ms_per_step"], "precision": "fp64",
+                               "fp64_tflops": r["fp64_tflops"],
+                               "speedup_vs_history_sum_step": ms_step / r["ms_per_step"],
+                               "sample": f"2 steps after 1 warm-up from rho0 at N={N} "
+                                         "(per-step work independent of the history length)"}
 
     if rank == 0 and not a.no_cpu:
         t = oracle_unit_sample(N, a.nP)
