@@ -24,7 +24,7 @@ Printed JSON line (rank 0):
   time_linear  the same Heun step with the time-linear history (FP64, the
                history sum kept as one N^4 accumulator; cost independent of L)
 
---impl reference times the CPU oracle (the reference arm of this build) on a
+--impl reference times the CPU oracle (the reference arm) on a
 bounded sample per step: one (t_k, component) unit at N = 96.
 """
 from __future__ import annotations

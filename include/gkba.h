@@ -54,7 +54,7 @@ typedef enum {
     GKBA_ESTATE = 4,      /* call not valid in the current state (e.g. history full) */
     GKBA_ETIMEOUT = 5,    /* a device-side wait ran past its limit; results are invalid */
     GKBA_ENUMERIC = 6,    /* non-finite values produced */
-    GKBA_EUNSUPPORTED = 7 /* valid request that this build does not implement */
+    GKBA_EUNSUPPORTED = 7 /* valid request that the library does not implement */
 } gkba_status;
 
 typedef enum {
