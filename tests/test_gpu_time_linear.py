@@ -162,3 +162,39 @@ def test_time_linear_runs_are_bitwise_reproducible(P):
         ctx.close()
     for (ra, Ia, da), (rb, Ib, db) in zip(*outs):
         assert np.array_equal(ra, rb) and np.array_equal(Ia, Ib) and np.array_equal(da, db)
+
+
+def test_config1_time_linear_full_run(P):
+    # N = 24, 32 factors, dt = 0.02, the pulse on [0, 10], 1000 Heun steps:
+    # the first 100 against the oracle (tests/golden, written by the oracle
+    # only), then the whole run's invariants (particle number, Hermiticity,
+    # E_c < 0) with the time-linear history in FP64
+    import os
+    import time
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "config1_oracle_100steps.npz"))
+    s = gi.system(24, 32, seed=0)
+    dt = float(g["dt"])
+    E = gi.field(dt * np.arange(1001))
+    n = 1000
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear")
+    rho_at, tr, herm, ec = {}, [], 0.0, []
+    t0 = time.perf_counter()
+    for k in range(n):
+        rho, I, diag = ctx.step(E[k], E[k + 1])
+        if k < 100:
+            rho_at[k + 1] = rho
+            assert abs(diag[1] - g["energy_total"][k]) < 1e-10 * max(1.0, abs(g["energy_total"][k]))
+        tr.append(diag[0])
+        ec.append(diag[2])
+        herm = max(herm, np.abs(rho - rho.conj().T).max())
+    wall = time.perf_counter() - t0
+    ctx.close()
+    w_rho = max(rel(rho_at[m], r) for m, r in zip(g["steps"][1:], g["rho"][1:]))
+    tr = np.array(tr)
+    print(f"config1 time-linear FP64: 1000 steps in {wall:.2f} s, rho vs oracle (100 steps) "
+          f"{w_rho:.2e}, |Tr rho - 6| {np.abs(tr - 6).max():.2e}, herm {herm:.2e}, "
+          f"E_c end {ec[-1]:.4e}")
+    assert w_rho < 1e-10
+    assert np.abs(tr - 6.0).max() < 1e-11
+    assert herm < 1e-12
+    assert ec[-1] < 0.0
