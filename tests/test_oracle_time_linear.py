@@ -105,3 +105,20 @@ def test_time_linear_stepper_equals_history_sum_stepper(N, n, dt):
             assert rel(b.I[k], a.I[k]) < 1e-11
     assert np.abs(b.energy_total - a.energy_total).max() < 1e-12
     assert np.abs(b.I[0]).max() == 0.0
+
+
+def test_time_linear_stepper_against_config1_golden():
+    # the N = 24 propagation (32 factors, dt = 0.02, the pulse) stored by the
+    # history-sum oracle (tests/golden/make_config1_oracle.py): the first 20
+    # steps of the time-linear stepper reproduce it
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "config1_oracle_100steps.npz"))
+    s = gi.system(24, 32, seed=0)
+    dt = float(g["dt"])
+    E = gi.field(dt * np.arange(1001))
+    n = 20
+    r = O.propagate_time_linear(s["h"], s["v"], s["d"], s["rho0"], dt, n, E)
+    for i, m in enumerate(g["steps"]):
+        if m <= n:
+            assert rel(r.rho[m], g["rho"][i]) < 1e-12
+    assert np.abs(r.energy_total - g["energy_total"][: n + 1]).max() < 1e-12
