@@ -20,6 +20,11 @@
  *   Sec. II, Eq. (equalt)   d rho/dt = -i [h + E(t) d + Sigma_HF(rho), rho] - (I + I^+),
  *        (Sigma_HF)_ij = sum_kl (2 v_iklj - v_ikjl) rho_lk, advanced by Heun's
  *        method with U_n = exp(-i dt (h_HF(t_n) + h_HF(t_{n+1}))/2).
+ * Also (each documented at its declaration): the diagonal and symmetric
+ * interactions of Sec. III A-B (gkba_config.interaction); beyond the paper,
+ * stacked batches of systems (gkba_batch_*), gradients (gkba_sigma3,
+ * gkba_collision_vjp, gkba_adjoint) and the time-linear history of
+ * gkba_step (gkba_config.history).
  *
  * Conventions shared by every call
  *  - Complex matrices are N x N, row-major, interleaved (re, im) doubles

@@ -29,6 +29,12 @@ Readings of the paper that the oracle fixes (each is pinned by a test in
   average of h_HF at both ends of the step (the paper used no
   predictor-corrector; a second-order scheme is required here).
 * Spin-restricted: rho, I and Sigma are per spin (Sec. II).
+
+Beyond the paper: ``collision_vjp`` / ``collision_vjp_v`` (reverse-mode
+derivatives of the collision integral) and the time-linear form of the
+history sum (``collision_time_linear``, ``propagate_time_linear``), each
+pinned against the plain definitions above (finite differences, the history
+sum).
 """
 from __future__ import annotations
 
