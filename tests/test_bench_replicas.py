@@ -43,3 +43,15 @@ def test_job_timing_two_gloo_ranks():
 def test_job_timing_single_process():
     import bench
     assert bench.job_timing(12.5, 7) == (12.5, 7)
+
+
+def test_roofline_traffic_comes_from_the_committed_profiles():
+    # the bench's roofline.traffic reads dram_bytes_per_unit[<stage>] lines of
+    # the ncu summaries under profiles/ (per-unit DRAM bytes of k_tc_pair for
+    # S2 and S3, whose traffic is proportional to the units)
+    import bench
+    for stage in ("S2_G_x_X1", "S3_G_x_X2"):
+        t, src = bench.captured_traffic(stage, 2.0)
+        assert src is not None and src.startswith("k_tc_pair"), stage
+        assert 1e9 < t / 2.0 < 3e9  # ~1.33 GB per unit at N = 96 (X in + out)
+    assert bench.captured_traffic("no_such_stage", 1.0) == (None, None)
