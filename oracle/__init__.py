@@ -59,6 +59,7 @@ __all__ = [
     "hf_self_energy",
     "expm_hermitian",
     "Propagation",
+    "heun_step",
     "propagate",
     "energy",
     "time_linear_factors",
@@ -228,7 +229,7 @@ def gkba_greens(T, rho):
     return Gl_tk, Gg_tk, Gl_kt, Gg_kt
 
 
-def self_energies(v, T, rho, route="independent"):
+def self_energies(v, T, rho, route="paper"):
     """Sigma^<(t, t_k) and Sigma^>(t, t_k) from Eq. (2bse) with the GKBA
     Green's functions (explicit i phases).  Sigma^{<>} = S(G^{<>}(t,t_k),
     G^{><}(t_k,t)).  ``route`` picks the contraction order."""
@@ -250,7 +251,7 @@ def trapezoid_weights(L, dt):
     return w
 
 
-def collision(v, rho_hist, T_hist, weights, route="independent", chunk=256):
+def collision(v, rho_hist, T_hist, weights, route="paper", chunk=256):
     """First line of Eq. (collint) with the time integral as a weighted sum:
 
     I(t) = sum_k c_k [Sigma^>(t,t_k) G^<(t_k,t) - Sigma^<(t,t_k) G^>(t_k,t)]
@@ -457,23 +458,21 @@ def energy(h, d, E, v, rho, I):
     return one + hf + ec, ec
 
 
-def propagate(h, v, d, rho0, dt, n_steps, E_samples, route="independent"):
-    """Heun stepping of Eq. (equalt) with the GKBA collision integral.
+def heun_step(h, v, d, rho_hist, T_row, dt, E_n, E_np1, route="paper"):
+    """One Heun step t_n -> t_{n+1} of Eq. (equalt) from an explicit history.
 
-    E_samples[n] = E(t_n), n = 0 .. n_steps.  Per step n -> n+1:
-      k1 = F(t_n, rho_n) over history t_0..t_n with T(t_n, .)
+    rho_hist[k] = rho(t_k) and T_row[k] = T(t_n, t_k) for k = 0 .. n
+    (T_row[n] = 1).  With F = -i[h_HF, rho] - (I + I^dag),
+    h_HF(t, rho) = h + E(t) d + Sigma_HF(rho):
+      k1 = F(t_n, rho_n) over the history t_0..t_n with T(t_n, .)
       rho~ = rho_n + dt k1
       U_n = exp(-i dt (h_HF(t_n, rho_n) + h_HF(t_{n+1}, rho~)) / 2)
       T(t_{n+1}, t_k) = U_n T(t_n, t_k), T(t_{n+1}, t_{n+1}) = 1
-      k2 = F(t_{n+1}, rho~) over history t_0..t_n, t_{n+1} (rho~ in the last slot)
+      k2 = F(t_{n+1}, rho~) over t_0..t_n, t_{n+1} (rho~ in the last slot)
       rho_{n+1} = rho_n + dt/2 (k1 + k2)
-    where F = -i[h_HF, rho] - (I + I^dag), h_HF(t, rho) = h + E(t) d + Sigma_HF(rho).
-    Returns a ``Propagation`` with rho[0..n_steps] and I[0..n_steps].
+    Returns (rho_{n+1}, I(t_n) of k1, T(t_{n+1}, .) as a list).
     """
-    N = rho0.shape[0]
-    rho_hist = [rho0.copy()]
-    T_row = [np.eye(N, dtype=np.complex128)]
-    Is, energies, ecs = [], [], []
+    N = rho_hist[0].shape[0]
 
     def coll(rhos, Ts):
         L = len(rhos)
@@ -481,24 +480,43 @@ def propagate(h, v, d, rho0, dt, n_steps, E_samples, route="independent"):
             return np.zeros((N, N), np.complex128)
         return collision(v, np.array(rhos), np.array(Ts), trapezoid_weights(L, dt), route)
 
+    rho_n = rho_hist[-1]
+    hhf_n = h + E_n * d + hf_self_energy(v, rho_n)
+    I_n = coll(list(rho_hist), list(T_row))
+    k1 = _rhs(hhf_n, rho_n, I_n)
+    rho_t = rho_n + dt * k1
+    hhf_t = h + E_np1 * d + hf_self_energy(v, rho_t)
+    U = expm_hermitian(0.5 * (hhf_n + hhf_t), dt)
+    T_next = [U @ T for T in T_row] + [np.eye(N, dtype=np.complex128)]
+    I_t = coll(list(rho_hist) + [rho_t], T_next)
+    k2 = _rhs(hhf_t, rho_t, I_t)
+    return rho_n + 0.5 * dt * (k1 + k2), I_n, T_next
+
+
+def propagate(h, v, d, rho0, dt, n_steps, E_samples, route="paper"):
+    """Heun stepping of Eq. (equalt) with the GKBA collision integral: n_steps
+    calls of ``heun_step`` from rho(t_0) = rho0 with E_samples[n] = E(t_n),
+    n = 0 .. n_steps.  Returns a ``Propagation`` with rho[0..n_steps] and
+    I[0..n_steps] (I[n] is k1's collision integral at t_n; the last one is
+    evaluated without a step) and the energy of every t_n.
+    """
+    N = rho0.shape[0]
+    rho_hist = [rho0.copy()]
+    T_row = [np.eye(N, dtype=np.complex128)]
+    Is, energies, ecs = [], [], []
     for n in range(n_steps + 1):
-        rho_n = rho_hist[n]
-        hhf_n = h + E_samples[n] * d + hf_self_energy(v, rho_n)
-        I_n = coll(rho_hist, T_row)
+        if n == n_steps:
+            I_n = np.zeros((N, N), np.complex128) if n == 0 else collision(
+                v, np.array(rho_hist), np.array(T_row), trapezoid_weights(n + 1, dt), route)
+        else:
+            rho_next, I_n, T_row = heun_step(h, v, d, rho_hist, T_row, dt, E_samples[n],
+                                             E_samples[n + 1], route)
         Is.append(I_n)
-        et, ec = energy(h, d, E_samples[n], v, rho_n, I_n)
+        et, ec = energy(h, d, E_samples[n], v, rho_hist[n], I_n)
         energies.append(et)
         ecs.append(ec)
-        if n == n_steps:
-            break
-        k1 = _rhs(hhf_n, rho_n, I_n)
-        rho_t = rho_n + dt * k1
-        hhf_t = h + E_samples[n + 1] * d + hf_self_energy(v, rho_t)
-        U = expm_hermitian(0.5 * (hhf_n + hhf_t), dt)
-        T_row = [U @ T for T in T_row] + [np.eye(N, dtype=np.complex128)]
-        I_t = coll(rho_hist + [rho_t], T_row)
-        k2 = _rhs(hhf_t, rho_t, I_t)
-        rho_hist.append(rho_n + 0.5 * dt * (k1 + k2))
+        if n < n_steps:
+            rho_hist.append(rho_next)
 
     return Propagation(np.array(rho_hist), np.array(Is), np.asarray(E_samples[: n_steps + 1]),
                        np.array(energies), np.array(ecs))

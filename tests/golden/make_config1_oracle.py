@@ -2,7 +2,8 @@
 
 Config: N = 24, 32 Coulomb factors, seed 0, dt = 0.02, the pulse
 E(t) = 0.1 sin^2(pi t/10) sin t, 100 Heun steps of Eq. (equalt) with the GKBA
-second-Born collision integral (oracle.propagate).  Stored every 10 steps:
+second-Born collision integral (oracle.propagate, with the paper's Eq. (2b-opt)
+contraction route).  Stored every 10 steps:
 rho(t_n), I(t_n), and at every step Tr rho and the energies.
 Run: python tests/golden/make_config1_oracle.py   (about ten minutes on CPU)
 """
@@ -22,7 +23,7 @@ def main():
     N, nP, dt, n = 24, 32, 0.02, 100
     s = gi.system(N, nP, seed=0)
     E = gi.field(dt * np.arange(n + 1))
-    p = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, E)
+    p = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, E, route="paper")
     idx = np.arange(0, n + 1, 10)
     np.savez_compressed(os.path.join(HERE, "config1_oracle_100steps.npz"),
                         steps=idx, rho=p.rho[idx], I=p.I[idx],

@@ -13,12 +13,11 @@ import pytest
 
 import gkba_inputs as gi
 import oracle as O
+from _check import check, rel
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def cplx(rng, *shape):
@@ -48,9 +47,8 @@ def test_sigma3_vs_oracle(P, precision, N):
     ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.02, precision=precision)
     S = ctx.sigma3(A, B, C)
     ctx.close()
-    e = rel(S, O.sigma3(s["v"], A, B, C))
+    e = check(S, O.sigma3(s["v"], A, B, C), 1e-10 if precision == "fp64" else 2e-5, "S3")
     print(f"N={N} {precision} sigma3 rel err {e:.2e}")
-    assert e < (1e-10 if precision == "fp64" else 2e-5)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "tf32"])
@@ -65,9 +63,9 @@ def test_collision_vjp_vs_oracle(P, precision, N, L):
     rb, tb = ctx.collision_vjp(rho, T, Ibar)
     ctx.close()
     rr, tr = O.collision_vjp(s["v"], rho, T, w, Ibar)
-    er, et = rel(rb, rr), rel(tb, tr)
+    er = check(rb, rr, TOL[precision], "rho_bar")
+    et = check(tb, tr, TOL[precision], "T_bar")
     print(f"N={N} L={L} {precision} collision VJP rel err rho_bar {er:.2e} T_bar {et:.2e}")
-    assert er < TOL[precision] and et < TOL[precision]
 
 
 def test_collision_autograd(P):
@@ -86,10 +84,10 @@ def test_collision_autograd(P):
     loss = torch.real(torch.sum(torch.conj(torch.tensor(a, device="cuda")) * I))
     loss.backward()
     rr, tr = O.collision_vjp(s["v"], rho, T, O.trapezoid_weights(L, 0.02), a)
-    assert rel(r.grad.cpu().numpy(), rr) < 1e-10
-    assert rel(t.grad.cpu().numpy(), tr) < 1e-10
-    ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.02))
-    assert rel(I.detach().cpu().numpy(), ref) < 1e-10
+    check(r.grad.cpu().numpy(), rr, 1e-10)
+    check(t.grad.cpu().numpy(), tr, 1e-10)
+    ref = O.collision(s["v"], rho, T, O.trapezoid_weights(L, 0.02), route="paper")
+    check(I.detach().cpu().numpy(), ref, 1e-10)
     ctx.close()
 
 
@@ -104,11 +102,11 @@ def test_collision_vjp_v_vs_oracle(P):
     rb, tb, vb = ctx.collision_vjp(rho, T, Ibar, want_v=True)
     ctx.close()
     ref = O.collision_vjp_v(s["v"], rho, T, O.trapezoid_weights(L, 0.02), Ibar)
-    e = rel(vb, ref)
+    e = check(vb, ref, 1e-10, "v_bar")
     print(f"N={N} L={L} collision dL/dv rel err {e:.2e}")
-    assert e < 1e-10
     rr, tr = O.collision_vjp(s["v"], rho, T, O.trapezoid_weights(L, 0.02), Ibar)
-    assert rel(rb, rr) < 1e-10 and rel(tb, tr) < 1e-10
+    check(rb, rr, 1e-10, "rho_bar")
+    check(tb, tr, 1e-10, "T_bar")
 
 
 def test_v_gradient_needs_fp64(P):

@@ -11,12 +11,10 @@ import numpy as np
 import pytest
 
 import gkba_inputs as gi
+import oracle as O
+from _check import check, rel
 
 pytestmark = pytest.mark.gpu
-
-
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 @pytest.fixture(scope="module")
@@ -30,11 +28,16 @@ def P():
     return p
 
 
-def make(P, N, L, seed, steps, precision="tf32"):
+def member(N, L, seed):
     # a system with a synthetic history of L points (the last L points of a
     # longer one are a valid history as well)
     s = gi.system(N, 8, seed=seed)
     rho, T = gi.history(N, L, 0.02, seed=seed)
+    return s, rho, T
+
+
+def make(P, N, L, seed, steps, precision="tf32"):
+    s, rho, T = member(N, L, seed)
     ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.02, max_steps=L + steps,
                     precision=precision)
     ctx.set_history(L - 1, rho, T)
@@ -99,3 +102,36 @@ def test_batch_rejects_bad_members(P):
         assert ei.value.status == 4
     a.close()
     f.close()
+
+
+@pytest.mark.parametrize("precision", ["tf32", "tf32acc"])
+def test_batch_step_vs_oracle(P, precision):
+    # One stacked step of members of every basis-size group of the batched
+    # workload (N = 8 ... 48), each checked against the oracle's Heun step
+    # (Eq. equalt) from that member's own history with the paper's Eq.
+    # (2b-opt) contraction: rho(t_{n+1}) and, through the step's diagnostics,
+    # E_c = 1/2 Im Tr I(t_n) and Re Tr I(t_n).
+    spec = [(8, 40, 21), (12, 25, 22), (16, 18, 23), (24, 12, 24), (32, 9, 25), (48, 6, 26),
+            (16, 7, 27)]
+    dt, E_n, E_np1 = 0.02, 0.03, -0.02
+    batched = [make(P, N, L, sd, 1, precision) for N, L, sd in spec]
+    with P.Batch(batched) as b:
+        rhos, diags = b.step(E_n, E_np1)
+    for i, (N, L, sd) in enumerate(spec):
+        s, rho, T = member(N, L, sd)
+        r_ref, I_ref, _ = O.heun_step(s["h"], s["v"], s["d"], list(rho), list(T), dt, E_n, E_np1,
+                                      route="paper")
+        # the step's increment rho(t_{n+1}) - rho(t_n) is linear in the two
+        # collision integrals (plus FP64 commutators), so it carries their
+        # relative error: the split-TF32 collision tolerance applies to it
+        e = check(rhos[i] - rho[-1], r_ref - rho[-1], 2e-5, f"member N={N} L={L} increment")
+        check(rhos[i], r_ref, 1e-5, f"member N={N} L={L} rho")
+        ec_ref = 0.5 * np.trace(I_ref).imag
+        # |Tr X| <= sqrt(N) ||X||_F bounds the trace's error by the matrix's
+        assert abs(diags[i][2] - ec_ref) < 2e-5 * 0.5 * np.sqrt(N) * np.linalg.norm(I_ref), \
+            (N, L, diags[i][2], ec_ref)
+        assert abs(diags[i][3]) < 1e-5 * np.abs(I_ref).max() * N
+        print(f"batch member N={N} L={L} {precision}: rho vs oracle {e:.2e}, "
+              f"E_c {diags[i][2]:.6e} vs {ec_ref:.6e}")
+    for c in batched:
+        c.close()

@@ -14,12 +14,11 @@ import pytest
 
 import gkba_inputs as gi
 import oracle as O
+from _check import check, rel
 
 pytestmark = pytest.mark.gpu
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +60,7 @@ def test_structured_sigma_vs_closed_forms(P, kind, N):
     S = ctx.sigma(G, Gb)
     ctx.close()
     for u in range(3):
-        assert rel(S[u], closed_form(kind, c["v"], G[u], Gb[u])) < 1e-12
+        check(S[u], closed_form(kind, c["v"], G[u], Gb[u]), 1e-12)
 
 
 @pytest.mark.parametrize("kind", ["diagonal", "symmetric"])
@@ -74,10 +73,9 @@ def test_structured_collision_vs_oracle(P, kind):
     ctx = P.Context(c["h"], c["v"], c["d"], c["rho0"], dt, interaction=kind)
     I = ctx.collision(rho, T)
     ctx.close()
-    ref = O.collision(expand(kind, c["v"]), rho, T, O.trapezoid_weights(L, dt))
-    e = rel(I, ref)
+    ref = O.collision(expand(kind, c["v"]), rho, T, O.trapezoid_weights(L, dt), route="paper")
+    e = check(I, ref, 1e-12, f"{kind} collision")
     print(f"{kind} N={N} L={L} collision rel err {e:.3e}")
-    assert e < 1e-12
 
 
 @pytest.mark.parametrize("kind,dt", [("diagonal", 0.01), ("symmetric", 0.025)])
@@ -86,12 +84,12 @@ def test_structured_propagation_vs_oracle(P, kind, dt):
     N, n = 10, 20
     c = gi.chain(N, kind)
     E = np.zeros(n + 1)
-    ref = O.propagate(c["h"], expand(kind, c["v"]), c["d"], c["rho0"], dt, n, E)
+    ref = O.propagate(c["h"], expand(kind, c["v"]), c["d"], c["rho0"], dt, n, E, route="paper")
     ctx = P.Context(c["h"], c["v"], c["d"], c["rho0"], dt, max_steps=n, interaction=kind)
     worst = 0.0
     for k in range(n):
         rho, I, diag = ctx.step(0.0, 0.0)
-        worst = max(worst, rel(rho, ref.rho[k + 1]))
+        worst = max(worst, check(rho, ref.rho[k + 1], 1e-10, f"rho step {k + 1}"))
         assert abs(diag[1] - ref.energy_total[k]) < 1e-10
     ctx.close()
     print(f"{kind} chain, {n} steps: max rel err of rho vs oracle {worst:.3e}")

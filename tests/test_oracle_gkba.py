@@ -177,8 +177,9 @@ def test_flipped_sigma_sign_breaks_energy_conservation(monkeypatch):
     s = gi.system(4, 8, seed=0)
     dt, n = 0.1, 60
     good = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, np.zeros(n + 1))
-    orig = O.sigma_independent
-    monkeypatch.setattr(O, "sigma_independent", lambda v, G, Gb: -orig(v, G, Gb))
+    # the propagation's default route is the paper's Eq. (2b-opt)
+    orig = O.sigma_paper
+    monkeypatch.setattr(O, "sigma_paper", lambda v, G, Gb: -orig(v, G, Gb))
     with np.errstate(all="ignore"):
         try:
             bad = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, np.zeros(n + 1))
