@@ -1548,9 +1548,21 @@ extern "C" gkba_status gkba_sigma_noalloc(int N, int n_units, const double* v, c
     if ((size_t)(q - s) > kNoAllocScratchBytes)
         return noalloc_fail(err, err_len, GKBA_EINVAL, "gkba_sigma_noalloc: scratch layout overflow");
 
+    // An error pending from earlier, unrelated work is reported as such and
+    // left in place for its owner; launch errors of this call are checked
+    // after every group of launches, so a failed launch stops the rest.
+    ce = cudaPeekAtLastError();
+    if (ce != cudaSuccess)
+        return noalloc_fail(err, err_len, GKBA_ECUDA,
+                            "gkba_sigma_noalloc: a CUDA error is pending from earlier work: %s",
+                            cudaGetErrorString(ce));
     // model operands (rebuilt on every call; every element is written)
     k_build_wS64<<<grid1(N4, 256), 256, 0, stream>>>(N, v, wS);
     k_build_vK64<<<grid1(N4, 256), 256, 0, stream>>>(N, v, vK);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess)
+        return noalloc_fail(err, err_len, GKBA_ECUDA, "gkba_sigma_noalloc: launch failed: %s",
+                            cudaGetErrorString(ce));
     const double2* Gd = (const double2*)G;
     const double2* Gbd = (const double2*)Gbar;
     double2* Sd = (double2*)S_out;
@@ -1587,11 +1599,11 @@ extern "C" gkba_status gkba_sigma_noalloc(int N, int n_units, const double* v, c
         dim3 g1(grid1(nb * NN, 256), nzc);
         k_reduce_partials_p1<double><<<g1, 256, 0, stream>>>(N, N, nb, nz, zper, n * R, R, part, red);
         k_reduce_partials_p2<<<grid1(nb * NN, 256), 256, 0, stream>>>(nb * NN, nzc, red, Sd + u0 * NN);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess)
+            return noalloc_fail(err, err_len, GKBA_ECUDA, "gkba_sigma_noalloc: launch failed: %s",
+                                cudaGetErrorString(ce));
     }
-    ce = cudaGetLastError();
-    if (ce != cudaSuccess)
-        return noalloc_fail(err, err_len, GKBA_ECUDA, "gkba_sigma_noalloc: launch failed: %s",
-                            cudaGetErrorString(ce));
     return GKBA_OK;
 }
 

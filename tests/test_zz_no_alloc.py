@@ -14,14 +14,14 @@ import numpy as np
 import pytest
 
 import gkba_inputs as gi
+import oracle as O
+from _check import check
 
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10  # the FP64 path's tolerance in tests/test_gpu_parity.py
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def test_noalloc_sigma_matches_gkba_sigma_on_two_calls():
@@ -50,8 +50,11 @@ def test_noalloc_sigma_matches_gkba_sigma_on_two_calls():
         stream.synchronize()
         assert st == gkba.OK, msg.value.decode()
         S = S_d.cpu().numpy()
+        # against the context entry point, and against the oracle's Eq. (2b-opt) route
+        oracle_ref = O.sigma_paper(s["v"], G, Gb)
         for u in range(U):
-            assert rel(S[u], ref[u]) < TOL64, (call, u, rel(S[u], ref[u]))
+            check(S[u], ref[u], TOL64, f"call {call} unit {u} vs gkba_sigma")
+            check(S[u], oracle_ref[u], TOL64, f"call {call} unit {u} vs oracle")
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
