@@ -66,13 +66,16 @@ typedef enum {
     GKBA_FP64 = 0,       /* every contraction in FP64 on the CUDA cores */
     GKBA_SPLIT_TF32 = 1, /* contractions on tcgen05 tensor cores: FP32 data,
                             3 TF32 products (hi*hi + hi*lo + lo*hi), FP32
-                            accumulation inside a K-chunk, FP64 across chunks;
+                            accumulation in short tensor-memory windows (see
+                            gkba_config.acc_window), added on the CUDA cores and
+                            across the last contraction's K ranges in FP64;
                             P/Q, T recursion, I history sum and rho update stay FP64 */
-    GKBA_SPLIT_TF32_ACC = 2 /* as GKBA_SPLIT_TF32 with the correction products
-                            accumulated apart from hi*hi and 64-long FP32 chunks in
-                            the last contraction: about half the error of
-                            GKBA_SPLIT_TF32 (tensor-core accumulation truncates),
-                            about 25% slower */
+    GKBA_SPLIT_TF32_ACC = 2 /* as GKBA_SPLIT_TF32; for N > 48, where the first three
+                            contractions accumulate a whole tile in one tensor-memory
+                            accumulator, the correction products go to a second
+                            accumulator so that only hi*hi truncates at the scale of
+                            the result (about 15 % slower there; identical to
+                            GKBA_SPLIT_TF32 for N <= 48) */
 } gkba_precision;
 
 typedef enum {
@@ -106,13 +109,18 @@ typedef struct {
     int device;        /* CUDA device ordinal (-1 = current device) */
     int timing;        /* nonzero: time every contraction kernel with CUDA events
                           (see gkba_get_stats) */
-    int s4_kchunk;     /* split-TF32 modes: length of the K ranges (K = N^3) the
-                          tensor core accumulates in FP32 in the last contraction
-                          before they are added on the CUDA cores (8 ranges per
-                          FP32 partial, partials summed in FP64); a multiple of 64,
-                          0 = default (512 for GKBA_SPLIT_TF32, 64 for
-                          GKBA_SPLIT_TF32_ACC).  Shorter ranges bound the
-                          tensor-core accumulation error. */
+    int acc_window;    /* split-TF32 modes: K length (8, 16 or 32; 0 = 32) of one
+                          tensor-memory accumulation window.  The tensor core
+                          truncates its FP32 accumulator additions toward zero, a
+                          coherent bias that grows with the accumulation length,
+                          so the last contraction (K = N^3) and, for N <= 48,
+                          every contraction accumulate only that much of K in
+                          tensor memory before the epilogue adds the window in
+                          FP32 registers (Kahan-compensated in the last one);
+                          inside a window the correction products come first and
+                          hi*hi last, so only the hi*hi MMAs truncate at the scale
+                          of the result.  Shorter windows: smaller bias, more
+                          drains. */
     int interaction;   /* gkba_interaction: form of the v argument of gkba_init;
                           GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC need precision GKBA_FP64 */
     int history;       /* gkba_history: how gkba_step evaluates the history sum
@@ -282,7 +290,10 @@ gkba_status gkba_get_stats(gkba_ctx* ctx, gkba_kernel_stat* stats, int max_stats
  * race with each other: serialise them.  Every scratch element a call reads
  * is written earlier in the same call, so nothing left by a previous call
  * leaks into the result.  The call only enqueues work: S_out is valid after
- * the stream is synchronised; launch errors return GKBA_ECUDA.
+ * the stream is synchronised.  Launch errors return GKBA_ECUDA (checked after
+ * every chunk of units, so a failed launch stops the rest); a CUDA error that
+ * is already pending from earlier work on the calling thread is reported as
+ * GKBA_ECUDA before anything is launched and left in place.
  */
 gkba_status gkba_sigma_noalloc(int N, int n_units, const double* v, const double* G,
                                const double* Gbar, double* S_out, void* cuda_stream, char* err,
@@ -324,7 +335,7 @@ gkba_status gkba_collision_vjp(gkba_ctx* ctx, int L, const double* rho_hist, con
  * N^2 / N^3 work (mean field, propagator, Heun update) runs per system.
  *
  * gkba_batch_create - ctxs: n_ctx distinct contexts made by gkba_init with
- *   the same split-TF32 precision and s4_kchunk, the general interaction and
+ *   the same split-TF32 precision and acc_window, the general interaction and
  *   the same device.  They stay owned by the caller and must outlive the
  *   batch; during gkba_batch_step every member runs on the batch's stream.
  *   workspace_bytes caps the stacked workspaces of all groups together (0 =
@@ -356,6 +367,19 @@ void gkba_batch_destroy(gkba_batch* batch);
  * The context stays usable.
  */
 gkba_status gkba_selftest_timeout(gkba_ctx* ctx, double limit_ms, double* elapsed_ms);
+
+/*
+ * gkba_measure_tf32_mma - measures the tensor-pipe rate that bounds the
+ * split-TF32 contraction (the roofline denominator; the paper has no
+ * counterpart): every pair of SMs issues `iters` x 4 back-to-back
+ * tcgen05.mma.cta_group::2.kind::tf32 instructions of the stage kernels'
+ * shape (M = 256, N = 192, K = 8, A in tensor memory, B in shared memory,
+ * zero operands) with nothing else running on the SM; the launch is timed
+ * with CUDA events on the context's stream after a shorter warm-up launch.
+ *   iters   16 ... 1e8 (1e5 takes about 20 ms on a GB300)
+ *   tflops  out: 2 x 256 x 192 x 8 flops per MMA over the measured time
+ */
+gkba_status gkba_measure_tf32_mma(gkba_ctx* ctx, int iters, double* tflops);
 
 /* Message for the last failing call on ctx (or the last failed gkba_init when ctx is NULL). */
 const char* gkba_last_error(const gkba_ctx* ctx);

@@ -105,7 +105,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const double form_bytes = !gen ? 0.0 : tc ? 4.0 * 2 * Np * Np * 4 : (2.0 * NN + 4.0 * NN) * 8;
     const double N3 = (double)NN * N;
     const double part_per_unit = !gen ? 0.0
-                                 : tc ? (std::ceil((double)Np * Np * Np / (8.0 * c->s4_kchunk)) * Np * 2.0 * Np * 4)
+                                 : tc ? (std::ceil((double)Np * Np * Np / kTcItemK) * Np * 2.0 * Np * 4)
                                       : (std::ceil(N3 / 8192.0) * N * 2.0 * N * 8);
     const double per_unit = 2 * x_bytes + form_bytes + part_per_unit + (4.0 + kReduceSplit) * NN * 16 + 8;
     size_t cap = c->ws_cap;
@@ -137,7 +137,7 @@ gkba_status ensure_workspace(gkba_ctx* c, int want_units) {
     const size_t oX2 = cv.take((size_t)(x_bytes * ub));
     size_t part_bytes;
     if (!gen) part_bytes = 0;
-    else if (tc) part_bytes = tf32_part_bytes((int)Np, ub, c->s4_kchunk);
+    else if (tc) part_bytes = tf32_part_bytes((int)Np, ub, c->acc_window);
     else {
         const long long nz = (long long)std::ceil(N3 / 8192.0);
         part_bytes = (size_t)(nz * N * 2LL * N * ub * 8);
@@ -451,9 +451,9 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         return fail(nullptr, GKBA_EINVAL, "gkba_init: dt must be positive and finite");
     if (cfg->max_steps < 0 || cfg->max_steps > 100000000)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: max_steps=%d invalid", cfg->max_steps);
-    if (cfg->s4_kchunk < 0 || cfg->s4_kchunk % 64 != 0)
-        return fail(nullptr, GKBA_EINVAL, "gkba_init: s4_kchunk=%d must be a non-negative multiple of 64",
-                    cfg->s4_kchunk);
+    if (cfg->acc_window != 0 && cfg->acc_window != 8 && cfg->acc_window != 16 && cfg->acc_window != 32)
+        return fail(nullptr, GKBA_EINVAL, "gkba_init: acc_window=%d must be 0, 8, 16 or 32",
+                    cfg->acc_window);
     if (cfg->precision != GKBA_FP64 && cfg->precision != GKBA_SPLIT_TF32 &&
         cfg->precision != GKBA_SPLIT_TF32_ACC)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown precision %d", cfg->precision);
@@ -535,8 +535,7 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
     c->history = cfg->history;
     c->ws_cap = cfg->workspace_bytes ? cfg->workspace_bytes : ((size_t)64 << 30);
     c->timing = cfg->timing != 0;
-    c->s4_kchunk = cfg->s4_kchunk > 0 ? cfg->s4_kchunk
-                                       : (cfg->precision == GKBA_SPLIT_TF32_ACC ? 64 : 512);
+    c->acc_window = cfg->acc_window > 0 ? cfg->acc_window : kTcWindowK;
     c->device = -1;
     auto bail = [&](gkba_status st) {
         {
@@ -1172,6 +1171,15 @@ gkba_status gkba_selftest_timeout(gkba_ctx* c, double limit_ms, double* elapsed_
     return finish(c);  // reads the error word the expired wait wrote: GKBA_ETIMEOUT
 }
 
+gkba_status gkba_measure_tf32_mma(gkba_ctx* c, int iters, double* tflops) {
+    if (!c || !tflops) return fail(c, GKBA_EINVAL, "gkba_measure_tf32_mma: NULL argument");
+    if (iters < 16 || iters > 100000000)
+        return fail(c, GKBA_EINVAL, "gkba_measure_tf32_mma: iters=%d must be in [16, 1e8]", iters);
+    GKBA_CUDA(c, cudaSetDevice(c->device));
+    GKBA_TRY(measure_tf32_mma(c, iters, tflops));
+    return finish(c);
+}
+
 const char* gkba_last_error(const gkba_ctx* c) {
     if (c) return c->err.c_str();
     std::lock_guard<std::mutex> g(g_err_mu);
@@ -1402,9 +1410,9 @@ gkba_status gkba_batch_create(gkba_batch** out, gkba_ctx* const* ctxs, int n_ctx
         if (!tensor_core_path(c) || c->kind != GKBA_V_GENERAL)
             return batch_fail(nullptr, GKBA_EINVAL,
                               "gkba_batch_create: context %d is not a split-TF32 general-basis context", i);
-        if (c->prec != ctxs[0]->prec || c->device != ctxs[0]->device || c->s4_kchunk != ctxs[0]->s4_kchunk)
+        if (c->prec != ctxs[0]->prec || c->device != ctxs[0]->device || c->acc_window != ctxs[0]->acc_window)
             return batch_fail(nullptr, GKBA_EINVAL,
-                              "gkba_batch_create: contexts differ in precision, device or s4_kchunk");
+                              "gkba_batch_create: contexts differ in precision, device or acc_window");
     }
     gkba_batch* b = new gkba_batch();
     b->device = ctxs[0]->device;
@@ -1443,7 +1451,7 @@ gkba_status gkba_batch_create(gkba_batch** out, gkba_ctx* const* ctxs, int n_ctx
         sh->num_sms = c0->num_sms;
         sh->pair_clusters = c0->pair_clusters;
         sh->fin_pair_clusters = c0->fin_pair_clusters;
-        sh->s4_kchunk = c0->s4_kchunk;
+        sh->acc_window = c0->acc_window;
         sh->ws_cap = cap_total / b->groups.size();
         sh->nsys = (int)g.members.size();
         const long long Np = sh->Np, Np4 = Np * Np * Np * Np;

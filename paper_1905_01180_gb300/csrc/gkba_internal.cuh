@@ -71,7 +71,7 @@ struct gkba_ctx {
     int nsys = 1;
     double* vm = nullptr;       // U (N) or V (N*N) of a structured interaction
     int history = GKBA_HISTORY_SUM;  // gkba_history
-    int s4_kchunk = 512;
+    int acc_window = 32;
 
     // model on the device
     double2* h = nullptr;   // N*N
@@ -303,9 +303,15 @@ gkba_status collision_vjp_dev(gkba_ctx* c, int L, const double2* rho, const doub
 gkba_status build_forms3_tf32(gkba_ctx* c, int nb, const double2* A);
 gkba_status reduce_partials_launch(gkba_ctx* c, int nb, int nz, long long zstride, long long Rld,
                                    const void* part, bool fp32, double2* S);
+// K length of one work item of the tensor-core S4 stage (one FP32 partial per
+// item and output row).
+constexpr int kTcItemK = 4096;
+// Default K length of one tensor-memory accumulation window of that stage.
+constexpr int kTcWindowK = 32;
 size_t tf32_part_bytes(int Np, int ub, int kchunk);
 // Launch the bounded-wait self-test (a wait that must run out); elapsed_ms[2].
 gkba_status wait_selftest(gkba_ctx* c, double limit_ms, double* elapsed_ms);
+gkba_status measure_tf32_mma(gkba_ctx* c, int iters, double* tflops);
 
 // ---- time-linear history (time_linear.cu) ---------------------------------
 // Terms of nk history points (rho_k, W_k = Ucal_k^+ at stride sW) summed into

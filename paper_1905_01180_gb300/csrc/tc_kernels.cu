@@ -27,6 +27,7 @@
 // MMAs, frees its tensor memory and returns.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstdlib>
 
 #include "gkba_internal.cuh"
@@ -312,9 +313,13 @@ struct StageParams {
     long long out_unit;
     StageMap map;
     int* err;
+    int wsteps;        // 0: one accumulator per tile; 1 or 2: windows of that many K steps
+    int nring;         // windowed: accumulators in the ring (<= kStageRing)
+    int as2;           // windowed: ring stride in columns (2 Np rounded up to 32)
 };
 
 constexpr int kStageAStages = 4;
+constexpr int kStageRing = 8;
 constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-11 epilogue
 
 // ---------------------------------------------------------------------------
@@ -359,7 +364,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
     uint64_t* bars = (uint64_t*)(sA + kStageAStages * kTileBytes);
     constexpr int BFULL = 0, BPEER = 1, BEMPTY = 2, AFULL = 3, AEMPTY = AFULL + kStageAStages,
                   TFULL = AEMPTY + kStageAStages, TEMPTY = TFULL + 2, ACCF = TEMPTY + 2,
-                  ACCE = ACCF + 2, DRAIN = ACCE + 2, NBARS = DRAIN + 1;
+                  ACCE = ACCF + 2, DRAIN = ACCE + 2, WF = DRAIN + 1, WE = WF + kStageRing,
+                  NBARS = WE + kStageRing;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     auto bar = [&](int i) { return smem_u32(bars + i); };
@@ -382,6 +388,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             mbar_init(bar(ACCF + s), 1);
             mbar_init(bar(ACCE + s), 8);
         }
+        for (int b = 0; b < kStageRing; ++b) {
+            mbar_init(bar(WF + b), 1);
+            mbar_init(bar(WE + b), 8);
+        }
         mbar_init(bar(DRAIN), 1);
         *abort_flag = 0;
         fence_barrier_init();
@@ -400,6 +410,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
     cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // A slot columns: windowed mode 0 / 64 (the ring follows at 128), else 192 / 448
+    const bool win = p.wsteps > 0;
+    const uint32_t slot_col0 = win ? 0u : 192u, slot_col1 = win ? 64u : 448u;
+    const int ktail = (Np & (kKC - 1)) ? (Np & (kKC - 1)) / 8 : 4;  // K steps of a plane's last chunk
+    // K steps of chunk c (a plane's last chunk holds Np % 32 = 16 valid K when Np is an odd
+    // multiple of 16) and windows per tile in the windowed mode
+    int win_per_tile = 0;
+    if (win)
+        for (int c = 0; c < nchunk; ++c) win_per_tile += ((c % p.kch) == p.kch - 1 ? ktail : 4) / p.wsteps;
 
     const long long ipu = p.mtiles / 2;  // 256-row tiles per unit
     const long long total = (long long)p.units * ipu;
@@ -467,7 +486,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             const unsigned long long dBlo0 = desc_sw128(smem_u32(sBlo));
             int cur_u = -1;
             uint32_t bfph = 0;
-            long long it = 0, tile_i = 0;
+            long long it = 0, tile_i = 0, wcount = 0;
             bool ok = true, issued = false;
             for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
                 const int u = (int)(t / ipu);
@@ -477,6 +496,45 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     bfph ^= 1;
                     cur_u = u;
                     tc_fence_after();
+                }
+                if (win) {
+                    // Windowed accumulation: every wsteps K steps go to the next
+                    // accumulator of a ring that the epilogue drains into FP32
+                    // register sums; inside a window the correction products come
+                    // first, while the accumulator is still small, then hi*hi.
+                    int kc = 0;
+                    for (int c = 0; c < nchunk && ok; ++c, ++it) {
+                        const int slot = (int)(it & 1);
+                        const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                        if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t ahi = tmem + (slot ? slot_col1 : slot_col0);
+                        const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
+                        const unsigned long long dl = dBlo0 + ((unsigned long long)(c * chunkB) >> 4);
+                        const int ksteps = kc == p.kch - 1 ? ktail : 4;
+                        if (++kc == p.kch) kc = 0;
+                        for (int kw = 0; kw < ksteps; kw += p.wsteps, ++wcount) {
+                            const int b = (int)(wcount % p.nring);
+                            if (!mbar_wait_cl(bar(WE + b), (uint32_t)((wcount / p.nring) & 1) ^ 1u, abort_flag, peer_abort, p.err, 19)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t dw = tmem + 128u + (uint32_t)(b * p.as2);
+#pragma unroll 1
+                            for (int kk = kw; kk < kw + p.wsteps; ++kk) {
+                                mma_tf32_pair(dw, ahi + kk * 8, dl + 2ull * kk, id, kk == kw ? 0u : 1u);
+                                mma_tf32_pair(dw, ahi + kk * 8 + 32, dh + 2ull * kk, id, 1u);
+                            }
+#pragma unroll 1
+                            for (int kk = kw; kk < kw + p.wsteps; ++kk)
+                                mma_tf32_pair(dw, ahi + kk * 8, dh + 2ull * kk, id, 1u);
+                            mma_commit_pair(bar(WF + b), (uint16_t)3);
+                        }
+                        if (!ok) break;
+                        issued = true;
+                        mma_commit_pair(bar(TEMPTY + slot), (uint16_t)3);
+                    }
+                    if (!ok) break;
+                    if (t + 1 < t1 && (int)((t + 1) / ipu) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
+                    continue;
                 }
                 const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
                 const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
@@ -488,7 +546,46 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 // multiple of 16 (the rest is the TMA's zero fill): its zero K steps are
                 // skipped.  kc counts chunks within the plane (no division in this loop:
                 // this thread's issue rate bounds the kernel).
-                const int ktail = (Np & (kKC - 1)) ? (Np & (kKC - 1)) / 8 : 4;
+                if (!SPLIT_ACC && nchunk <= 2) {
+                    // The tile's whole K fits the two A slots: issue every correction
+                    // product first, while the accumulator is still small, then hi*hi,
+                    // so the only truncating additions at the scale of the result are
+                    // those of the hi*hi MMAs (as with separate accumulators, but
+                    // keeping the double-buffered accumulator).
+                    int ksteps[2];
+                    for (int c = 0; c < nchunk; ++c) {
+                        const long long ic = it + c;
+                        if (!mbar_wait_cl(bar(TFULL + (int)(ic & 1)), (uint32_t)((ic >> 1) & 1), abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
+                        ksteps[c] = (c % p.kch) == p.kch - 1 ? ktail : 4;
+                    }
+                    if (!ok) break;
+                    tc_fence_after();
+                    bool first = true;
+                    for (int c = 0; c < nchunk; ++c) {
+                        const uint32_t ahi = tmem + (((it + c) & 1) ? slot_col1 : slot_col0);
+                        const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
+                        const unsigned long long dl = dBlo0 + ((unsigned long long)(c * chunkB) >> 4);
+#pragma unroll 1
+                        for (int kk = 0; kk < ksteps[c]; ++kk) {
+                            mma_tf32_pair(dacc, ahi + kk * 8, dl + 2ull * kk, id, first ? 0u : 1u);
+                            mma_tf32_pair(dacc, ahi + kk * 8 + 32, dh + 2ull * kk, id, 1u);
+                            first = false;
+                        }
+                    }
+                    for (int c = 0; c < nchunk; ++c) {
+                        const uint32_t ahi = tmem + (((it + c) & 1) ? slot_col1 : slot_col0);
+                        const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
+#pragma unroll 1
+                        for (int kk = 0; kk < ksteps[c]; ++kk)
+                            mma_tf32_pair(dacc, ahi + kk * 8, dh + 2ull * kk, id, 1u);
+                        mma_commit_pair(bar(TEMPTY + (int)((it + c) & 1)), (uint16_t)3);
+                    }
+                    it += nchunk;
+                    issued = true;
+                    mma_commit_pair(bar(ACCF + ab), (uint16_t)3);
+                    if (t + 1 < t1 && (int)((t + 1) / ipu) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
+                    continue;
+                }
                 int kc = 0;
                 for (int c = 0; c < nchunk; ++c, ++it) {
                     const int slot = (int)(it & 1);
@@ -496,7 +593,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
                     tc_fence_after();
                     // descriptor start field = address >> 4: a 32-byte K step adds 2
-                    const uint32_t ahi = tmem + (slot ? 448u : 192u);
+                    const uint32_t ahi = tmem + (slot ? slot_col1 : slot_col0);
                     const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
                     const unsigned long long dl = dBlo0 + ((unsigned long long)(c * chunkB) >> 4);
                     const int ksteps = kc == p.kch - 1 ? ktail : 4;
@@ -562,7 +659,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 const uint32_t sph = (uint32_t)((it >> 1) & 1);
                 if (!warp_wait_cl(bar(TEMPTY + slot), sph ^ 1, abort_flag, peer_abort, p.err, 7)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t ta = lane_base + (slot ? 448u : 192u);
+                const uint32_t ta = lane_base + (slot ? slot_col1 : slot_col0);
                 tmem_st32(ta, hi);
                 tmem_st32(ta + 32, lo);
                 tmem_wait_st();
@@ -577,9 +674,51 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
         const int rloc = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
         const int ncc = (2 * Np) / 32;
-        long long tile_i = 0;
+        long long tile_i = 0, wc = 0;
         bool ok = true;
-        for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
+        for (long long t = t0; t < t1 && ok && win; ++t) {
+            // windowed mode (2 Np <= 96): add the tile's windows in FP32 registers
+            const int u = (int)(t / ipu);
+            float acc[96];
+#pragma unroll
+            for (int j = 0; j < 96; ++j) acc[j] = 0.0f;
+            for (int i = 0; i < win_per_tile; ++i, ++wc) {
+                const int b = (int)(wc % p.nring);
+                if (!warp_wait_cl(bar(WF + b), (uint32_t)((wc / p.nring) & 1), abort_flag, peer_abort, p.err, 20)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    if (cc < ncc) {
+                        uint32_t v[32];
+                        tmem_ld32(lane_base + 128u + (uint32_t)(b * p.as2 + cc * 32), v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[cc * 32 + j] += __uint_as_float(v[j]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(bar0(WE + b));
+            }
+            if (!ok) break;
+            const long long row = (t % ipu) * (2 * kBM) + (long long)rank * kBM + rloc;
+            if (row < p.M) {
+                const long long x = row % p.map.Dx;
+                const long long rb = row / p.map.Dx;
+                const long long xo = p.map.XB ? (x >> 5) * p.map.XB + (x & 31) : x * p.map.SX;
+                float* o = p.out + (long long)u * p.out_unit + (rb / p.map.Db) * p.map.SA +
+                           (rb % p.map.Db) * p.map.SB + xo;
+#pragma unroll
+                for (int col = 0; col < 96; ++col) {
+                    if (col < 2 * Np) {
+                        const int hc = col >= Np ? 1 : 0;
+                        const int y = col - hc * Np;
+                        o[hc * p.map.SC + (long long)y * p.map.SY] = acc[col];
+                    }
+                }
+            }
+        }
+        for (long long t = t0; t < t1 && ok && !win; ++t, ++tile_i) {
             const int u = (int)(t / ipu);
             const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
             const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
@@ -643,28 +782,66 @@ struct FinalParams {
     long long Rld;
     int* err;
     int blocked;   // A is K-blocked: [K/32][Rld rows][32] (3-D map) instead of [rows][K]
-    int KS;        // pair kernel: K length accumulated in TMEM before the epilogue adds it
+    int KS;        // K length of one accumulation window in tensor memory: 8, 16 or 32
     const int* unit_sys;  // batches of several systems: unit -> system (3-D vK maps), else null
 };
 
-constexpr int kFinThreads = 384;
+constexpr int kFinThreads = 448;  // 14 warps: see the S4 kernel
 
 // ---------------------------------------------------------------------------
 // Stage S4 on CTA pairs: D[(u,c,j)][i] = sum_K X3[(u,c,j)][K] vK[i][K].
-// Work item = (256-row group g: one 128-row tile per CTA, K range of KW).
-// Each CTA stages, per 64-wide K chunk, its A tile (two 32-wide boxes) and its
-// Np/2 rows of vK (hi and lo); the even CTA
-// issues M = 256, N = Np MMAs for the pair.  The accumulator is double
-// buffered: every KS of K the MMAs switch buffers and the epilogue adds the
-// finished FP32 partial (the tensor core's own accumulation covers at most
-// KS terms, which bounds its truncation error) into per-thread register
-// sums, written once per item.  Barrier protocol as in k_tc_pair; a stage is
-// free again when both CTAs' converters have read A and the pair's MMAs have
-// read B (EMPTY count 4 + 1 multicast commit).
+//
+// Work item = (256-row group g: one 128-row tile per CTA, a K range of KW).
+// Per 32-wide K chunk each CTA stages its A box and its Np/2 rows of vK (hi
+// and lo) in one of eight pipeline stages; a converter warpgroup splits the A
+// box into TF32 hi and lo in the CTA's tensor memory; the even CTA issues
+// M = 256, N = Np MMAs for the pair.
+//
+// Accuracy: the tensor core truncates its FP32 accumulator additions toward
+// zero.  Over the N^3-long sum of this stage that bias is not uniform: it
+// depends on how much a unit's partial sums cancel, so it differs between the
+// Sigma^< and Sigma^> units and breaks the exact cancellation behind
+// particle-number conservation (Re Tr I = 0); measured against the FP64
+// path it grows with the accumulation length roughly as its 1.8th power.
+// This stage therefore accumulates in tensor memory only over windows of KS
+// (8, 16 or 32) of K, each drained by the epilogue into FP32 register sums
+// with Kahan compensation (so the number of windows does not add rounding
+// error).  Inside a window the two correction products hi*lo + lo*hi (about
+// 2^-11 of the result) are issued first, while the accumulator is still
+// small, and the hi*hi products after them, so the only truncations at the
+// scale of the result are those of the KS / 8 hi*hi MMAs.  The window
+// accumulators rotate so the MMAs do not wait on the drains.
+//
+// Tensor memory (512 columns, same address in both CTAs): three A slots (hi
+// in 32 columns, lo in the next 32) at 0, 64 and 128, so the converter works
+// up to two chunks ahead of the MMAs; three window accumulators of AS = Np
+// rounded up to 32 columns at 192 + b AS.
+//
+// Warps: 0 TMA producer, 1 MMA issuer (even CTA), 4-7 converter, and eight
+// epilogue warps, two per tensor-memory lane quarter (a warp reads only the
+// lanes of quarter warp % 4): 8-11 drain the first half of the Np columns,
+// 12, 13, 2, 3 the second half.
+//
+// Barriers: FULL (TMA bytes) and EMPTY (4 converter warps read A + one
+// multicast commit of the MMAs that read B) per stage and CTA; TFULL (4
+// converter warps of each CTA arrive on the even CTA's barrier) and TEMPTY
+// per A slot; WF / WE (full / drained by 8 warps of each CTA) per window
+// accumulator.  Every wait is bounded.
 // ---------------------------------------------------------------------------
-constexpr int kFinPairStages = 3;
-constexpr int kFinKC = 2 * kKC;  // K per pipeline chunk: two 32-wide TMA boxes
+constexpr int kFinPairStages = 8;
+constexpr int kFinKC = kKC;      // K per pipeline chunk: one 32-wide TMA box
 constexpr int kFinMaxNp = 96;
+constexpr int kFinWindows = 3;   // window accumulators in tensor memory
+constexpr int kFinSlots = 3;     // A (hi, lo) slots in tensor memory
+constexpr uint32_t kFinWinCol = 64u * kFinSlots;  // first window accumulator column
+constexpr int kFinEpiWarps = 8;
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : W8(v, 0)
+                 : "r"(taddr)
+                 : "memory");
+}
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     k_tc_final_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
@@ -672,20 +849,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int Np = p.Np, Nh = Np / 2;
-    const uint32_t bbytes = (uint32_t)(Nh * 128);  // this CTA's B rows, one 32-wide box
-    const uint32_t stage_bytes = 2 * kTileBytes + 4 * bbytes;  // A0 A1 Bhi0 Bhi1 Blo0 Blo1
+    const uint32_t AS = (uint32_t)((Np + 31) & ~31);  // window accumulator stride in columns
+    const uint32_t bbytes = (uint32_t)(Nh * 128);     // this CTA's B rows, one 32-wide box
+    const uint32_t stage_bytes = kTileBytes + 2 * bbytes;  // A, Bhi, Blo
     uint64_t* bars = (uint64_t*)(smem + kFinPairStages * stage_bytes);
     constexpr int FULL = 0, EMPTY = FULL + kFinPairStages, TFULL = EMPTY + kFinPairStages,
-                  TEMPTY = TFULL + 2, ACCF = TEMPTY + 2, ACCE = ACCF + 2, DRAIN = ACCE + 2,
-                  NBARS = DRAIN + 1;
+                  TEMPTY = TFULL + kFinSlots, WF = TEMPTY + kFinSlots, WE = WF + kFinWindows,
+                  DRAIN = WE + kFinWindows, NBARS = DRAIN + 1;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     auto bar = [&](int i) { return smem_u32(bars + i); };
-    auto stA = [&](int s, int h) { return smem + s * stage_bytes + h * kTileBytes; };
-    auto stBhi = [&](int s, int h) { return smem + s * stage_bytes + 2 * kTileBytes + h * bbytes; };
-    auto stBlo = [&](int s, int h) {
-        return smem + s * stage_bytes + 2 * kTileBytes + (2 + h) * bbytes;
-    };
+    auto stA = [&](int s) { return smem + s * stage_bytes; };
+    auto stBhi = [&](int s) { return smem + s * stage_bytes + kTileBytes; };
+    auto stBlo = [&](int s) { return smem + s * stage_bytes + kTileBytes + bbytes; };
 
     const uint32_t rank = cluster_rank();
     const uint32_t peer_abort = mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
@@ -696,11 +872,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
             mbar_init(bar(FULL + s), 1);
             mbar_init(bar(EMPTY + s), 5);  // 4 converter warps + 1 multicast MMA commit
         }
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kFinSlots; ++s) {
             mbar_init(bar(TFULL + s), 8);
             mbar_init(bar(TEMPTY + s), 1);
-            mbar_init(bar(ACCF + s), 1);
-            mbar_init(bar(ACCE + s), 8);
+        }
+        for (int b = 0; b < kFinWindows; ++b) {
+            mbar_init(bar(WF + b), 1);
+            mbar_init(bar(WE + b), 2 * kFinEpiWarps);
         }
         mbar_init(bar(DRAIN), 1);
         *abort_flag = 0;
@@ -719,9 +897,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     __syncthreads();
     cluster_sync_all();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;  // accumulators at 0 and 128, A slots at 256 and 384
+    const uint32_t tmem = *tmem_slot;
     const long long items = (long long)p.ngroups * p.nks;
     const long long ncl = cluster_count_x(), cid = cluster_id_x();
+    // epilogue role: warps 8-11 (first half of the columns), 12, 13, 2, 3 (second half)
+    const int epi = warp >= 8 ? warp - 8 : (warp == 2 || warp == 3) ? warp + 4 : -1;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -740,17 +920,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                     const uint32_t ph = (uint32_t)((it / kFinPairStages) & 1);
                     if (!mbar_wait_cl(bar(EMPTY + s), ph ^ 1, abort_flag, peer_abort, p.err, 11)) { ok = false; break; }
                     mbar_expect_tx(bar(FULL + s), stage_bytes);
-                    for (int h = 0; h < 2; ++h) {
-                        const int kh = (int)k + h * kKC;
-                        if (p.blocked) tma_3d(smem_u32(stA(s, h)), &tmA, bar(FULL + s), 0, row0, kh >> 5);
-                        else tma_2d(smem_u32(stA(s, h)), &tmA, bar(FULL + s), kh, row0);
-                        if (p.unit_sys) {
-                            tma_3d(smem_u32(stBhi(s, h)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh, sys);
-                            tma_3d(smem_u32(stBlo(s, h)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh, sys);
-                        } else {
-                            tma_2d(smem_u32(stBhi(s, h)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh);
-                            tma_2d(smem_u32(stBlo(s, h)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh);
-                        }
+                    const int kh = (int)k;
+                    if (p.blocked) tma_3d(smem_u32(stA(s)), &tmA, bar(FULL + s), 0, row0, kh >> 5);
+                    else tma_2d(smem_u32(stA(s)), &tmA, bar(FULL + s), kh, row0);
+                    if (p.unit_sys) {
+                        tma_3d(smem_u32(stBhi(s)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh, sys);
+                        tma_3d(smem_u32(stBlo(s)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh, sys);
+                    } else {
+                        tma_2d(smem_u32(stBhi(s)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh);
+                        tma_2d(smem_u32(stBlo(s)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh);
                     }
                 }
             }
@@ -769,43 +947,43 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
         if (lane == 0 && rank == 0) {
             // ---------------- MMA issuer (even CTA, for the pair) ----------------
             const uint32_t id = idesc_tf32_pair(Np);
-            long long it = 0, sub_i = 0;
+            const int wk = p.KS / 8;  // K steps per window (KS divides the 32-wide chunk)
+            long long it = 0, w = 0;
             bool ok = true;
             for (long long item = cid; item < items && ok; item += ncl) {
                 const int ks = (int)(item / p.ngroups);
                 const long long k0 = (long long)ks * p.KW;
                 const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-                for (long long ksub = k0; ksub < k1 && ok; ksub += p.KS, ++sub_i) {
-                    const int ab = (int)(sub_i & 1);
-                    const uint32_t abph = (uint32_t)((sub_i >> 1) & 1);
-                    if (!mbar_wait_cl(bar(ACCE + ab), abph ^ 1, abort_flag, peer_abort, p.err, 12)) { ok = false; break; }
+                for (long long k = k0; k < k1 && ok; k += kFinKC, ++it) {
+                    const int s = (int)(it % kFinPairStages);
+                    const int slot = (int)(it % kFinSlots);
+                    const uint32_t sph = (uint32_t)((it / kFinSlots) & 1);
+                    if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 13)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t dacc = tmem + (uint32_t)(ab * 128);
-                    const long long kend = ksub + p.KS < k1 ? ksub + p.KS : k1;
-                    for (long long k = ksub; k < kend; k += kFinKC, ++it) {
-                        const int s = (int)(it % kFinPairStages);
-                        const int slot = (int)(it & 1);
-                        const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                        if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 13)) { ok = false; break; }
+                    // a 32-byte K step adds 2 to the descriptor's start field
+                    const unsigned long long dh = desc_sw128(smem_u32(stBhi(s)));
+                    const unsigned long long dl = desc_sw128(smem_u32(stBlo(s)));
+                    const uint32_t ahi = tmem + (uint32_t)(slot * 64), alo = ahi + 32u;
+                    for (int kw = 0; kw < 4; kw += wk, ++w) {
+                        const int b = (int)(w % kFinWindows);
+                        if (!mbar_wait_cl(bar(WE + b), (uint32_t)((w / kFinWindows) & 1) ^ 1u, abort_flag, peer_abort, p.err, 12)) { ok = false; break; }
                         tc_fence_after();
-                        // B boxes h = 0, 1 are bbytes apart: descriptor start field + (bbytes >> 4)
-                        const unsigned long long dh = desc_sw128(smem_u32(stBhi(s, 0)));
-                        const unsigned long long dl = desc_sw128(smem_u32(stBlo(s, 0)));
-                        const uint32_t ah0 = tmem + 256u + (uint32_t)(slot * 128);  // hi 64 cols, lo 64 cols
+                        const uint32_t dw = tmem + kFinWinCol + (uint32_t)b * AS;
+                        // correction products first (the window starts from zero) ...
 #pragma unroll 1
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const uint32_t ah = ah0 + kk * 8;
-                            const unsigned long long o =
-                                (unsigned long long)((kk >> 2) * (bbytes >> 4)) + 2ull * (kk & 3);
-                            mma_tf32_pair(dacc, ah, dh + o, id, (k == ksub && kk == 0) ? 0u : 1u);
-                            mma_tf32_pair(dacc, ah, dl + o, id, 1u);
-                            mma_tf32_pair(dacc, ah + 64, dh + o, id, 1u);
+                        for (int kk = kw; kk < kw + wk; ++kk) {
+                            mma_tf32_pair(dw, ahi + kk * 8, dl + 2ull * kk, id, kk == kw ? 0u : 1u);
+                            mma_tf32_pair(dw, alo + kk * 8, dh + 2ull * kk, id, 1u);
                         }
-                        mma_commit_pair(bar(TEMPTY + slot), (uint16_t)3);
-                        mma_commit_pair(bar(EMPTY + s), (uint16_t)3);
+                        // ... then hi*hi
+#pragma unroll 1
+                        for (int kk = kw; kk < kw + wk; ++kk)
+                            mma_tf32_pair(dw, ahi + kk * 8, dh + 2ull * kk, id, 1u);
+                        mma_commit_pair(bar(WF + b), (uint16_t)3);
                     }
                     if (!ok) break;
-                    mma_commit_pair(bar(ACCF + ab), (uint16_t)3);
+                    mma_commit_pair(bar(TEMPTY + slot), (uint16_t)3);
+                    mma_commit_pair(bar(EMPTY + s), (uint16_t)3);
                 }
             }
             // closing commit: no CTA leaves while an MMA reads its memory
@@ -817,7 +995,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
             while (!mbar_try(bar(DRAIN), 0) && gtimer() - g0 < kWaitLimitNs) {}
         }
     } else if (warp >= 4 && warp < 8) {
-        // ---------------- converter: A tile -> TF32 hi/lo in this CTA's TMEM ----------------
+        // ---------------- converter: A box -> TF32 hi / lo in this CTA's TMEM ----------------
         const int wq = warp & 3;
         const int r = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
@@ -831,70 +1009,89 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                 const int s = (int)(it % kFinPairStages);
                 const uint32_t ph = (uint32_t)((it / kFinPairStages) & 1);
                 if (!warp_wait_cl(bar(FULL + s), ph, abort_flag, peer_abort, p.err, 14)) { ok = false; break; }
-                uint32_t hi0[32], lo0[32], hi1[32], lo1[32];
-                load_split_row(stA(s, 0), r, hi0, lo0);
-                load_split_row(stA(s, 1), r, hi1, lo1);
+                uint32_t hi[32], lo[32];
+                load_split_row(stA(s), r, hi, lo);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(EMPTY + s));
-                const int slot = (int)(it & 1);
-                const uint32_t sph = (uint32_t)((it >> 1) & 1);
+                const int slot = (int)(it % kFinSlots);
+                const uint32_t sph = (uint32_t)((it / kFinSlots) & 1);
                 if (!warp_wait_cl(bar(TEMPTY + slot), sph ^ 1, abort_flag, peer_abort, p.err, 15)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t ta = lane_base + 256u + (uint32_t)(slot * 128);
-                tmem_st32(ta, hi0);
-                tmem_st32(ta + 32, hi1);
-                tmem_st32(ta + 64, lo0);
-                tmem_st32(ta + 96, lo1);
+                const uint32_t ta = lane_base + (uint32_t)(slot * 64);
+                tmem_st32(ta, hi);
+                tmem_st32(ta + 32, lo);
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive_cluster(bar0(TFULL + slot));
             }
         }
-    } else if (warp >= 8) {
-        // ---------------- epilogue: sum the buffers of an item, write its partial ----------------
-        const int wq = warp & 3;
+    } else if (epi >= 0) {
+        // ---------------- epilogue: Kahan sums of the drained windows, one partial per item ----------------
+        const int wq = warp & 3;  // == epi & 3
         const int rloc = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
-        const int nq = Np / 16;
-        long long sub_i = 0;
+        const int cw = Np / 2;                 // columns of this warp: [c0, c0 + cw)
+        const int c0 = (epi >> 2) * cw;
+        constexpr int kMaxC = kFinMaxNp / 2;   // 48
+        long long w = 0;
         bool ok = true;
         for (long long item = cid; item < items && ok; item += ncl) {
             const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
             const long long k0 = (long long)ks * p.KW;
             const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-            float acc[kFinMaxNp];
+            float sum[kMaxC], cmp[kMaxC];
 #pragma unroll
-            for (int j = 0; j < kFinMaxNp; ++j) acc[j] = 0.0f;
-            for (long long ksub = k0; ksub < k1; ksub += p.KS, ++sub_i) {
-                const int ab = (int)(sub_i & 1);
-                const uint32_t abph = (uint32_t)((sub_i >> 1) & 1);
-                if (!warp_wait_cl(bar(ACCF + ab), abph, abort_flag, peer_abort, p.err, 16)) { ok = false; break; }
+            for (int j = 0; j < kMaxC; ++j) sum[j] = cmp[j] = 0.0f;
+            for (long long kw = k0; kw < k1; kw += p.KS, ++w) {
+                const int b = (int)(w % kFinWindows);
+                if (!warp_wait_cl(bar(WF + b), (uint32_t)((w / kFinWindows) & 1), abort_flag, peer_abort, p.err, 16)) { ok = false; break; }
                 tc_fence_after();
+                const uint32_t col = lane_base + kFinWinCol + (uint32_t)b * AS + (uint32_t)c0;
+                // 16 columns per load while they last, then an 8-column tail
 #pragma unroll
-                for (int q = 0; q < kFinMaxNp / 16; ++q) {
-                    if (q < nq) {
+                for (int q = 0; q < kMaxC / 16; ++q) {
+                    if (q * 16 + 16 <= cw) {
                         uint32_t v[16];
-                        tmem_ld16(lane_base + (uint32_t)(ab * 128 + q * 16), v);
+                        tmem_ld16(col + (uint32_t)(q * 16), v);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[q * 16 + j] += __uint_as_float(v[j]);
+                        for (int j = 0; j < 16; ++j) {
+                            // Kahan: sum + cmp carries the exact running sum to ~2 ulp
+                            const float y = __uint_as_float(v[j]) - cmp[q * 16 + j];
+                            const float t = sum[q * 16 + j] + y;
+                            cmp[q * 16 + j] = (t - sum[q * 16 + j]) - y;
+                            sum[q * 16 + j] = t;
+                        }
+                    }
+                }
+                if (cw & 8) {
+                    uint32_t v[8];
+                    tmem_ld8(col + (uint32_t)(cw - 8), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+                        for (int q = 0; q < kMaxC / 8; ++q) {
+                            if (q * 8 == cw - 8) {
+                                const float y = __uint_as_float(v[j]) - cmp[q * 8 + j];
+                                const float t = sum[q * 8 + j] + y;
+                                cmp[q * 8 + j] = (t - sum[q * 8 + j]) - y;
+                                sum[q * 8 + j] = t;
+                            }
+                        }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(bar0(ACCE + ab));
+                if (lane == 0) mbar_arrive_cluster(bar0(WE + b));
             }
             if (!ok) break;
             float* base = p.part + (long long)ks * Np * p.Rld;
             const long long row = (long long)g * 2 * kBM + (long long)rank * kBM + rloc;
 #pragma unroll
-            for (int q = 0; q < kFinMaxNp / 16; ++q) {
-                if (q < nq) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) base[(long long)(q * 16 + j) * p.Rld + row] = acc[q * 16 + j];
-                }
-            }
+            for (int j = 0; j < kMaxC; ++j)
+                if (j < cw) base[(long long)(c0 + j) * p.Rld + row] = sum[j];
         }
     }
     tc_fence_before();
@@ -937,6 +1134,91 @@ __global__ void __cluster_dims__(2, 1, 1) k_wait_selftest(int* err, unsigned lon
     }
     __syncthreads();
     cluster_sync_all();  // no remote store is in flight when either CTA leaves
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-pipe rate probe (measurement of the roofline denominator): every
+// CTA pair runs a stream of back-to-back M = 256, N = 192, K = 8 kind::tf32
+// MMAs (A in tensor memory, B in shared memory, both zero), the shape and
+// operand placement of the stage kernels, with nothing else on the SM.  The
+// host times the launch with CUDA events; flops = pairs x iters x 4 x
+// 2 x 256 x 192 x 8.  One commit per 64 MMAs bounds the issue queue; the
+// closing commit keeps both CTAs resident until the last MMA is done.
+// ---------------------------------------------------------------------------
+constexpr int kRateN = 192;
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
+    k_mma_rate(int iters, int* err) {
+    __shared__ __align__(1024) uint8_t sB[(kRateN / 2) * 128];
+    __shared__ __align__(8) uint64_t bars[3];  // two alternating periodic commits, the closing one
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_s;
+    volatile int* abort_flag = &abort_s;
+    const uint32_t rank = cluster_rank();
+    const uint32_t peer_abort = mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < (kRateN / 2) * 32; i += blockDim.x)
+        reinterpret_cast<float*>(sB)[i] = 0.0f;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(smem_u32(&bars[b]), 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    // zero B (generic writes) must be visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 0) {
+        tmem_alloc_pair(smem_u32(&tmem_slot), 512);
+        tmem_relinquish_pair();
+        tc_fence_before();
+    }
+    __syncthreads();
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    {   // A (32 columns at 256) = 0 in this CTA's 128 lanes
+        uint32_t z[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) z[j] = 0u;
+        tmem_st32(tmem + ((uint32_t)(warp * 32) << 16) + 256u, z);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    tc_fence_after();
+    if (rank == 0 && threadIdx.x == 0) {
+        // one period = 16 iterations (64 MMAs), committed to bars[period & 1];
+        // before issuing period q + 1 wait for period q - 1, so one period is
+        // always queued behind the running one
+        const uint32_t id = idesc_tf32_pair(kRateN);
+        const unsigned long long db = desc_sw128(smem_u32(sB));
+        bool ok = true;
+        for (int i = 0; i < iters && ok; ++i) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_tf32_pair(tmem, tmem + 256u + kk * 8, db + 2ull * kk, id, (i | kk) ? 1u : 0u);
+            if ((i & 15) == 15) {
+                const int q = i >> 4;
+                mma_commit_pair(smem_u32(&bars[q & 1]), (uint16_t)3);
+                if (q >= 1)
+                    ok = mbar_wait_cl(smem_u32(&bars[(q - 1) & 1]), (uint32_t)(((q - 1) >> 1) & 1),
+                                      abort_flag, peer_abort, err, 95);
+            }
+        }
+        mma_commit_pair(smem_u32(&bars[2]), (uint16_t)3);
+        const unsigned long long g0 = gtimer();
+        while (!mbar_try(smem_u32(&bars[2]), 0) && gtimer() - g0 < kWaitLimitNs) {}
+    } else if (rank == 1 && threadIdx.x == 0) {
+        // the odd CTA receives the multicast commits too; it only waits for the closing one
+        const unsigned long long g0 = gtimer();
+        while (!mbar_try(smem_u32(&bars[2]), 0) && gtimer() - g0 < kWaitLimitNs) {}
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 512);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1068,11 +1350,10 @@ size_t stage_smem_bytes(int Np) {
     return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 512;
 }
 size_t final_pair_smem_bytes(int Np) {
-    return 1024 + (size_t)kFinPairStages * (2 * kTileBytes + 4 * (Np / 2) * 128) + 512;
+    return 1024 + (size_t)kFinPairStages * (kTileBytes + 2 * (Np / 2) * 128) + 512;
 }
-// K length of one S4 work item (one partial per item and row) for a TMEM
-// accumulation length kchunk.
-constexpr int kFinSubsPerItem = 8;
+// K length of one S4 work item (one FP32 partial per item and row); a
+// multiple of every hi*hi window length and of Np^3 for Np a multiple of 16.
 
 }  // namespace
 
@@ -1237,6 +1518,10 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     sp.out_unit = 2 * N4;
     sp.unit_sys = nullptr;
     sp.err = err;
+    // windowed accumulation where the ring fits next to the A slots (2 Np <= 96)
+    sp.as2 = ((2 * Np + 31) / 32) * 32;
+    sp.wsteps = 2 * Np <= 96 ? std::max(1, std::min(2, c->acc_window / 8)) : 0;
+    sp.nring = std::min(kStageRing, (512 - 128) / sp.as2);
     // S1: rows (j,m,q), cols (c,r) -> X1[j][r][m][c][q]
     sp.planes = 1;
     sp.a_unit = 0;
@@ -1281,8 +1566,8 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     FinalParams fp{};
     fp.Np = Np;
     fp.K = N3;
-    fp.KS = c->s4_kchunk;
-    fp.KW = kFinSubsPerItem * c->s4_kchunk;
+    fp.KS = c->acc_window;
+    fp.KW = kTcItemK;
     fp.nks = (int)((N3 + fp.KW - 1) / fp.KW);
     fp.rows = rows;
     fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
@@ -1324,9 +1609,46 @@ gkba_status wait_selftest(gkba_ctx* c, double limit_ms, double* elapsed_ms) {
     return GKBA_OK;
 }
 
+gkba_status measure_tf32_mma(gkba_ctx* c, int iters, double* tflops) {
+    // unused dynamic shared memory keeps one CTA (and one tensor-memory
+    // allocation) per SM, as in the stage kernels
+    const int pad = 150 * 1024;
+    GKBA_CUDA(c, cudaFuncSetAttribute(k_mma_rate, cudaFuncAttributeMaxDynamicSharedMemorySize, pad));
+    int ncl = 0;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(c->num_sms & ~1));
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = pad;
+        cfg.stream = c->stream;
+        GKBA_CUDA(c, cudaOccupancyMaxActiveClusters(&ncl, k_mma_rate, &cfg));
+    }
+    if (ncl < 1) return fail(c, GKBA_ECUDA, "no 2-CTA cluster of the rate probe fits");
+    const int pairs = std::min(ncl, c->num_sms / 2);
+    cudaEvent_t e0, e1;
+    GKBA_CUDA(c, cudaEventCreate(&e0));
+    GKBA_CUDA(c, cudaEventCreate(&e1));
+    k_mma_rate<<<2 * pairs, 128, pad, c->stream>>>(std::max(16, iters / 8), c->dint + 1);  // warm-up
+    cudaEventRecord(e0, c->stream);
+    k_mma_rate<<<2 * pairs, 128, pad, c->stream>>>(iters, c->dint + 1);
+    cudaEventRecord(e1, c->stream);
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t se = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (le != cudaSuccess || se != cudaSuccess)
+        return fail(c, GKBA_ECUDA, "rate probe: %s", cudaGetErrorString(le != cudaSuccess ? le : se));
+    const double flops = (double)pairs * iters * 4.0 * 2.0 * 256.0 * kRateN * 8.0;
+    *tflops = ms > 0.0f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+    return GKBA_OK;
+}
+
 size_t tf32_part_bytes(int Np, int ub, int kchunk) {
     const long long N3 = (long long)Np * Np * Np;
-    const long long kw = (long long)kFinSubsPerItem * kchunk;
+    (void)kchunk;
+    const long long kw = kTcItemK;
     const long long nks = (N3 + kw - 1) / kw;
     const long long rows = 2LL * Np * ub;
     const long long Rld = ((rows + 255) / 256) * 256;

@@ -34,7 +34,8 @@ EXPORTED = ["gkba_init", "gkba_sigma", "gkba_collision", "gkba_step", "gkba_set_
             "gkba_get_history", "gkba_get_state", "gkba_mean_field", "gkba_adjoint",
             "gkba_get_stats", "gkba_last_error", "gkba_destroy", "gkba_sigma_noalloc",
             "gkba_batch_create", "gkba_batch_step", "gkba_batch_last_error", "gkba_batch_destroy",
-            "gkba_selftest_timeout", "gkba_sigma3", "gkba_collision_vjp"]
+            "gkba_selftest_timeout", "gkba_sigma3", "gkba_collision_vjp",
+            "gkba_measure_tf32_mma"]
 
 
 class GKBAError(RuntimeError):
@@ -47,7 +48,7 @@ class Config(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dt", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
-                ("timing", ctypes.c_int), ("s4_kchunk", ctypes.c_int),
+                ("timing", ctypes.c_int), ("acc_window", ctypes.c_int),
                 ("interaction", ctypes.c_int), ("history", ctypes.c_int)]
 
 
@@ -87,6 +88,7 @@ def load():
     L.gkba_sigma_noalloc.argtypes = [I, I, P, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
     L.gkba_batch_create.argtypes = [ctypes.POINTER(P), P, I, ctypes.c_size_t]
     L.gkba_selftest_timeout.argtypes = [P, D, P]
+    L.gkba_measure_tf32_mma.argtypes = [P, I, P]
     L.gkba_sigma3.argtypes = [P, I, P, P, P, P, I]
     L.gkba_collision_vjp.argtypes = [P, I, P, P, P, P, P, P, P, I]
     L.gkba_batch_step.argtypes = [P, P, P, P, P]
@@ -132,7 +134,7 @@ class Context:
     """
 
     def __init__(self, h, v, d, rho0, dt, max_steps=0, precision="fp64", stream=None,
-                 workspace_bytes=0, device=-1, timing=False, s4_kchunk=0, interaction="general",
+                 workspace_bytes=0, device=-1, timing=False, acc_window=0, interaction="general",
                  history="sum"):
         L = load()
         on_dev = _is_torch(h)
@@ -152,7 +154,7 @@ class Context:
                 SPLIT_TF32: SPLIT_TF32, SPLIT_TF32_ACC: SPLIT_TF32_ACC}[precision]
         cfg = Config(N=N, dt=float(dt), max_steps=int(max_steps), precision=prec,
                      cuda_stream=stream, workspace_bytes=int(workspace_bytes), device=int(device),
-                     timing=1 if timing else 0, s4_kchunk=int(s4_kchunk), interaction=kind,
+                     timing=1 if timing else 0, acc_window=int(acc_window), interaction=kind,
                      history=_HISTORY[history])
         handle = ctypes.c_void_p()
         st = L.gkba_init(ctypes.byref(handle), ctypes.byref(cfg), ph[1], pv[1], pd[1], pr[1],
@@ -315,6 +317,13 @@ class Context:
         el = np.zeros(2, np.float64)
         st = load().gkba_selftest_timeout(self._h, float(limit_ms), el.ctypes.data)
         return st, el
+
+    def measure_tf32_mma(self, iters=100000):
+        """Tensor-pipe rate (TFLOP/s) of back-to-back kind::tf32 MMAs of the
+        stage kernels' shape on every SM pair (gkba_measure_tf32_mma)."""
+        out = np.zeros(1, np.float64)
+        self._check(load().gkba_measure_tf32_mma(self._h, int(iters), out.ctypes.data))
+        return float(out[0])
 
     def adjoint(self, rho_bar_final, want_v=False):
         """Gradients of L(rho(t_n)) w.r.t. the field samples E(t_0 .. t_n),

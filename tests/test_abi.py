@@ -55,7 +55,7 @@ def _init(lib, N=4, dt=0.05, prec=0, h=None, v=None, d=None, rho=None, interacti
     d = s["d"] if d is None else d
     rho = s["rho0"] if rho is None else rho
     cfg = gkba.Config(N=N, dt=dt, max_steps=1, precision=prec, cuda_stream=None,
-                      workspace_bytes=0, device=-1, timing=0, s4_kchunk=0,
+                      workspace_bytes=0, device=-1, timing=0, acc_window=0,
                       interaction=interaction, history=history)
     out = ctypes.c_void_p()
     arrs = [np.ascontiguousarray(x) for x in (h, v, d, rho)]

@@ -243,12 +243,14 @@ def test_config1_fp64_vs_oracle_100_steps(P, config1):
     ctx.close()
 
 
-# split-TF32 rho drifts systematically (the tensor core truncates accumulator
-# additions), so the error grows with the number of steps: the accurate mode
-# keeps it below 1e-5 over the first 100 steps of this configuration; the fast
-# mode's error is stated and bounded at 2.5e-5.
-@pytest.mark.parametrize("precision,bound", [("tf32acc", 1e-5), ("tf32", 2.5e-5)])
-def test_config1_tf32_vs_fp64_100_steps(P, config1, precision, bound):
+# The split-TF32 collision integral carries a coherent relative bias (the
+# tensor core truncates its FP32 accumulator additions toward zero), and the
+# correlated quench of this model amplifies a coherent bias of I about 30-fold
+# in rho over 1000 steps (random errors about 6-fold).  The kernels therefore
+# accumulate in short tensor-memory windows; the gate is the stated 1e-5 on rho
+# against the FP64 GPU path, for both split-TF32 modes.
+@pytest.mark.parametrize("precision", ["tf32", "tf32acc"])
+def test_config1_tf32_vs_fp64_100_steps(P, config1, precision):
     g, s, dt, E = config1
     n = 100
     c64 = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
@@ -257,38 +259,46 @@ def test_config1_tf32_vs_fp64_100_steps(P, config1, precision, bound):
     for k in range(n):
         r64, _, _ = c64.step(E[k], E[k + 1])
         rtc, _, _ = ctc.step(E[k], E[k + 1])
-        worst = max(worst, rel(rtc, r64))
+        worst = max(worst, check(rtc, r64, 1e-5, f"{precision} rho step {k + 1}"))
     print(f"config1 {n} steps: {precision} rho vs FP64 GPU path, max rel err {worst:.2e}")
-    assert worst < bound
     c64.close()
     ctc.close()
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision,trace_bound", [("tf32acc", 5e-5), ("tf32", 5e-4)])
-def test_config1_tf32_full_run_invariants(P, config1, precision, trace_bound):
-    # 1000 Heun steps (t in [0, 20]).  Particle number is conserved exactly by
-    # the method (Re Tr I = 0); on the split-TF32 paths its drift measures the
-    # systematic part of the contraction error (the tensor core truncates
-    # accumulator additions): measured 1.7e-5 (accurate mode) and 1.9e-4
-    # (fast mode) after 1000 steps, against 3e-14 on the FP64 path.  rho stays
+@pytest.mark.parametrize("precision", ["tf32", "tf32acc"])
+def test_config1_tf32_full_run_vs_fp64(P, config1, precision):
+    # The whole config-1 run: 1000 Heun steps (t in [0, 20], the pulse on
+    # [0, 10]); rho against the FP64 GPU path at every step, <= 1e-5.  The
+    # FP64 reference runs with the time-linear history, which equals the
+    # history sum up to rounding (checked against it over the first 100 steps
+    # here, and against the oracle in test_gpu_time_linear.py).  Particle
+    # number is conserved exactly by the method (Re Tr I = 0); rho stays
     # Hermitian and the correlation energy negative.
     g, s, dt, E = config1
     n = 1000
-    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=precision)
-    tr, ec, herm = [], [], 0.0
+    ref = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear")
+    h64 = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=100)
+    ctc = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=precision)
+    worst, tr, herm, ec = 0.0, [], 0.0, 0.0
     for k in range(n):
-        rho, I, diag = ctx.step(E[k], E[k + 1])
+        r64, _, _ = ref.step(E[k], E[k + 1])
+        if k < 100:
+            rh, _, _ = h64.step(E[k], E[k + 1])
+            check(r64, rh, 1e-11, f"time-linear vs history-sum FP64 step {k + 1}")
+        rtc, _, diag = ctc.step(E[k], E[k + 1])
+        worst = max(worst, check(rtc, r64, 1e-5, f"{precision} rho step {k + 1}"))
         tr.append(diag[0])
-        ec.append(diag[2])
-        herm = max(herm, np.abs(rho - rho.conj().T).max())
+        ec = diag[2]
+        herm = max(herm, np.abs(rtc - rtc.conj().T).max())
     tr = np.array(tr)
-    print(f"config1 1000 steps {precision}: |Tr rho - 6| {np.abs(tr - 6).max():.2e}, "
-          f"herm {herm:.2e}, E_c end {ec[-1]:.4e}")
-    assert np.abs(tr - 6.0).max() < trace_bound
+    print(f"config1 1000 steps {precision}: rho vs FP64 max rel err {worst:.2e}, "
+          f"|Tr rho - 6| {np.abs(tr - 6).max():.2e}, herm {herm:.2e}, E_c {ec:.4e}")
+    assert np.abs(tr - 6.0).max() < 5e-5
     assert herm < 1e-12
-    assert ec[-1] < 0.0
-    ctx.close()
+    assert ec < 0.0
+    for x in (ref, h64, ctc):
+        x.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "tf32acc"])
