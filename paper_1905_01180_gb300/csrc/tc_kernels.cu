@@ -179,21 +179,29 @@ __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols
 }
 // D[tmem] (+)= A[tmem] * B[smem desc] over the CTA pair: M = 256 (128 rows per
 // CTA's TMEM), B's N rows split in halves across the two CTAs' shared memory.
+// Called by all 32 lanes of a converged warp with warp-uniform operands: one
+// elected lane issues the instruction.  Issuing from a single divergent lane
+// instead halved the MMA rate at N = 96 (measured with gkba_measure_tf32_mma's
+// kernel): the operands then are per-thread values.
 __device__ __forceinline__ void mma_tf32_pair(uint32_t d, uint32_t a, unsigned long long bdesc,
                                               uint32_t idesc, uint32_t accumulate) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::2.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "@e tcgen05.mma.cta_group::2.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
         "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-// Arrive (once the issuing thread's earlier MMAs are done) on the mbarrier at
-// this shared offset in every CTA of `mask`.
+// Arrive (once the earlier MMAs issued by this warp are done) on the mbarrier
+// at this shared offset in every CTA of `mask`; warp-collective like
+// mma_tf32_pair.
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t mask) {
     asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
-        "[%0], %1;" ::"r"(bar),
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;\n\t}" ::"r"(bar),
         "h"(mask)
         : "memory");
 }
@@ -300,6 +308,22 @@ __device__ __forceinline__ void load_split_row(const uint8_t* tile, int r, uint3
 // ---------------------------------------------------------------------------
 // Stages S1-S3: resident per-unit B operand, persistent CTAs over (unit, tile).
 // ---------------------------------------------------------------------------
+// Position and phase bit of a ring of n barriers, advanced one entry at a
+// time: keeps divisions by ring sizes that are not powers of two (64-bit
+// integer division is a long software routine) out of the issue loops.
+struct Ring {
+    int i;
+    uint32_t ph;
+    int n;
+    __device__ explicit Ring(int n_) : i(0), ph(0u), n(n_) {}
+    __device__ __forceinline__ void next() {
+        if (++i == n) {
+            i = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
 struct StageParams {
     int Np;
     int planes;        // 1 for S1 (real A), 2 for S2/S3 (planar complex A)
@@ -479,20 +503,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0 && rank == 0) {
+        if (rank == 0) {
             // ---------------- MMA issuer (even CTA, for the pair) ----------------
             const uint32_t id = idesc_tf32_pair(2 * Np);
             const unsigned long long dBhi0 = desc_sw128(smem_u32(sBhi));
             const unsigned long long dBlo0 = desc_sw128(smem_u32(sBlo));
             int cur_u = -1;
             uint32_t bfph = 0;
-            long long it = 0, tile_i = 0, wcount = 0;
+            long long it = 0, tile_i = 0;
+            Ring wr(p.nring > 0 ? p.nring : 1);
             bool ok = true, issued = false;
             for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
                 const int u = (int)(t / ipu);
                 if (u != cur_u) {
-                    if (!mbar_wait_cl(bar(BFULL), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
-                    if (!mbar_wait_cl(bar(BPEER), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
+                    if (!warp_wait_cl(bar(BFULL), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
+                    if (!warp_wait_cl(bar(BPEER), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
                     bfph ^= 1;
                     cur_u = u;
                     tc_fence_after();
@@ -506,16 +531,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     for (int c = 0; c < nchunk && ok; ++c, ++it) {
                         const int slot = (int)(it & 1);
                         const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                        if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
+                        if (!warp_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t ahi = tmem + (slot ? slot_col1 : slot_col0);
                         const unsigned long long dh = dBhi0 + ((unsigned long long)(c * chunkB) >> 4);
                         const unsigned long long dl = dBlo0 + ((unsigned long long)(c * chunkB) >> 4);
                         const int ksteps = kc == p.kch - 1 ? ktail : 4;
                         if (++kc == p.kch) kc = 0;
-                        for (int kw = 0; kw < ksteps; kw += p.wsteps, ++wcount) {
-                            const int b = (int)(wcount % p.nring);
-                            if (!mbar_wait_cl(bar(WE + b), (uint32_t)((wcount / p.nring) & 1) ^ 1u, abort_flag, peer_abort, p.err, 19)) { ok = false; break; }
+                        for (int kw = 0; kw < ksteps; kw += p.wsteps, wr.next()) {
+                            const int b = wr.i;
+                            if (!warp_wait_cl(bar(WE + b), wr.ph ^ 1u, abort_flag, peer_abort, p.err, 19)) { ok = false; break; }
                             tc_fence_after();
                             const uint32_t dw = tmem + 128u + (uint32_t)(b * p.as2);
 #pragma unroll 1
@@ -538,7 +563,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 }
                 const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
                 const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
-                if (!mbar_wait_cl(bar(ACCE + ab), abph ^ 1, abort_flag, peer_abort, p.err, 4)) { ok = false; break; }
+                if (!warp_wait_cl(bar(ACCE + ab), abph ^ 1, abort_flag, peer_abort, p.err, 4)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dacc = tmem + (uint32_t)(ab * 256);
                 const uint32_t dcor = SPLIT_ACC ? tmem + 256u : dacc;
@@ -555,7 +580,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     int ksteps[2];
                     for (int c = 0; c < nchunk; ++c) {
                         const long long ic = it + c;
-                        if (!mbar_wait_cl(bar(TFULL + (int)(ic & 1)), (uint32_t)((ic >> 1) & 1), abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
+                        if (!warp_wait_cl(bar(TFULL + (int)(ic & 1)), (uint32_t)((ic >> 1) & 1), abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
                         ksteps[c] = (c % p.kch) == p.kch - 1 ? ktail : 4;
                     }
                     if (!ok) break;
@@ -590,7 +615,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 for (int c = 0; c < nchunk; ++c, ++it) {
                     const int slot = (int)(it & 1);
                     const uint32_t sph = (uint32_t)((it >> 1) & 1);
-                    if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
+                    if (!warp_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 5)) { ok = false; break; }
                     tc_fence_after();
                     // descriptor start field = address >> 4: a 32-byte K step adds 2
                     const uint32_t ahi = tmem + (slot ? slot_col1 : slot_col0);
@@ -674,7 +699,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
         const int rloc = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
         const int ncc = (2 * Np) / 32;
-        long long tile_i = 0, wc = 0;
+        long long tile_i = 0;
+        Ring wr(p.nring > 0 ? p.nring : 1);
         bool ok = true;
         for (long long t = t0; t < t1 && ok && win; ++t) {
             // windowed mode (2 Np <= 96): add the tile's windows in FP32 registers
@@ -682,9 +708,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             float acc[96];
 #pragma unroll
             for (int j = 0; j < 96; ++j) acc[j] = 0.0f;
-            for (int i = 0; i < win_per_tile; ++i, ++wc) {
-                const int b = (int)(wc % p.nring);
-                if (!warp_wait_cl(bar(WF + b), (uint32_t)((wc / p.nring) & 1), abort_flag, peer_abort, p.err, 20)) { ok = false; break; }
+            for (int i = 0; i < win_per_tile; ++i, wr.next()) {
+                const int b = wr.i;
+                if (!warp_wait_cl(bar(WF + b), wr.ph, abort_flag, peer_abort, p.err, 20)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
@@ -782,7 +808,7 @@ struct FinalParams {
     long long Rld;
     int* err;
     int blocked;   // A is K-blocked: [K/32][Rld rows][32] (3-D map) instead of [rows][K]
-    int KS;        // K length of one accumulation window in tensor memory: 8, 16 or 32
+    int KS;        // unused (the windows are the 32-wide chunks)
     const int* unit_sys;  // batches of several systems: unit -> system (3-D vK maps), else null
 };
 
@@ -794,8 +820,8 @@ constexpr int kFinThreads = 448;  // 14 warps: see the S4 kernel
 // Work item = (256-row group g: one 128-row tile per CTA, a K range of KW).
 // Per 32-wide K chunk each CTA stages its A box and its Np/2 rows of vK (hi
 // and lo) in one of eight pipeline stages; a converter warpgroup splits the A
-// box into TF32 hi and lo in the CTA's tensor memory; the even CTA issues
-// M = 256, N = Np MMAs for the pair.
+// box into TF32 hi and lo in the CTA's tensor memory; the MMA warp of the even
+// CTA issues M = 256, N = Np MMAs for the pair.
 //
 // Accuracy: the tensor core truncates its FP32 accumulator additions toward
 // zero.  Over the N^3-long sum of this stage that bias is not uniform: it
@@ -803,36 +829,43 @@ constexpr int kFinThreads = 448;  // 14 warps: see the S4 kernel
 // Sigma^< and Sigma^> units and breaks the exact cancellation behind
 // particle-number conservation (Re Tr I = 0); measured against the FP64
 // path it grows with the accumulation length roughly as its 1.8th power.
-// This stage therefore accumulates in tensor memory only over windows of KS
-// (8, 16 or 32) of K, each drained by the epilogue into FP32 register sums
-// with Kahan compensation (so the number of windows does not add rounding
-// error).  Inside a window the two correction products hi*lo + lo*hi (about
-// 2^-11 of the result) are issued first, while the accumulator is still
-// small, and the hi*hi products after them, so the only truncations at the
-// scale of the result are those of the KS / 8 hi*hi MMAs.  The window
-// accumulators rotate so the MMAs do not wait on the drains.
+// This stage therefore accumulates each 32-wide chunk in its own tensor-
+// memory window, drained by the epilogue into FP32 register sums with Kahan
+// compensation (so the number of windows adds no rounding error).  Inside a
+// window the two correction products hi*lo + lo*hi (about 2^-11 of the
+// result) are issued first, while the accumulator is still small, and the
+// hi*hi products after them, so the only truncations at the scale of the
+// result are those of the four hi*hi MMAs.
 //
 // Tensor memory (512 columns, same address in both CTAs): three A slots (hi
 // in 32 columns, lo in the next 32) at 0, 64 and 128, so the converter works
 // up to two chunks ahead of the MMAs; three window accumulators of AS = Np
-// rounded up to 32 columns at 192 + b AS.
+// rounded up to 32 columns at 192 + b AS.  Chunk c uses slot and window
+// c mod 3.
 //
-// Warps: 0 TMA producer, 1 MMA issuer (even CTA), 4-7 converter, and eight
-// epilogue warps, two per tensor-memory lane quarter (a warp reads only the
-// lanes of quarter warp % 4): 8-11 drain the first half of the Np columns,
-// 12, 13, 2, 3 the second half.
+// Warps: 0 TMA producer, 1 MMA issuer (even CTA; the whole warp, one elected
+// lane issues), 4-7 converter, and eight epilogue warps, two per tensor-
+// memory lane quarter (a warp reads only the lanes of quarter warp % 4), each
+// draining half of a window's Np columns: 8-11 the first half, 12, 13, 2, 3
+// the second.
 //
-// Barriers: FULL (TMA bytes) and EMPTY (4 converter warps read A + one
-// multicast commit of the MMAs that read B) per stage and CTA; TFULL (4
-// converter warps of each CTA arrive on the even CTA's barrier) and TEMPTY
-// per A slot; WF / WE (full / drained by 8 warps of each CTA) per window
-// accumulator.  Every wait is bounded.
+// Barriers (every wait is bounded):
+//   FULL[stage]  TMA bytes landed;
+//   EMPTY[stage] the stage may be refilled: the 4 converter warps arrive once
+//                the chunk's MMAs are done (they read A, the MMAs read B);
+//   TFULL[slot]  the slot's hi / lo are in tensor memory (4 converter warps of
+//                each CTA arrive on the even CTA's barrier);
+//   DONE[slot]   one multicast commit per chunk once its MMAs are done: the
+//                window is full (epilogue), the slot and the stage's B are free
+//                (converter);
+//   WE[slot]     the window was drained (8 epilogue warps of each CTA).
+// One commit per chunk: each tcgen05.commit costs the tensor pipe about 130
+// clocks (measured), a quarter of the chunk's MMA time.
 // ---------------------------------------------------------------------------
 constexpr int kFinPairStages = 8;
-constexpr int kFinKC = kKC;      // K per pipeline chunk: one 32-wide TMA box
+constexpr int kFinKC = kKC;      // K per pipeline chunk and window: one 32-wide TMA box
 constexpr int kFinMaxNp = 96;
-constexpr int kFinWindows = 3;   // window accumulators in tensor memory
-constexpr int kFinSlots = 3;     // A (hi, lo) slots in tensor memory
+constexpr int kFinSlots = 3;     // A (hi, lo) slots and window accumulators in tensor memory
 constexpr uint32_t kFinWinCol = 64u * kFinSlots;  // first window accumulator column
 constexpr int kFinEpiWarps = 8;
 
@@ -854,8 +887,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     const uint32_t stage_bytes = kTileBytes + 2 * bbytes;  // A, Bhi, Blo
     uint64_t* bars = (uint64_t*)(smem + kFinPairStages * stage_bytes);
     constexpr int FULL = 0, EMPTY = FULL + kFinPairStages, TFULL = EMPTY + kFinPairStages,
-                  TEMPTY = TFULL + kFinSlots, WF = TEMPTY + kFinSlots, WE = WF + kFinWindows,
-                  DRAIN = WE + kFinWindows, NBARS = DRAIN + 1;
+                  DONE = TFULL + kFinSlots, WE = DONE + kFinSlots, DRAIN = WE + kFinSlots,
+                  NBARS = DRAIN + 1;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     auto bar = [&](int i) { return smem_u32(bars + i); };
@@ -870,15 +903,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kFinPairStages; ++s) {
             mbar_init(bar(FULL + s), 1);
-            mbar_init(bar(EMPTY + s), 5);  // 4 converter warps + 1 multicast MMA commit
+            mbar_init(bar(EMPTY + s), 4);  // the 4 converter warps
         }
         for (int s = 0; s < kFinSlots; ++s) {
             mbar_init(bar(TFULL + s), 8);
-            mbar_init(bar(TEMPTY + s), 1);
-        }
-        for (int b = 0; b < kFinWindows; ++b) {
-            mbar_init(bar(WF + b), 1);
-            mbar_init(bar(WE + b), 2 * kFinEpiWarps);
+            mbar_init(bar(DONE + s), 1);
+            mbar_init(bar(WE + s), 2 * kFinEpiWarps);
         }
         mbar_init(bar(DRAIN), 1);
         *abort_flag = 0;
@@ -900,13 +930,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     const uint32_t tmem = *tmem_slot;
     const long long items = (long long)p.ngroups * p.nks;
     const long long ncl = cluster_count_x(), cid = cluster_id_x();
-    // epilogue role: warps 8-11 (first half of the columns), 12, 13, 2, 3 (second half)
+    // epilogue role e = 4 h + quarter: warps 8-11 (h = 0), 12, 13, 2, 3 (h = 1)
     const int epi = warp >= 8 ? warp - 8 : (warp == 2 || warp == 3) ? warp + 4 : -1;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer (both CTAs) ----------------
             long long it = 0;
+            Ring st(kFinPairStages);
             bool ok = true;
             for (long long item = cid; item < items && ok; item += ncl) {
                 const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
@@ -915,10 +946,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                 const int row0 = g * 2 * kBM + (int)rank * kBM;
                 // a 256-row group never straddles two systems (their units are padded)
                 const int sys = p.unit_sys ? p.unit_sys[(g * 2 * kBM) / (2 * Np)] : 0;
-                for (long long k = k0; k < k1; k += kFinKC, ++it) {
-                    const int s = (int)(it % kFinPairStages);
-                    const uint32_t ph = (uint32_t)((it / kFinPairStages) & 1);
-                    if (!mbar_wait_cl(bar(EMPTY + s), ph ^ 1, abort_flag, peer_abort, p.err, 11)) { ok = false; break; }
+                for (long long k = k0; k < k1; k += kFinKC, ++it, st.next()) {
+                    const int s = st.i;
+                    if (!mbar_wait_cl(bar(EMPTY + s), st.ph ^ 1, abort_flag, peer_abort, p.err, 11)) { ok = false; break; }
                     mbar_expect_tx(bar(FULL + s), stage_bytes);
                     const int kh = (int)k;
                     if (p.blocked) tma_3d(smem_u32(stA(s)), &tmA, bar(FULL + s), 0, row0, kh >> 5);
@@ -944,46 +974,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0 && rank == 0) {
-            // ---------------- MMA issuer (even CTA, for the pair) ----------------
+        if (rank == 0) {
+            // ---------------- MMA issuer (even CTA, for the pair; warp-collective) ----------------
             const uint32_t id = idesc_tf32_pair(Np);
-            const int wk = p.KS / 8;  // K steps per window (KS divides the 32-wide chunk)
-            long long it = 0, w = 0;
+            Ring st(kFinPairStages), sl(kFinSlots);
             bool ok = true;
             for (long long item = cid; item < items && ok; item += ncl) {
                 const int ks = (int)(item / p.ngroups);
                 const long long k0 = (long long)ks * p.KW;
                 const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-                for (long long k = k0; k < k1 && ok; k += kFinKC, ++it) {
-                    const int s = (int)(it % kFinPairStages);
-                    const int slot = (int)(it % kFinSlots);
-                    const uint32_t sph = (uint32_t)((it / kFinSlots) & 1);
-                    if (!mbar_wait_cl(bar(TFULL + slot), sph, abort_flag, peer_abort, p.err, 13)) { ok = false; break; }
+                for (long long k = k0; k < k1 && ok; k += kFinKC, st.next(), sl.next()) {
+                    const int s = st.i, j = sl.i;
+                    if (!warp_wait_cl(bar(TFULL + j), sl.ph, abort_flag, peer_abort, p.err, 13)) { ok = false; break; }
+                    if (!warp_wait_cl(bar(WE + j), sl.ph ^ 1u, abort_flag, peer_abort, p.err, 12)) { ok = false; break; }
                     tc_fence_after();
                     // a 32-byte K step adds 2 to the descriptor's start field
                     const unsigned long long dh = desc_sw128(smem_u32(stBhi(s)));
                     const unsigned long long dl = desc_sw128(smem_u32(stBlo(s)));
-                    const uint32_t ahi = tmem + (uint32_t)(slot * 64), alo = ahi + 32u;
-                    for (int kw = 0; kw < 4; kw += wk, ++w) {
-                        const int b = (int)(w % kFinWindows);
-                        if (!mbar_wait_cl(bar(WE + b), (uint32_t)((w / kFinWindows) & 1) ^ 1u, abort_flag, peer_abort, p.err, 12)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t dw = tmem + kFinWinCol + (uint32_t)b * AS;
-                        // correction products first (the window starts from zero) ...
-#pragma unroll 1
-                        for (int kk = kw; kk < kw + wk; ++kk) {
-                            mma_tf32_pair(dw, ahi + kk * 8, dl + 2ull * kk, id, kk == kw ? 0u : 1u);
-                            mma_tf32_pair(dw, alo + kk * 8, dh + 2ull * kk, id, 1u);
-                        }
-                        // ... then hi*hi
-#pragma unroll 1
-                        for (int kk = kw; kk < kw + wk; ++kk)
-                            mma_tf32_pair(dw, ahi + kk * 8, dh + 2ull * kk, id, 1u);
-                        mma_commit_pair(bar(WF + b), (uint16_t)3);
-                    }
-                    if (!ok) break;
-                    mma_commit_pair(bar(TEMPTY + slot), (uint16_t)3);
-                    mma_commit_pair(bar(EMPTY + s), (uint16_t)3);
+                    const uint32_t ahi = tmem + (uint32_t)(j * 64), alo = ahi + 32u;
+                    const uint32_t dw = tmem + kFinWinCol + (uint32_t)j * AS;
+                    // correction products first (the window starts from zero), then hi*hi
+                    mma_tf32_pair(dw, ahi, dl, id, 0u);
+                    mma_tf32_pair(dw, alo, dh, id, 1u);
+                    mma_tf32_pair(dw, ahi + 8, dl + 2, id, 1u);
+                    mma_tf32_pair(dw, alo + 8, dh + 2, id, 1u);
+                    mma_tf32_pair(dw, ahi + 16, dl + 4, id, 1u);
+                    mma_tf32_pair(dw, alo + 16, dh + 4, id, 1u);
+                    mma_tf32_pair(dw, ahi + 24, dl + 6, id, 1u);
+                    mma_tf32_pair(dw, alo + 24, dh + 6, id, 1u);
+                    mma_tf32_pair(dw, ahi, dh, id, 1u);
+                    mma_tf32_pair(dw, ahi + 8, dh + 2, id, 1u);
+                    mma_tf32_pair(dw, ahi + 16, dh + 4, id, 1u);
+                    mma_tf32_pair(dw, ahi + 24, dh + 6, id, 1u);
+                    mma_commit_pair(bar(DONE + j), (uint16_t)3);
                 }
             }
             // closing commit: no CTA leaves while an MMA reads its memory
@@ -996,36 +1019,54 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
         }
     } else if (warp >= 4 && warp < 8) {
         // ---------------- converter: A box -> TF32 hi / lo in this CTA's TMEM ----------------
+        // Software-pipelined: the tensor-memory stores of chunk c complete
+        // (tcgen05.wait::st, then TFULL) while chunk c + 1 is read and split,
+        // unless chunk c + 1 has not landed yet.  A chunk's stage is released
+        // (EMPTY) once its MMAs are done, observed when its slot is reused.
         const int wq = warp & 3;
         const int r = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+        Ring st(kFinPairStages), sl(kFinSlots), rel(kFinPairStages);
         long long it = 0;
         bool ok = true;
+        int pend = -1;  // slot whose stores were issued but not yet waited for
+        auto finish_pending = [&]() {
+            if (pend >= 0) {
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(bar0(TFULL + pend));
+                pend = -1;
+            }
+        };
         for (long long item = cid; item < items && ok; item += ncl) {
             const int ks = (int)(item / p.ngroups);
             const long long k0 = (long long)ks * p.KW;
             const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-            for (long long k = k0; k < k1; k += kFinKC, ++it) {
-                const int s = (int)(it % kFinPairStages);
-                const uint32_t ph = (uint32_t)((it / kFinPairStages) & 1);
-                if (!warp_wait_cl(bar(FULL + s), ph, abort_flag, peer_abort, p.err, 14)) { ok = false; break; }
+            for (long long k = k0; k < k1; k += kFinKC, ++it, st.next(), sl.next()) {
+                const int s = st.i;
+                if (pend >= 0 && !__all_sync(0xffffffffu, mbar_try(bar(FULL + s), st.ph))) finish_pending();
+                if (!warp_wait_cl(bar(FULL + s), st.ph, abort_flag, peer_abort, p.err, 14)) { ok = false; break; }
                 uint32_t hi[32], lo[32];
                 load_split_row(stA(s), r, hi, lo);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(bar(EMPTY + s));
-                const int slot = (int)(it % kFinSlots);
-                const uint32_t sph = (uint32_t)((it / kFinSlots) & 1);
-                if (!warp_wait_cl(bar(TEMPTY + slot), sph ^ 1, abort_flag, peer_abort, p.err, 15)) { ok = false; break; }
+                finish_pending();
+                const int j = sl.i;
+                // the slot (and chunk c - 3's stage) is free once chunk c - 3's MMAs are done
+                if (!warp_wait_cl(bar(DONE + j), sl.ph ^ 1, abort_flag, peer_abort, p.err, 15)) { ok = false; break; }
+                if (it >= kFinSlots) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(EMPTY + rel.i));
+                    rel.next();
+                }
                 tc_fence_after();
-                const uint32_t ta = lane_base + (uint32_t)(slot * 64);
+                const uint32_t ta = lane_base + (uint32_t)(j * 64);
                 tmem_st32(ta, hi);
                 tmem_st32(ta + 32, lo);
-                tmem_wait_st();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(bar0(TFULL + slot));
+                pend = j;
             }
         }
+        if (ok) finish_pending();
+        else tmem_wait_st();  // no store may be in flight when the CTA frees its tensor memory
     } else if (epi >= 0) {
         // ---------------- epilogue: Kahan sums of the drained windows, one partial per item ----------------
         const int wq = warp & 3;  // == epi & 3
@@ -1034,7 +1075,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
         const int cw = Np / 2;                 // columns of this warp: [c0, c0 + cw)
         const int c0 = (epi >> 2) * cw;
         constexpr int kMaxC = kFinMaxNp / 2;   // 48
-        long long w = 0;
+        Ring sl(kFinSlots);
         bool ok = true;
         for (long long item = cid; item < items && ok; item += ncl) {
             const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
@@ -1043,9 +1084,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
             float sum[kMaxC], cmp[kMaxC];
 #pragma unroll
             for (int j = 0; j < kMaxC; ++j) sum[j] = cmp[j] = 0.0f;
-            for (long long kw = k0; kw < k1; kw += p.KS, ++w) {
-                const int b = (int)(w % kFinWindows);
-                if (!warp_wait_cl(bar(WF + b), (uint32_t)((w / kFinWindows) & 1), abort_flag, peer_abort, p.err, 16)) { ok = false; break; }
+            for (long long kw = k0; kw < k1; kw += kFinKC, sl.next()) {
+                const int b = sl.i;
+                if (!warp_wait_cl(bar(DONE + b), sl.ph, abort_flag, peer_abort, p.err, 16)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t col = lane_base + kFinWinCol + (uint32_t)b * AS + (uint32_t)c0;
                 // 16 columns per load while they last, then an 8-column tail
@@ -1185,7 +1226,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
     __syncthreads();
     cluster_sync_all();
     tc_fence_after();
-    if (rank == 0 && threadIdx.x == 0) {
+    if (rank == 0 && warp == 0) {
         // one period = 16 iterations (64 MMAs), committed to bars[period & 1];
         // before issuing period q + 1 wait for period q - 1, so one period is
         // always queued behind the running one
@@ -1200,7 +1241,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
                 const int q = i >> 4;
                 mma_commit_pair(smem_u32(&bars[q & 1]), (uint16_t)3);
                 if (q >= 1)
-                    ok = mbar_wait_cl(smem_u32(&bars[(q - 1) & 1]), (uint32_t)(((q - 1) >> 1) & 1),
+                    ok = warp_wait_cl(smem_u32(&bars[(q - 1) & 1]), (uint32_t)(((q - 1) >> 1) & 1),
                                       abort_flag, peer_abort, err, 95);
             }
         }
