@@ -109,18 +109,19 @@ typedef struct {
     int device;        /* CUDA device ordinal (-1 = current device) */
     int timing;        /* nonzero: time every contraction kernel with CUDA events
                           (see gkba_get_stats) */
-    int acc_window;    /* split-TF32 modes: K length (8, 16 or 32; 0 = 32) of one
-                          tensor-memory accumulation window.  The tensor core
+    int acc_window;    /* split-TF32 modes: K length (8 or 16; 32 behaves as 16;
+                          0 = 32) of one tensor-memory accumulation window of the
+                          first three contractions for N <= 48.  The tensor core
                           truncates its FP32 accumulator additions toward zero, a
                           coherent bias that grows with the accumulation length,
-                          so the last contraction (K = N^3) and, for N <= 48,
-                          every contraction accumulate only that much of K in
-                          tensor memory before the epilogue adds the window in
-                          FP32 registers (Kahan-compensated in the last one);
+                          so those contractions (for N <= 48) and the last one
+                          (K = N^3, always 32-wide windows) accumulate only a
+                          window of K in tensor memory before the epilogue adds it
+                          in FP32 registers (Kahan-compensated in the last one);
                           inside a window the correction products come first and
                           hi*hi last, so only the hi*hi MMAs truncate at the scale
-                          of the result.  Shorter windows: smaller bias, more
-                          drains. */
+                          of the result.  For N > 48 the first three
+                          contractions accumulate a tile's whole K (96 or 192). */
     int interaction;   /* gkba_interaction: form of the v argument of gkba_init;
                           GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC need precision GKBA_FP64 */
     int history;       /* gkba_history: how gkba_step evaluates the history sum
