@@ -34,7 +34,9 @@ Beyond the paper: ``collision_vjp`` / ``collision_vjp_v`` (reverse-mode
 derivatives of the collision integral) and the time-linear form of the
 history sum (``collision_time_linear``, ``propagate_time_linear``), each
 pinned against the plain definitions above (finite differences, the history
-sum).
+sum).  ``oracle.stepper_grad`` (a submodule, imported on demand because it
+needs PyTorch) gives the gradients of the whole Heun trajectory by automatic
+differentiation of the same stepper, pinned by finite differences.
 """
 from __future__ import annotations
 
