@@ -64,6 +64,12 @@ def parse():
                     help="skip the stated-error leg (1000 config-1 steps against the FP64 path)")
     ap.add_argument("--precision", default="tf32", choices=["tf32", "tf32acc"],
                     help="split-TF32 mode of the timed step")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="gradients of the final dipole at N=32, 800 steps (adjoint run)")
+    ap.add_argument("--fd-samples", type=int, default=6,
+                    help="field samples checked by finite differences (--adjoint)")
+    ap.add_argument("--fd-dirs", type=int, default=32,
+                    help="Coulomb-factor directions checked by finite differences (--adjoint)")
     ap.add_argument("--batch", action="store_true",
                     help="time 32 systems of uneven N and L stacked in one batch vs one by one")
     ap.add_argument("--chains", action="store_true",
@@ -433,8 +439,89 @@ def run_batch_case(a, lo, hi):
                       "algorithmic_flops": flops}), flush=True)
 
 
+def dipole_fd_forward(P, s, dt, E, B=None):
+    """Final dipole Re Tr[d rho(t_n)] of an FP64 propagation with the history
+    sum kept as one N^4 accumulator (the same discrete trajectory as the
+    history-sum stepper up to rounding), for central finite differences."""
+    v = s["v"] if B is None else np.ascontiguousarray(np.einsum("pil,pjk->ijkl", B, B))
+    n = len(E) - 1
+    ctx = P.Context(s["h"], v, s["d"], s["rho0"], dt, max_steps=n, precision="fp64",
+                    history="time_linear")
+    for k in range(n):
+        rho, _, _ = ctx.step(E[k], E[k + 1])
+    ctx.close()
+    return float(np.real(np.trace(s["d"] @ rho)))
+
+
+def run_adjoint(a):
+    """Gradients of the final dipole L = Re Tr[d rho(T)] at N = 32 with 32
+    Coulomb factors, 800 Heun steps of dt = 0.025 under the pulse E(t) of the
+    seeded generator: dL/dE(t_k) for all 801 samples and dL/dB^P for the 32
+    factors, from the split-TF32 forward (history sum) and gkba_adjoint over
+    the recorded trajectory.  Checked by central finite differences (h = 1e-6)
+    of FP64 propagations (time-linear history) on a subset of the samples and
+    on one symmetric direction per factor."""
+    import torch
+    import gkba_inputs as gi
+    from paper_1905_01180_gb300 import build as b
+    b.build()
+    import paper_1905_01180_gb300 as P
+    from paper_1905_01180_gb300 import gkba
+    N, nP, n, dt = 32, 32, 800, 0.025
+    s = gi.system(N, nP, seed=0)
+    E = gi.field(np.arange(n + 1) * dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=a.precision)
+    for k in range(n):
+        rho, _, _ = ctx.step(E[k], E[k + 1])
+    t1 = time.perf_counter()
+    E_bar, rho0_bar, vb = ctx.adjoint(s["d"], want_v=True)
+    t2 = time.perf_counter()
+    ctx.close()
+    L = float(np.real(np.trace(s["d"] @ rho)))
+    B_bar = gkba.coulomb_factor_grad(s["B"], vb)
+    h = 1e-6
+    t3 = time.perf_counter()
+    L64 = dipole_fd_forward(P, s, dt, E)
+    fdE = {}
+    for k in [int(x) for x in np.linspace(0, 400, a.fd_samples)]:
+        Ep, Em = E.copy(), E.copy()
+        Ep[k] += h
+        Em[k] -= h
+        fdE[k] = (dipole_fd_forward(P, s, dt, Ep) - dipole_fd_forward(P, s, dt, Em)) / (2 * h)
+    rng = np.random.default_rng(3)
+    fdB = []
+    for Pf in range(min(nP, a.fd_dirs)):
+        X = rng.normal(size=(N, N))
+        D = np.zeros_like(s["B"])
+        D[Pf] = 0.5 * (X + X.T)
+        fd = (dipole_fd_forward(P, s, dt, E, s["B"] + h * D)
+              - dipole_fd_forward(P, s, dt, E, s["B"] - h * D)) / (2 * h)
+        fdB.append((Pf, float(np.sum(B_bar * D)), fd))
+    t4 = time.perf_counter()
+    errE = max(abs(E_bar[k] - f) for k, f in fdE.items()) / max(abs(f) for f in fdE.values())
+    errB = max(abs(ad - fd) for _, ad, fd in fdB) / max(abs(fd) for _, _, fd in fdB)
+    print(json.dumps({
+        "workload": f"gkba_adjoint_N{N}_nP{nP}_{n}_steps_dt{dt}",
+        "metric": "gradient of the final dipole w.r.t. all field samples and Coulomb factors",
+        "value": t2 - t0, "unit": "s", "higher_is_better": False,
+        "forward_s": t1 - t0, "adjoint_s": t2 - t1, "precision": a.precision,
+        "L_split_tf32": L, "L_fp64": L64, "L_rel_diff": abs(L - L64) / abs(L64),
+        "fd": {"h": h, "forward": "fp64, time-linear history", "seconds": t4 - t3,
+               "E_samples": {str(k): [float(E_bar[k]), f] for k, f in fdE.items()},
+               "E_max_rel_err": errE,
+               "B_directions": [[p_, ad, fd] for p_, ad, fd in fdB],
+               "B_max_rel_err": errB},
+        "E_bar_norm": float(np.linalg.norm(E_bar)), "B_bar_norm": float(np.linalg.norm(B_bar)),
+        "data": "synthetic (seeded generator, seed 0)"}), flush=True)
+
+
 def main():
     a = parse()
+    if a.adjoint:
+        run_adjoint(a)
+        return
     if a.batch:
         run_batch(a)
         return

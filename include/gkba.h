@@ -253,9 +253,12 @@ gkba_status gkba_mean_field(gkba_ctx* ctx, const double* rho, double* sigma_hf, 
  * Frechet derivative of the exponential (a 2N x 2N exponential).
  *   v_bar         N^4 doubles (host, may be NULL): dL/dv_abcd through every
  *                 collision integral and mean field of the trajectory (each
- *                 entry an independent real variable); FP64 contexts only.
- * GKBA_EUNSUPPORTED for a structured interaction, a trajectory started by
- * gkba_set_history(n > 0), or v_bar on a split-TF32 context.
+ *                 entry an independent real variable).  On a split-TF32
+ *                 context the two slot contractions read the FP32 X3 of the
+ *                 tensor-core chain (the w slot runs the chain once more on
+ *                 the omega layout of v) and sum in FP64.
+ * GKBA_EUNSUPPORTED for a structured interaction or a trajectory started by
+ * gkba_set_history(n > 0).
  */
 gkba_status gkba_adjoint(gkba_ctx* ctx, const double* rho_bar_final, double* E_bar, double* rho0_bar,
                          double* v_bar);
@@ -321,8 +324,8 @@ gkba_status gkba_sigma3(gkba_ctx* ctx, int n_units, const double* A, const doubl
  * otherwise).  Costs about four collision integrals.
  *   v_bar  N^4 doubles or NULL: dL/dv_abcd, every entry an independent real
  *          variable (chain it to a parametrization of v, e.g. Coulomb
- *          factors, on the caller's side); FP64 contexts only
- *          (GKBA_EUNSUPPORTED otherwise); two more chains per unit.
+ *          factors, on the caller's side); one more chain (S1-S3) and
+ *          two slot contractions per unit, on either precision path.
  */
 gkba_status gkba_collision_vjp(gkba_ctx* ctx, int L, const double* rho_hist, const double* T_hist,
                                const double* weights, const double* I_bar, double* rho_bar,

@@ -302,7 +302,16 @@ gkba_status collision_vjp_dev(gkba_ctx* c, int L, const double2* rho, const doub
         GKBA_TRY(scale_units(c, nb, c->coef, Ibar, tC));  // Ybar
         GKBA_TRY(zgemm_batched(c, K_RED, N, 'N', 'C', one, tC, NN, Gbv, NN, zero, Sbv, NN, nb, 0));
         GKBA_TRY(zgemm_batched(c, K_RED, N, 'C', 'N', one, Sv, NN, tC, NN, zero, Gbb, NN, nb, 0));
-        if (vslot) {
+        if (vslot && tensor_core_path(c)) {
+            // dL/dv (tensor cores): the v slot against the X3 of S above, still in
+            // X13; the w slot against the chain run on the omega layout of v
+            GKBA_TRY(vbar_slot_tf32(c, nb, Sbv, 0, vslot));
+            GKBA_TRY(unit_xform(c, nb, Gv, tA, 0, 1));
+            GKBA_TRY(unit_xform(c, nb, Gbv, tB, 0, 1));
+            GKBA_TRY(build_forms(c, nb, tA, NN, tB, NN, 0));
+            GKBA_TRY(tf32_chain_omega(c, nb));
+            GKBA_TRY(vbar_slot_tf32(c, nb, Sbv, 1, wslot));
+        } else if (vslot) {
             // dL/dv (FP64 path): the v slot against X3 = W3 still in X13 from S above
             GKBA_TRY(vbar_slot(c, nb, Sbv, 0, (const double*)c->X13, vslot));
             // the w slot against the same chain run on v in the omega layout with G^T, Gb^T
@@ -416,7 +425,7 @@ void free_ctx(gkba_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->tl_acc, c->tl_s, c->tl_W, c->tl_Wn, c->tl_uf,
                     c->h, c->d, c->v, c->vm, c->vjp, c->rhot_hist, c->U_hist, c->adj_ws, c->vomega,
-                    c->vgrad, c->hfK, c->wS64, c->vK64, c->wS32, c->vKhi, c->vKlo,
+                    c->vgrad, c->hfK, c->wS64, c->vK64, c->wS32, c->vO32, c->vKhi, c->vKlo,
                     c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
                     c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
                     c->stage};
@@ -734,13 +743,14 @@ gkba_status gkba_collision(gkba_ctx* c, int L, const double* rho_hist, const dou
     return finish(c);
 }
 
-// Buffers of dL/dv (FP64 path): the omega layout of v and three accumulators
-// (v slot N x N^3, w slot N x N^3, natural N^4), zeroed.
+// Buffers of dL/dv: the omega layout of v (FP64, or FP32 padded to Np on the
+// tensor-core path) and three FP64 accumulators (v slot N x N^3, w slot
+// N x N^3, natural N^4), zeroed.
 static gkba_status prepare_vgrad(gkba_ctx* c) {
-    if (c->prec != GKBA_FP64)
-        return fail(c, GKBA_EUNSUPPORTED, "dL/dv is computed on the FP64 path only");
     const size_t N4 = (size_t)c->N * c->N * c->N * c->N;
-    if (!c->vomega) {
+    if (tensor_core_path(c)) {
+        GKBA_TRY(tf32_prepare_vgrad(c));
+    } else if (!c->vomega) {
         GKBA_TRY(alloc(c, (void**)&c->vomega, N4 * 8));
         GKBA_TRY(build_vomega64(c, c->vomega));
     }

@@ -85,6 +85,7 @@ struct gkba_ctx {
 
     // split-TF32 contraction operands (padded Np, zero padding)
     float* wS32 = nullptr;    // raw FP32 [j][m][q][s]
+    float* vO32 = nullptr;    // omega layout of v, FP32 [i][n][p][r] (dL/dv, made on demand)
     float* vKhi = nullptr;    // TF32-rounded [i][(n,r,p)]
     float* vKlo = nullptr;    // TF32-rounded remainder
 
@@ -257,6 +258,9 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb);
 // Structured interaction (GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC): S(G_u, Gb_u) into Su.
 gkba_status contract_structured(gkba_ctx* c, int nb, const double2* G, const double2* Gb);
 gkba_status tf32_prepare_model(gkba_ctx* c);  // build wS32, vKhi, vKlo
+gkba_status tf32_prepare_vgrad(gkba_ctx* c);  // build vO32
+gkba_status tf32_chain_omega(gkba_ctx* c, int nb);
+gkba_status vbar_slot_tf32(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, double* out);
 gkba_status fp64_prepare_model(gkba_ctx* c);  // build wS64, vK64, hfK
 
 // Per-unit operand forms for a batch: units u = 0..nb-1 given (G_u, Gb_u) pointers

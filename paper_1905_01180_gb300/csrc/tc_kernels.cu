@@ -1305,6 +1305,105 @@ __global__ void k_build_vK32(int N, int Np, const double* __restrict__ v, float*
     lo[e] = l;
 }
 
+// Omega layout of v for the w-slot chain of dL/dv: vO[i][n][p][r] = v_irpn
+// (zero in the padding); it takes wS32's place as stage S1's A operand.
+__global__ void k_build_vO32(int N, int Np, const double* __restrict__ v, float* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long Np4 = (long long)Np * Np * Np * Np;
+    if (e >= Np4) return;
+    const int r = (int)(e % Np), pp = (int)((e / Np) % Np), n = (int)((e / Np / Np) % Np),
+              i = (int)(e / Np / Np / Np);
+    float x = 0.0f;
+    if (r < N && pp < N && n < N && i < N) {
+        const long long NN = N;
+        x = (float)v[((i * NN + r) * NN + pp) * NN + n];
+    }
+    out[e] = x;
+}
+
+// One slot of dL/dv on the tensor-core path, from the X3 that stages S1-S3
+// left in X13 (rows (u, c, b) = (2u + c) Np + b, K = (n, r, p)):
+//   out[a][(n,r,p)] += sum_{u, c, b < N} S_c(u, a, b) X3[(u,c,b)][(n,r,p)]
+// with S_c the real (c = 0) / imaginary (c = 1) part of Sbar_u[a][b], or of
+// Sbar_u[b][a] when transposeS (out = Re sum conj(Sbar) X3 over b).  A thread
+// owns one K (in the N basis) and kVbA consecutive a; the rows are split over
+// blockIdx.z.  Products and short runs are FP32 (X3 is FP32), every kVbFlush
+// rows the run is added into an FP64 sum, and the block's sums go to out by
+// FP64 atomics.
+constexpr int kVbA = 32;       // a per thread (blockIdx.y picks the range)
+constexpr int kVbRows = 64;    // rows of S staged in shared memory at a time
+constexpr int kVbFlush = 256;  // FP32 run length before the FP64 sum
+constexpr int kVbThreads = 128;
+__global__ void __launch_bounds__(kVbThreads) k_vbar_slot_tc(int N, int Np, int nb, long long Rld,
+                                                             int blocked, long long rows_per_z,
+                                                             const double2* __restrict__ Sbar,
+                                                             int transposeS, const float* __restrict__ X,
+                                                             double* __restrict__ out) {
+    __shared__ float sS[kVbRows][kVbA];
+    const long long NN = (long long)N * N, N3 = NN * N;
+    const long long Np3 = (long long)Np * Np * Np;
+    const long long KN = (long long)blockIdx.x * kVbThreads + threadIdx.x;
+    const bool kok = KN < N3;
+    const long long n = KN / NN, r = (KN / N) % N, p = KN % N;
+    const long long K = (n * Np + r) * Np + p;
+    const float* xk = blocked ? X + (K >> 5) * Rld * 32 + (K & 31) : X + K;
+    const long long xstride = blocked ? 32 : Np3;  // per X3 row
+    const int a0 = blockIdx.y * kVbA;
+    const long long Rtot = 2LL * N * nb;  // compact rows (u, c, b < N)
+    const long long R0 = (long long)blockIdx.z * rows_per_z;
+    const long long R1 = R0 + rows_per_z < Rtot ? R0 + rows_per_z : Rtot;
+    float acc[kVbA];
+    double sum[kVbA];
+#pragma unroll
+    for (int t = 0; t < kVbA; ++t) {
+        acc[t] = 0.0f;
+        sum[t] = 0.0;
+    }
+    int run = 0;
+    for (long long rs = R0; rs < R1; rs += kVbRows) {
+        const int nrow = (int)(R1 - rs < kVbRows ? R1 - rs : kVbRows);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kVbRows * kVbA; e += kVbThreads) {
+            const int rr = e / kVbA, aa = e % kVbA, a = a0 + aa;
+            float val = 0.0f;
+            if (rr < nrow && a < N) {
+                const long long Rc = rs + rr, uc = Rc / N;
+                const int b = (int)(Rc % N), u = (int)(uc >> 1), cc = (int)(uc & 1);
+                const double2 s = transposeS ? Sbar[u * NN + (long long)b * N + a]
+                                             : Sbar[u * NN + (long long)a * N + b];
+                val = (float)(cc ? s.y : s.x);
+            }
+            sS[rr][aa] = val;
+        }
+        __syncthreads();
+        if (kok) {
+            long long uc = rs / N;
+            int b = (int)(rs % N);
+            for (int rr = 0; rr < nrow; ++rr) {
+                const float x = xk[(uc * Np + b) * xstride];
+#pragma unroll
+                for (int t = 0; t < kVbA; ++t) acc[t] = fmaf(sS[rr][t], x, acc[t]);
+                if (++b == N) {
+                    b = 0;
+                    ++uc;
+                }
+                if (++run == kVbFlush) {
+                    run = 0;
+#pragma unroll
+                    for (int t = 0; t < kVbA; ++t) {
+                        sum[t] += (double)acc[t];
+                        acc[t] = 0.0f;
+                    }
+                }
+            }
+        }
+    }
+    if (!kok) return;
+#pragma unroll
+    for (int t = 0; t < kVbA; ++t)
+        if (a0 + t < N) atomicAdd(out + (long long)(a0 + t) * N3 + KN, sum[t] + (double)acc[t]);
+}
+
 // Per-unit B operands of the tensor-core path (padded to Np, zero padding),
 // stored as TF32 hi then lo blocks of ub units:
 //   B1[u][(c,r)][s] = Gb_c[s][r]                                   (S1)
@@ -1464,8 +1563,10 @@ gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG, con
     return build_forms_fp64(c, nb, G, Gb);
 }
 
-// Tensor-core contraction of one batch (forms built): S_u -> c->Su.
-gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
+// Stages S1-S3 of one batch (forms built) with A1 as S1's A operand (wS32,
+// or the omega layout of v for dL/dv): X3 lands in X13, K-blocked when
+// Np % 32 == 0.  With do_final, stage S4 and the reduction follow: S_u -> c->Su.
+static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_final) {
     const int Np = c->Np;
     const long long N2 = (long long)Np * Np, N3 = N2 * Np, N4 = N3 * Np;
     const int kch = (Np + kKC - 1) / kKC;
@@ -1491,12 +1592,12 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)N3, (cuuint64_t)c->nsys};
         cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)(N4 * 4)};
         cuuint32_t b[3] = {kKC, kBM, 1};
-        GKBA_TRY(make_map(c, &mA1, c->wS32, 3, d, s, b));
+        GKBA_TRY(make_map(c, &mA1, A1, 3, d, s, b));
     } else {
         cuuint64_t d[2] = {(cuuint64_t)Np, (cuuint64_t)N3};
         cuuint64_t s[1] = {(cuuint64_t)Np * 4};
         cuuint32_t b[2] = {kKC, kBM};
-        GKBA_TRY(make_map(c, &mA1, c->wS32, 2, d, s, b));
+        GKBA_TRY(make_map(c, &mA1, A1, 2, d, s, b));
     }
     {
         cuuint64_t d[4] = {(cuuint64_t)Np, 2, (cuuint64_t)N3, (cuuint64_t)nb};
@@ -1591,6 +1692,8 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     const long long rows = 2LL * Np * nb;
     const long long Rld = ((rows + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
     const bool blocked = (Np % 32) == 0;
+    if (blocked && (size_t)(N3 * Rld * 4) > c->x13_bytes)
+        return fail(c, GKBA_ESTATE, "X3 buffer too small for the K-blocked layout");
     sp.out = X13;
     if (blocked) {
         sp.map = StageMap{32, Np * Rld, 0, 32 * Np, N2 * Rld, Np, Np, Np, 32 * Rld};
@@ -1603,6 +1706,7 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in2, mG3h, mG3l, sp);
         GKBA_TRY(launch_end(c, t));
     }
+    if (!do_final) return GKBA_OK;
     // S4: split-K over (n,r,p)
     FinalParams fp{};
     fp.Np = Np;
@@ -1617,8 +1721,6 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
     fp.part = (float*)c->part;
     fp.err = err;
     fp.unit_sys = c->unit_sys;
-    if (blocked && (size_t)(N3 * Rld * 4) > c->x13_bytes)
-        return fail(c, GKBA_ESTATE, "X3 buffer too small for the K-blocked layout");
     if ((size_t)fp.nks * Np * fp.Rld * 4 > c->part_bytes)
         return fail(c, GKBA_ESTATE, "partial buffer too small");
     {
@@ -1629,6 +1731,44 @@ gkba_status contract_batch_tf32(gkba_ctx* c, int nb) {
         GKBA_TRY(launch_end(c, t));
     }
     return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
+}
+
+// Tensor-core contraction of one batch (forms built): S_u -> c->Su.
+gkba_status contract_batch_tf32(gkba_ctx* c, int nb) { return tf32_chain(c, nb, c->wS32, true); }
+
+// dL/dv on the tensor-core path: the omega layout of v (once per context).
+gkba_status tf32_prepare_vgrad(gkba_ctx* c) {
+    if (c->vO32) return GKBA_OK;
+    const long long Np4 = (long long)c->Np * c->Np * c->Np * c->Np;
+    if (cudaMalloc(&c->vO32, Np4 * 4) != cudaSuccess) {
+        cudaGetLastError();
+        c->vO32 = nullptr;
+        return fail(c, GKBA_ENOMEM, "omega layout of v (%lld floats) does not fit", Np4);
+    }
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_build_vO32<<<grid1(Np4, 256), 256, 0, c->stream>>>(c->N, c->Np, c->v, c->vO32);
+    return launch_end(c, t);
+}
+
+// X3 of the w-slot chain: stages S1-S3 with the omega layout of v (forms built).
+gkba_status tf32_chain_omega(gkba_ctx* c, int nb) { return tf32_chain(c, nb, c->vO32, false); }
+
+gkba_status vbar_slot_tf32(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, double* out) {
+    const int N = c->N, Np = c->Np;
+    const long long N3 = (long long)N * N * N;
+    const long long rows = 2LL * Np * nb;
+    const long long Rld = ((rows + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
+    const long long Rtot = 2LL * N * nb;
+    const unsigned gx = grid1(N3, kVbThreads), gy = (unsigned)((N + kVbA - 1) / kVbA);
+    // enough blocks for about eight per SM, each over at least 1024 rows
+    long long gz = std::max(1LL, std::min((Rtot + 1023) / 1024,
+                                          (8LL * c->num_sms + gx * gy - 1) / ((long long)gx * gy)));
+    const long long per = ((Rtot + gz - 1) / gz + kVbRows - 1) / kVbRows * kVbRows;
+    gz = (Rtot + per - 1) / per;
+    auto t = launch_begin(c, K_RED, 4.0 * (double)N3 * N * Rtot, 4.0 * (double)Rtot * N3);
+    k_vbar_slot_tc<<<dim3(gx, gy, (unsigned)gz), kVbThreads, 0, c->stream>>>(
+        N, Np, nb, Rld, (Np % 32) == 0 ? 1 : 0, per, Sbar, transposeS, (const float*)c->X13, out);
+    return launch_end(c, t);
 }
 
 gkba_status wait_selftest(gkba_ctx* c, double limit_ms, double* elapsed_ms) {

@@ -327,7 +327,7 @@ class Context:
 
     def adjoint(self, rho_bar_final, want_v=False):
         """Gradients of L(rho(t_n)) w.r.t. the field samples E(t_0 .. t_n),
-        rho(t_0) [and v, FP64 contexts] through the steps taken since
+        rho(t_0) [and v] through the steps taken since
         gkba_init; rho_bar_final = dL/dRe rho(t_n) + i dL/dIm rho(t_n).
         Returns (E_bar, rho0_bar[, v_bar])."""
         rb, rbp = _host(rho_bar_final, np.complex128)

@@ -109,12 +109,22 @@ def test_collision_vjp_v_vs_oracle(P):
     check(tb, tr, 1e-10, "T_bar")
 
 
-def test_v_gradient_needs_fp64(P):
-    N = 4
-    s = gi.system(N, 4, seed=1)
-    rho, T = gi.history(N, 2, 0.02, seed=2)
-    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.02, precision="tf32")
-    with pytest.raises(P.GKBAError) as ei:
-        ctx.collision_vjp(rho, T, np.eye(N, dtype=complex), want_v=True)
-    assert ei.value.status == P.gkba.EUNSUPPORTED
+@pytest.mark.parametrize("N", [5, 32, 40])
+@pytest.mark.parametrize("precision", ["tf32", "tf32acc"])
+def test_collision_vjp_v_split_tf32_vs_oracle(P, N, precision):
+    # dL/dv on the tensor-core path: the v slot reads the chain's FP32 X3, the
+    # w slot runs the chain on the omega layout of v.  N = 5 and 40 pad to
+    # Np = 16 and 48 (row-major X3), N = 32 is the K-blocked X3 layout.
+    L = 3
+    s = gi.system(N, 8, seed=16)
+    rho, T = gi.history(N, L, 0.02, seed=17)
+    Ibar = cplx(np.random.default_rng(18), N, N)
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], 0.02, precision=precision)
+    rb, tb, vb = ctx.collision_vjp(rho, T, Ibar, want_v=True)
     ctx.close()
+    ref = O.collision_vjp_v(s["v"], rho, T, O.trapezoid_weights(L, 0.02), Ibar)
+    e = check(vb, ref, 2e-5, f"v_bar N={N} {precision}")
+    print(f"N={N} L={L} {precision} collision dL/dv rel err {e:.2e}")
+    rr, tr = O.collision_vjp(s["v"], rho, T, O.trapezoid_weights(L, 0.02), Ibar)
+    check(rb, rr, 2e-5, "rho_bar")
+    check(tb, tr, 2e-5, "T_bar")
