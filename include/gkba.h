@@ -93,8 +93,12 @@ typedef enum {
     GKBA_HISTORY_TIME_LINEAR = 1 /* gkba_step keeps the history sum as one N^4 accumulator
                                     (T(t_n,t_k) = Ucal_n Ucal_k^+ factored out; an extension,
                                     not in the paper): O(N^5) per step at any history
-                                    length, the same result up to rounding.  FP64 and a
-                                    general v only; 2 x 16 N^4 bytes more device memory */
+                                    length, the same result up to rounding.  General v
+                                    only; 2 x 16 N^4 bytes more device memory.  On a
+                                    split-TF32 context the contractions (terms, their
+                                    accumulation over j, the three back-transforms and
+                                    stage S4) run on the tensor cores and the
+                                    accumulator stays FP64 */
 } gkba_history;
 
 typedef struct {
@@ -125,8 +129,8 @@ typedef struct {
     int interaction;   /* gkba_interaction: form of the v argument of gkba_init;
                           GKBA_V_DIAGONAL / GKBA_V_SYMMETRIC need precision GKBA_FP64 */
     int history;       /* gkba_history: how gkba_step evaluates the history sum
-                          (GKBA_HISTORY_TIME_LINEAR needs GKBA_FP64 and
-                          GKBA_V_GENERAL, else GKBA_EUNSUPPORTED) */
+                          (GKBA_HISTORY_TIME_LINEAR needs GKBA_V_GENERAL, else
+                          GKBA_EUNSUPPORTED) */
 } gkba_config;
 
 /* Per-kernel-class counters (see gkba_get_stats). */

@@ -475,10 +475,9 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
                     cfg->precision);
     if (cfg->history != GKBA_HISTORY_SUM && cfg->history != GKBA_HISTORY_TIME_LINEAR)
         return fail(nullptr, GKBA_EINVAL, "gkba_init: unknown history mode %d", cfg->history);
-    if (cfg->history == GKBA_HISTORY_TIME_LINEAR &&
-        (cfg->precision != GKBA_FP64 || kind != GKBA_V_GENERAL))
+    if (cfg->history == GKBA_HISTORY_TIME_LINEAR && kind != GKBA_V_GENERAL)
         return fail(nullptr, GKBA_EUNSUPPORTED,
-                    "gkba_init: the time-linear history runs on the FP64 path with a general v");
+                    "gkba_init: the time-linear history needs a general v");
     const int Np = ((N + 15) / 16) * 16;
     if (cfg->precision != GKBA_FP64 && Np > 96)
         return fail(nullptr, GKBA_EINVAL,
@@ -637,6 +636,12 @@ gkba_status gkba_init(gkba_ctx** out, const gkba_config* cfg, const double* h, c
         ALLOC(c->wS32, Np4 * 4);
         ALLOC(c->vKhi, Np4 * 4);
         ALLOC(c->vKlo, Np4 * 4);
+        if (c->history == GKBA_HISTORY_TIME_LINEAR) {
+            ALLOC(c->tl_acc, 2 * N4 * 8);
+            ALLOC(c->tl_s, 2 * N4 * 8);
+            ALLOC(c->tl_W, NN * 16);
+            ALLOC(c->tl_Wn, NN * 16);
+        }
     }
 #undef ALLOC
     if (cudaMallocHost((void**)&c->hdiag, 16 * 8) != cudaSuccess) {

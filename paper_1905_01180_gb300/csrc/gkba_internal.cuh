@@ -261,6 +261,9 @@ gkba_status tf32_prepare_model(gkba_ctx* c);  // build wS32, vKhi, vKlo
 gkba_status tf32_prepare_vgrad(gkba_ctx* c);  // build vO32
 gkba_status tf32_chain_omega(gkba_ctx* c, int nb);
 gkba_status vbar_slot_tf32(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, double* out);
+gkba_status tl_terms_tf32(gkba_ctx* c, int nb, const double2* Gb, int k0, double w_first,
+                          double w_rest, double* D);
+gkba_status tl_apply_tf32(gkba_ctx* c, const double2* W, const double* lam);
 gkba_status fp64_prepare_model(gkba_ctx* c);  // build wS64, vK64, hfK
 
 // Per-unit operand forms for a batch: units u = 0..nb-1 given (G_u, Gb_u) pointers

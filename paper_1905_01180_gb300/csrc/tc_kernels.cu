@@ -342,6 +342,16 @@ struct StageParams {
     int as2;           // windowed: ring stride in columns (2 Np rounded up to 32)
 };
 
+// Output address of row `row` of unit u through the stage's map (rows below
+// 2^31: 32-bit unsigned division).
+__device__ __forceinline__ float* stage_out_row(const StageParams& p, int u, uint32_t row) {
+    const uint32_t Dx = (uint32_t)p.map.Dx, Db = (uint32_t)p.map.Db;
+    const uint32_t x = row % Dx, rb = row / Dx;
+    const long long xo = p.map.XB ? (long long)(x >> 5) * p.map.XB + (x & 31) : (long long)x * p.map.SX;
+    return p.out + (long long)u * p.out_unit + (long long)(rb / Db) * p.map.SA +
+           (long long)(rb % Db) * p.map.SB + xo;
+}
+
 constexpr int kStageAStages = 4;
 constexpr int kStageRing = 8;
 constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-11 epilogue
@@ -392,6 +402,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                   NBARS = WE + kStageRing;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    // windowed mode: a 32 x 32 FP32 staging block per epilogue warp (after the
+    // 512-byte barrier area) through which the epilogue turns its per-row
+    // results into 16-byte stores
+    float* stage_out = (float*)(sA + kStageAStages * kTileBytes + 512);
     auto bar = [&](int i) { return smem_u32(bars + i); };
 
     const uint32_t rank = cluster_rank();
@@ -445,6 +459,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
         for (int c = 0; c < nchunk; ++c) win_per_tile += ((c % p.kch) == p.kch - 1 ? ktail : 4) / p.wsteps;
 
     const long long ipu = p.mtiles / 2;  // 256-row tiles per unit
+    // tile and row indices stay below 2^31 (checked on the host): 32-bit
+    // unsigned division, a short instruction sequence, in the per-tile paths
+    const uint32_t ipu32 = (uint32_t)ipu;
     const long long total = (long long)p.units * ipu;
     const long long ncl = cluster_count_x(), cid = cluster_id_x();
     const long long t0 = total * cid / ncl;
@@ -458,8 +475,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             long long it = 0;
             bool ok = true, loaded_b = false;
             for (long long t = t0; t < t1 && ok; ++t) {
-                const int u = (int)(t / ipu);
-                const long long row0 = (t % ipu) * (2 * kBM) + (long long)rank * kBM;
+                const int u = (int)((uint32_t)t / ipu32);
+                const long long row0 = (long long)((uint32_t)t % ipu32) * (2 * kBM) + (long long)rank * kBM;
                 if (u != cur_u) {
                     if (cur_u >= 0) {
                         if (!mbar_wait_cl(bar(BEMPTY), bph, abort_flag, peer_abort, p.err, 1)) { ok = false; break; }
@@ -514,7 +531,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             Ring wr(p.nring > 0 ? p.nring : 1);
             bool ok = true, issued = false;
             for (long long t = t0; t < t1 && ok; ++t, ++tile_i) {
-                const int u = (int)(t / ipu);
+                const int u = (int)((uint32_t)t / ipu32);
                 if (u != cur_u) {
                     if (!warp_wait_cl(bar(BFULL), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
                     if (!warp_wait_cl(bar(BPEER), bfph, abort_flag, peer_abort, p.err, 3)) { ok = false; break; }
@@ -558,7 +575,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                         mma_commit_pair(bar(TEMPTY + slot), (uint16_t)3);
                     }
                     if (!ok) break;
-                    if (t + 1 < t1 && (int)((t + 1) / ipu) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
+                    if (t + 1 < t1 && (int)((uint32_t)(t + 1) / ipu32) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
                     continue;
                 }
                 const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
@@ -608,7 +625,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     it += nchunk;
                     issued = true;
                     mma_commit_pair(bar(ACCF + ab), (uint16_t)3);
-                    if (t + 1 < t1 && (int)((t + 1) / ipu) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
+                    if (t + 1 < t1 && (int)((uint32_t)(t + 1) / ipu32) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
                     continue;
                 }
                 int kc = 0;
@@ -636,7 +653,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 }
                 if (!ok) break;
                 mma_commit_pair(bar(ACCF + ab), (uint16_t)3);
-                if (t + 1 < t1 && (int)((t + 1) / ipu) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
+                if (t + 1 < t1 && (int)((uint32_t)(t + 1) / ipu32) != u) mma_commit_pair(bar(BEMPTY), (uint16_t)3);
             }
             (void)issued;
             // Closing commit to both CTAs: it completes once every MMA this
@@ -656,7 +673,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             int cur_u = -1;
             uint32_t bph = 0;
             for (long long t = t0; t < t1; ++t) {
-                const int u = (int)(t / ipu);
+                const int u = (int)((uint32_t)t / ipu32);
                 if (u == cur_u) continue;
                 cur_u = u;
                 if (!mbar_wait_cl(bar(BFULL), bph, abort_flag, peer_abort, p.err, 9)) break;
@@ -702,9 +719,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
         long long tile_i = 0;
         Ring wr(p.nring > 0 ? p.nring : 1);
         bool ok = true;
+        // 16-byte stores need rows that run contiguously in memory, 16-byte
+        // aligned column offsets and a 16-byte aligned output
+        const bool vec_out = (p.map.XB != 0 || p.map.SX == 1) && (p.map.XB % 4) == 0 &&
+                             (p.map.SA % 4) == 0 && (p.map.SB % 4) == 0 && (p.map.SC % 4) == 0 &&
+                             (p.map.SY % 4) == 0 && (p.out_unit % 4) == 0 && (p.map.Dx % 4) == 0 &&
+                             (((uintptr_t)p.out) & 15) == 0;
         for (long long t = t0; t < t1 && ok && win; ++t) {
             // windowed mode (2 Np <= 96): add the tile's windows in FP32 registers
-            const int u = (int)(t / ipu);
+            const int u = (int)((uint32_t)t / ipu32);
             float acc[96];
 #pragma unroll
             for (int j = 0; j < 96; ++j) acc[j] = 0.0f;
@@ -727,16 +750,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 if (lane == 0) mbar_arrive_cluster(bar0(WE + b));
             }
             if (!ok) break;
-            const long long row = (t % ipu) * (2 * kBM) + (long long)rank * kBM + rloc;
-            if (row < p.M) {
-                const long long x = row % p.map.Dx;
-                const long long rb = row / p.map.Dx;
-                const long long xo = p.map.XB ? (x >> 5) * p.map.XB + (x & 31) : x * p.map.SX;
-                float* o = p.out + (long long)u * p.out_unit + (rb / p.map.Db) * p.map.SA +
-                           (rb % p.map.Db) * p.map.SB + xo;
+            if (vec_out) {
+                // 16-byte stores: four consecutive rows of one column are contiguous
+                // (x runs along the rows with unit stride or inside a 32-wide block);
+                // lane l stores rows 4 (l % 8) .. + 3 of columns l / 8 + 4 i.  Tiles
+                // never cross the M rows of a unit (M = Np^3 is a multiple of 256).
+                const uint32_t row = ((uint32_t)t % ipu32) * (2 * kBM) + rank * kBM + wq * 32 + 4 * (lane & 7);
+                float* o = stage_out_row(p, u, row);
+                float* stg = stage_out + wq * 1024;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    if (cc < ncc) {
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stg[j * 32 + lane] = acc[cc * 32 + j];
+                        __syncwarp();
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int cl = 4 * i + (lane >> 3);
+                            const int col = cc * 32 + cl;
+                            const int hc = col >= Np ? 1 : 0;
+                            const int y = col - hc * Np;
+                            const float4 v4 = *reinterpret_cast<const float4*>(stg + cl * 32 + 4 * (lane & 7));
+                            if (col < 2 * Np && (long long)row + 3 < p.M)
+                                *reinterpret_cast<float4*>(o + hc * p.map.SC + (long long)y * p.map.SY) = v4;
+                        }
+                    }
+                }
+            } else {
+                const uint32_t row = ((uint32_t)t % ipu32) * (2 * kBM) + rank * kBM + rloc;
+                float* o = stage_out_row(p, u, row);
 #pragma unroll
                 for (int col = 0; col < 96; ++col) {
-                    if (col < 2 * Np) {
+                    if (col < 2 * Np && (long long)row < p.M) {
                         const int hc = col >= Np ? 1 : 0;
                         const int y = col - hc * Np;
                         o[hc * p.map.SC + (long long)y * p.map.SY] = acc[col];
@@ -745,18 +791,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             }
         }
         for (long long t = t0; t < t1 && ok && !win; ++t, ++tile_i) {
-            const int u = (int)(t / ipu);
+            const int u = (int)((uint32_t)t / ipu32);
             const int ab = SPLIT_ACC ? 0 : (int)(tile_i & 1);
             const uint32_t abph = SPLIT_ACC ? (uint32_t)(tile_i & 1) : (uint32_t)((tile_i >> 1) & 1);
             if (!warp_wait_cl(bar(ACCF + ab), abph, abort_flag, peer_abort, p.err, 8)) { ok = false; break; }
             tc_fence_after();
-            const long long row = (t % ipu) * (2 * kBM) + (long long)rank * kBM + rloc;
-            const bool valid = row < p.M;
-            const long long x = row % p.map.Dx;
-            const long long rb = row / p.map.Dx;
-            const long long xo = p.map.XB ? (x >> 5) * p.map.XB + (x & 31) : x * p.map.SX;
-            float* o = p.out + (long long)u * p.out_unit + (rb / p.map.Db) * p.map.SA +
-                       (rb % p.map.Db) * p.map.SB + xo;
+            const uint32_t row = ((uint32_t)t % ipu32) * (2 * kBM) + rank * kBM + rloc;
+            const bool valid = (long long)row < p.M;
+            float* o = stage_out_row(p, u, row);
             for (int cc = 0; cc < ncc; ++cc) {
                 uint32_t v[32];
                 tmem_ld32(lane_base + (uint32_t)(ab * 256 + cc * 32), v);
@@ -1321,59 +1363,85 @@ __global__ void k_build_vO32(int N, int Np, const double* __restrict__ v, float*
     out[e] = x;
 }
 
-// One slot of dL/dv on the tensor-core path, from the X3 that stages S1-S3
-// left in X13 (rows (u, c, b) = (2u + c) Np + b, K = (n, r, p)):
-//   out[a][(n,r,p)] += sum_{u, c, b < N} S_c(u, a, b) X3[(u,c,b)][(n,r,p)]
-// with S_c the real (c = 0) / imaginary (c = 1) part of Sbar_u[a][b], or of
-// Sbar_u[b][a] when transposeS (out = Re sum conj(Sbar) X3 over b).  A thread
-// owns one K (in the N basis) and kVbA consecutive a; the rows are split over
-// blockIdx.z.  Products and short runs are FP32 (X3 is FP32), every kVbFlush
-// rows the run is added into an FP64 sum, and the block's sums go to out by
-// FP64 atomics.
-constexpr int kVbA = 32;       // a per thread (blockIdx.y picks the range)
-constexpr int kVbRows = 64;    // rows of S staged in shared memory at a time
-constexpr int kVbFlush = 256;  // FP32 run length before the FP64 sum
-constexpr int kVbThreads = 128;
-__global__ void __launch_bounds__(kVbThreads) k_vbar_slot_tc(int N, int Np, int nb, long long Rld,
-                                                             int blocked, long long rows_per_z,
-                                                             const double2* __restrict__ Sbar,
-                                                             int transposeS, const float* __restrict__ X,
-                                                             double* __restrict__ out) {
-    __shared__ float sS[kVbRows][kVbA];
+// Contraction of the X3 that stages S1-S3 left in X13 (rows (u, c, b) =
+// (2u + c) Np + b, K = (n, r, p)) over its rows, against per-row weights:
+//   out[(a % N) SJ + (a / N) SC + n SN + r SR + p] += sum_{u, c, b < N} w(u, c, b, a) X3[(u,c,b)][(n,r,p)]
+// for a < A.  Two uses:
+//   mode 0 (one slot of dL/dv, A = N): w = Re / Im (c = 0 / 1) of Sbar_u[a][b]
+//     (Sbar_u[b][a] when transposeS), i.e. out = Re sum conj(Sbar) X3 over b;
+//   mode 1 (the time-linear accumulator, A = 2N, a = (c2, j2)): w = the real
+//     form of coef_u Gb_u^T, coef_u = -wt (u even) / +wt (u odd), wt the
+//     trapezoid weight of history point k0 + u / 2:
+//       (c2, c) = (0, 0): Re, (0, 1): -Im, (1, 0): Im, (1, 1): Re of coef_u Gb_u[b][j2].
+// A thread owns one K (in the N basis) and kXsA consecutive a; the rows are
+// split over blockIdx.z.  Products and short runs are FP32 (X3 is FP32), every
+// kXsFlush rows the run is added into an FP64 sum, and the block's sums go to
+// out by FP64 atomics.
+struct XSlotParams {
+    int N, Np, nb;
+    long long Rld;         // rows of the K-blocked X3 layout
+    int blocked;           // X3 K-blocked (Np % 32 == 0) or row-major [row][Np^3]
+    long long rows_per_z;  // compact rows (u, c, b < N) per blockIdx.z
+    int A;                 // output columns a
+    int mode;              // 0: dL/dv slot, 1: time-linear accumulator
+    const double2* S;      // Sbar_u (mode 0) or Gb_u (mode 1), N x N per unit
+    int transposeS;
+    int k0;
+    double w_first, w_rest;
+    const float* X;
+    double* out;
+    long long SJ, SC, SN, SR;
+};
+constexpr int kXsA = 32;       // a per thread (blockIdx.y picks the range)
+constexpr int kXsRows = 64;    // rows of weights staged in shared memory at a time
+constexpr int kXsFlush = 256;  // FP32 run length before the FP64 sum
+constexpr int kXsThreads = 128;
+__global__ void __launch_bounds__(kXsThreads) k_xslot_tc(const XSlotParams p) {
+    __shared__ float sW[kXsRows][kXsA];
+    const int N = p.N, Np = p.Np;
     const long long NN = (long long)N * N, N3 = NN * N;
     const long long Np3 = (long long)Np * Np * Np;
-    const long long KN = (long long)blockIdx.x * kVbThreads + threadIdx.x;
+    const long long KN = (long long)blockIdx.x * kXsThreads + threadIdx.x;
     const bool kok = KN < N3;
-    const long long n = KN / NN, r = (KN / N) % N, p = KN % N;
-    const long long K = (n * Np + r) * Np + p;
-    const float* xk = blocked ? X + (K >> 5) * Rld * 32 + (K & 31) : X + K;
-    const long long xstride = blocked ? 32 : Np3;  // per X3 row
-    const int a0 = blockIdx.y * kVbA;
-    const long long Rtot = 2LL * N * nb;  // compact rows (u, c, b < N)
-    const long long R0 = (long long)blockIdx.z * rows_per_z;
-    const long long R1 = R0 + rows_per_z < Rtot ? R0 + rows_per_z : Rtot;
-    float acc[kVbA];
-    double sum[kVbA];
+    const long long n = KN / NN, r = (KN / N) % N, pp = KN % N;
+    const long long K = (n * Np + r) * Np + pp;
+    const float* xk = p.blocked ? p.X + (K >> 5) * p.Rld * 32 + (K & 31) : p.X + K;
+    const long long xstride = p.blocked ? 32 : Np3;  // per X3 row
+    const int a0 = blockIdx.y * kXsA;
+    const long long Rtot = 2LL * N * p.nb;  // compact rows (u, c, b < N)
+    const long long R0 = (long long)blockIdx.z * p.rows_per_z;
+    const long long R1 = R0 + p.rows_per_z < Rtot ? R0 + p.rows_per_z : Rtot;
+    float acc[kXsA];
+    double sum[kXsA];
 #pragma unroll
-    for (int t = 0; t < kVbA; ++t) {
+    for (int t = 0; t < kXsA; ++t) {
         acc[t] = 0.0f;
         sum[t] = 0.0;
     }
     int run = 0;
-    for (long long rs = R0; rs < R1; rs += kVbRows) {
-        const int nrow = (int)(R1 - rs < kVbRows ? R1 - rs : kVbRows);
+    for (long long rs = R0; rs < R1; rs += kXsRows) {
+        const int nrow = (int)(R1 - rs < kXsRows ? R1 - rs : kXsRows);
         __syncthreads();
-        for (int e = threadIdx.x; e < kVbRows * kVbA; e += kVbThreads) {
-            const int rr = e / kVbA, aa = e % kVbA, a = a0 + aa;
+        for (int e = threadIdx.x; e < kXsRows * kXsA; e += kXsThreads) {
+            const int rr = e / kXsA, aa = e % kXsA, a = a0 + aa;
             float val = 0.0f;
-            if (rr < nrow && a < N) {
+            if (rr < nrow && a < p.A) {
                 const long long Rc = rs + rr, uc = Rc / N;
                 const int b = (int)(Rc % N), u = (int)(uc >> 1), cc = (int)(uc & 1);
-                const double2 s = transposeS ? Sbar[u * NN + (long long)b * N + a]
-                                             : Sbar[u * NN + (long long)a * N + b];
-                val = (float)(cc ? s.y : s.x);
+                if (p.mode == 0) {
+                    const double2 sv = p.transposeS ? p.S[u * NN + (long long)b * N + a]
+                                                    : p.S[u * NN + (long long)a * N + b];
+                    val = (float)(cc ? sv.y : sv.x);
+                } else {
+                    const int c2 = a / N, j2 = a % N;
+                    const double2 g = p.S[u * NN + (long long)b * N + j2];
+                    const double wt = (p.k0 + u / 2 == 0) ? p.w_first : p.w_rest;
+                    const double coef = (u & 1) ? wt : -wt;
+                    const double re = coef * g.x, im = coef * g.y;
+                    val = (float)(c2 == 0 ? (cc == 0 ? re : -im) : (cc == 0 ? im : re));
+                }
             }
-            sS[rr][aa] = val;
+            sW[rr][aa] = val;
         }
         __syncthreads();
         if (kok) {
@@ -1382,15 +1450,15 @@ __global__ void __launch_bounds__(kVbThreads) k_vbar_slot_tc(int N, int Np, int 
             for (int rr = 0; rr < nrow; ++rr) {
                 const float x = xk[(uc * Np + b) * xstride];
 #pragma unroll
-                for (int t = 0; t < kVbA; ++t) acc[t] = fmaf(sS[rr][t], x, acc[t]);
+                for (int t = 0; t < kXsA; ++t) acc[t] = fmaf(sW[rr][t], x, acc[t]);
                 if (++b == N) {
                     b = 0;
                     ++uc;
                 }
-                if (++run == kVbFlush) {
+                if (++run == kXsFlush) {
                     run = 0;
 #pragma unroll
-                    for (int t = 0; t < kVbA; ++t) {
+                    for (int t = 0; t < kXsA; ++t) {
                         sum[t] += (double)acc[t];
                         acc[t] = 0.0f;
                     }
@@ -1399,9 +1467,38 @@ __global__ void __launch_bounds__(kVbThreads) k_vbar_slot_tc(int N, int Np, int 
         }
     }
     if (!kok) return;
+    const long long ko = n * p.SN + r * p.SR + pp;
 #pragma unroll
-    for (int t = 0; t < kVbA; ++t)
-        if (a0 + t < N) atomicAdd(out + (long long)(a0 + t) * N3 + KN, sum[t] + (double)acc[t]);
+    for (int t = 0; t < kXsA; ++t) {
+        const int a = a0 + t;
+        if (a < p.A) atomicAdd(p.out + (a % N) * p.SJ + (a / N) * p.SC + ko, sum[t] + (double)acc[t]);
+    }
+}
+
+// Time-linear back-transforms: Ucal = W^+ and conj(Ucal) = W^T as two units.
+__global__ void k_tl_ucal2(int N, const double2* __restrict__ W, double2* __restrict__ out) {
+    const long long NN = (long long)N * N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NN) return;
+    const int pr = (int)(e / N), q = (int)(e % N);
+    const double2 w = W[(long long)q * N + pr];
+    out[e] = make_double2(w.x, -w.y);
+    out[NN + e] = w;
+}
+
+// Lambda (FP64, N basis, [j][n][r][c][p]) to FP32 in the Np basis, zero padded.
+__global__ void k_tl_lam32(int N, int Np, const double* __restrict__ lam, float* __restrict__ out) {
+    const long long Npl = Np;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * Npl * Npl * Npl * Npl) return;
+    const int pp = (int)(e % Np), cc = (int)((e / Np) % 2), r = (int)((e / (2 * Npl)) % Np),
+              n = (int)((e / (2 * Npl * Npl)) % Np), j = (int)(e / (2 * Npl * Npl * Npl));
+    float x = 0.0f;
+    if (pp < N && r < N && n < N && j < N) {
+        const long long Nl = N;
+        x = (float)lam[(((j * Nl + n) * Nl + r) * 2 + cc) * Nl + pp];
+    }
+    out[e] = x;
 }
 
 // Per-unit B operands of the tensor-core path (padded to Np, zero padding),
@@ -1487,7 +1584,9 @@ gkba_status make_map(gkba_ctx* c, CUtensorMap* m, const void* base, int rank, co
 constexpr int kMaxTcNp = 96;  // largest padded basis of the tensor-core path
 size_t stage_smem_bytes(int Np) {
     const int kch = (Np + kKC - 1) / kKC;
-    return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 512;
+    // windowed mode (2 Np <= 96) adds the epilogue's 4 x 4 KB staging blocks
+    return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 512 +
+           (2 * Np <= 96 ? 4 * 32 * 32 * 4 : 0);
 }
 size_t final_pair_smem_bytes(int Np) {
     return 1024 + (size_t)kFinPairStages * (kTileBytes + 2 * (Np / 2) * 128) + 512;
@@ -1563,12 +1662,110 @@ gkba_status build_forms(gkba_ctx* c, int nb, const double2* G, long long sG, con
     return build_forms_fp64(c, nb, G, Gb);
 }
 
+// Parameters shared by every stage launch of nb units (S1-S3 and the
+// time-linear back-transforms); the caller sets planes, a_unit, out and map.
+static StageParams stage_base(gkba_ctx* c, int nb) {
+    const int Np = c->Np;
+    const long long N3 = (long long)Np * Np * Np;
+    StageParams sp{};
+    sp.Np = Np;
+    sp.kch = (Np + kKC - 1) / kKC;
+    sp.mtiles = (int)(N3 / kBM);
+    sp.M = N3;
+    sp.units = nb;
+    sp.out_unit = 2 * N3 * Np;
+    sp.unit_sys = nullptr;
+    sp.err = c->dint + 1;
+    // windowed accumulation where the ring fits next to the A slots (2 Np <= 96)
+    sp.as2 = ((2 * Np + 31) / 32) * 32;
+    sp.wsteps = 2 * Np <= 96 ? std::max(1, std::min(2, c->acc_window / 8)) : 0;
+    sp.nring = std::min(kStageRing, (512 - 128) / sp.as2);
+    return sp;
+}
+
+// Persistent grid of a stage launch: one CTA pair per resident cluster, at
+// most one per 256-row tile.
+static int stage_grid(gkba_ctx* c, int nb) {
+    // callers keep nb * Np^3 / 256 below 2^31 (the kernel's 32-bit tile index):
+    // nb is at most the workspace's units, far below 2^31 / 3456 at N = 96
+    const long long pair_tiles = (long long)nb * ((long long)c->Np * c->Np * c->Np / kBM) / 2;
+    return 2 * (int)(pair_tiles < c->pair_clusters ? pair_tiles : c->pair_clusters);
+}
+
+// Stage S4 and the reduction of nb units whose X3 stages S1-S3 (or the
+// time-linear back-transforms) left in X13: S_u -> c->Su.
+static gkba_status tf32_final(gkba_ctx* c, int nb) {
+    const int Np = c->Np;
+    const long long N2 = (long long)Np * Np, N3 = N2 * Np, N4 = N3 * Np;
+    float* X13 = (float*)c->X13;
+    int* err = c->dint + 1;
+    const double Nr = c->N;
+    const double fl_cr = 4.0 * Nr * Nr * Nr * Nr * Nr;
+    const double N4r = Nr * Nr * Nr * Nr;
+    const bool multi = c->unit_sys != nullptr;
+    const long long rows = 2LL * Np * nb;
+    const bool blocked = (Np % 32) == 0;
+    CUtensorMap mAf, mVh, mVl;
+    if (blocked) {
+        const long long Rl = ((2LL * Np * nb + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
+        cuuint64_t d[3] = {32, (cuuint64_t)Rl, (cuuint64_t)(N3 / 32)};
+        cuuint64_t s[2] = {32 * 4, (cuuint64_t)(Rl * 32 * 4)};
+        cuuint32_t b[3] = {kKC, kBM, 1};
+        GKBA_TRY(make_map(c, &mAf, X13, 3, d, s, b));
+    } else {
+        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)(2LL * Np * nb)};
+        cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
+        cuuint32_t b[2] = {kKC, kBM};
+        GKBA_TRY(make_map(c, &mAf, X13, 2, d, s, b));
+    }
+    if (multi) {
+        cuuint64_t d[3] = {(cuuint64_t)N3, (cuuint64_t)Np, (cuuint64_t)c->nsys};
+        cuuint64_t s[2] = {(cuuint64_t)N3 * 4, (cuuint64_t)(N4 * 4)};
+        cuuint32_t b[3] = {kKC, (cuuint32_t)(Np / 2), 1};
+        GKBA_TRY(make_map(c, &mVh, c->vKhi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &mVl, c->vKlo, 3, d, s, b));
+    } else {
+        // each CTA of an S4 pair loads Np/2 rows of vK
+        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)Np};
+        cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
+        cuuint32_t b[2] = {kKC, (cuuint32_t)(Np / 2)};
+        GKBA_TRY(make_map(c, &mVh, c->vKhi, 2, d, s, b));
+        GKBA_TRY(make_map(c, &mVl, c->vKlo, 2, d, s, b));
+    }
+    // split-K over (n,r,p)
+    FinalParams fp{};
+    fp.Np = Np;
+    fp.K = N3;
+    fp.KS = c->acc_window;
+    fp.KW = kTcItemK;
+    fp.nks = (int)((N3 + fp.KW - 1) / fp.KW);
+    fp.rows = rows;
+    fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
+    fp.Rld = (long long)fp.ngroups * 2 * kBM;
+    fp.blocked = blocked ? 1 : 0;
+    fp.part = (float*)c->part;
+    fp.err = err;
+    fp.unit_sys = c->unit_sys;
+    if ((size_t)fp.nks * Np * fp.Rld * 4 > c->part_bytes)
+        return fail(c, GKBA_ESTATE, "partial buffer too small");
+    {
+        const long long items = (long long)fp.ngroups * fp.nks;
+        const int g = 2 * (int)(items < c->fin_pair_clusters ? items : c->fin_pair_clusters);
+        auto t = launch_begin(c, K_FIN, fl_cr * nb, 4.0 * (2 * N4r * nb + 2 * N4r));
+        k_tc_final_pair<<<g, kFinThreads, final_pair_smem_bytes(Np), c->stream>>>(mAf, mVh, mVl, fp);
+        GKBA_TRY(launch_end(c, t));
+    }
+    return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
+}
+
 // Stages S1-S3 of one batch (forms built) with A1 as S1's A operand (wS32,
 // or the omega layout of v for dL/dv): X3 lands in X13, K-blocked when
 // Np % 32 == 0.  With do_final, stage S4 and the reduction follow: S_u -> c->Su.
 static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_final) {
     const int Np = c->Np;
     const long long N2 = (long long)Np * Np, N3 = N2 * Np, N4 = N3 * Np;
+    if ((long long)nb * (N3 / kBM) >= (1LL << 31))
+        return fail(c, GKBA_EINVAL, "%d units exceed the stage kernel's 32-bit tile index", nb);
     const int kch = (Np + kKC - 1) / kKC;
     const int mtiles = (int)(N3 / kBM);
     float* X13 = (float*)c->X13;
@@ -1586,7 +1783,7 @@ static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_fina
     const double fl_cr = 4.0 * Nr * Nr * Nr * Nr * Nr, fl_cc = 2.0 * fl_cr;
     const double N4r = Nr * Nr * Nr * Nr;
 
-    CUtensorMap mA1, mA23_in1, mA23_in2, mB1h, mB1l, mGh, mGl, mG3h, mG3l, mAf, mVh, mVl;
+    CUtensorMap mA1, mA23_in1, mA23_in2, mB1h, mB1l, mGh, mGl, mG3h, mG3l;
     const bool multi = c->unit_sys != nullptr;  // several systems: w and v per system
     if (multi) {
         cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)N3, (cuuint64_t)c->nsys};
@@ -1620,50 +1817,10 @@ static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_fina
         GKBA_TRY(make_map(c, &mG3h, G3hi, 3, dg, sg, b));
         GKBA_TRY(make_map(c, &mG3l, G3lo, 3, dg, sg, b));
     }
-    if ((Np % 32) == 0) {
-        const long long Rl = ((2LL * Np * nb + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
-        cuuint64_t d[3] = {32, (cuuint64_t)Rl, (cuuint64_t)(N3 / 32)};
-        cuuint64_t s[2] = {32 * 4, (cuuint64_t)(Rl * 32 * 4)};
-        cuuint32_t b[3] = {kKC, kBM, 1};
-        GKBA_TRY(make_map(c, &mAf, X13, 3, d, s, b));
-    } else {
-        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)(2LL * Np * nb)};
-        cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
-        cuuint32_t b[2] = {kKC, kBM};
-        GKBA_TRY(make_map(c, &mAf, X13, 2, d, s, b));
-    }
-    if (multi) {
-        cuuint64_t d[3] = {(cuuint64_t)N3, (cuuint64_t)Np, (cuuint64_t)c->nsys};
-        cuuint64_t s[2] = {(cuuint64_t)N3 * 4, (cuuint64_t)(N4 * 4)};
-        cuuint32_t b[3] = {kKC, (cuuint32_t)(Np / 2), 1};
-        GKBA_TRY(make_map(c, &mVh, c->vKhi, 3, d, s, b));
-        GKBA_TRY(make_map(c, &mVl, c->vKlo, 3, d, s, b));
-    } else {
-        // each CTA of an S4 pair loads Np/2 rows of vK
-        cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)Np};
-        cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
-        cuuint32_t b[2] = {kKC, (cuuint32_t)(Np / 2)};
-        GKBA_TRY(make_map(c, &mVh, c->vKhi, 2, d, s, b));
-        GKBA_TRY(make_map(c, &mVl, c->vKlo, 2, d, s, b));
-    }
-
     const size_t ssm = stage_smem_bytes(Np);
     auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_pair<true> : k_tc_pair<false>;
-    const long long pair_tiles = (long long)nb * mtiles / 2;  // 256-row tiles
-    const int grid = 2 * (int)(pair_tiles < c->pair_clusters ? pair_tiles : c->pair_clusters);
-    StageParams sp{};
-    sp.Np = Np;
-    sp.kch = kch;
-    sp.mtiles = mtiles;
-    sp.M = N3;
-    sp.units = nb;
-    sp.out_unit = 2 * N4;
-    sp.unit_sys = nullptr;
-    sp.err = err;
-    // windowed accumulation where the ring fits next to the A slots (2 Np <= 96)
-    sp.as2 = ((2 * Np + 31) / 32) * 32;
-    sp.wsteps = 2 * Np <= 96 ? std::max(1, std::min(2, c->acc_window / 8)) : 0;
-    sp.nring = std::min(kStageRing, (512 - 128) / sp.as2);
+    const int grid = stage_grid(c, nb);
+    StageParams sp = stage_base(c, nb);
     // S1: rows (j,m,q), cols (c,r) -> X1[j][r][m][c][q]
     sp.planes = 1;
     sp.a_unit = 0;
@@ -1707,30 +1864,7 @@ static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_fina
         GKBA_TRY(launch_end(c, t));
     }
     if (!do_final) return GKBA_OK;
-    // S4: split-K over (n,r,p)
-    FinalParams fp{};
-    fp.Np = Np;
-    fp.K = N3;
-    fp.KS = c->acc_window;
-    fp.KW = kTcItemK;
-    fp.nks = (int)((N3 + fp.KW - 1) / fp.KW);
-    fp.rows = rows;
-    fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
-    fp.Rld = (long long)fp.ngroups * 2 * kBM;
-    fp.blocked = blocked ? 1 : 0;
-    fp.part = (float*)c->part;
-    fp.err = err;
-    fp.unit_sys = c->unit_sys;
-    if ((size_t)fp.nks * Np * fp.Rld * 4 > c->part_bytes)
-        return fail(c, GKBA_ESTATE, "partial buffer too small");
-    {
-        const long long items = (long long)fp.ngroups * fp.nks;
-        const int g = 2 * (int)(items < c->fin_pair_clusters ? items : c->fin_pair_clusters);
-        auto t = launch_begin(c, K_FIN, fl_cr * nb, 4.0 * (2 * N4r * nb + 2 * N4r));
-        k_tc_final_pair<<<g, kFinThreads, final_pair_smem_bytes(Np), c->stream>>>(mAf, mVh, mVl, fp);
-        GKBA_TRY(launch_end(c, t));
-    }
-    return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
+    return tf32_final(c, nb);
 }
 
 // Tensor-core contraction of one batch (forms built): S_u -> c->Su.
@@ -1753,23 +1887,146 @@ gkba_status tf32_prepare_vgrad(gkba_ctx* c) {
 // X3 of the w-slot chain: stages S1-S3 with the omega layout of v (forms built).
 gkba_status tf32_chain_omega(gkba_ctx* c, int nb) { return tf32_chain(c, nb, c->vO32, false); }
 
-gkba_status vbar_slot_tf32(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, double* out) {
+// Launch of k_xslot_tc over the X3 of nb units in X13.
+static gkba_status xslot_launch(gkba_ctx* c, int nb, XSlotParams xp, int cls, double bytes) {
     const int N = c->N, Np = c->Np;
     const long long N3 = (long long)N * N * N;
     const long long rows = 2LL * Np * nb;
-    const long long Rld = ((rows + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
+    xp.N = N;
+    xp.Np = Np;
+    xp.nb = nb;
+    xp.Rld = ((rows + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
+    xp.blocked = (Np % 32) == 0 ? 1 : 0;
+    xp.X = (const float*)c->X13;
     const long long Rtot = 2LL * N * nb;
-    const unsigned gx = grid1(N3, kVbThreads), gy = (unsigned)((N + kVbA - 1) / kVbA);
+    const unsigned gx = grid1(N3, kXsThreads), gy = (unsigned)((xp.A + kXsA - 1) / kXsA);
     // enough blocks for about eight per SM, each over at least 1024 rows
     long long gz = std::max(1LL, std::min((Rtot + 1023) / 1024,
                                           (8LL * c->num_sms + gx * gy - 1) / ((long long)gx * gy)));
-    const long long per = ((Rtot + gz - 1) / gz + kVbRows - 1) / kVbRows * kVbRows;
+    const long long per = ((Rtot + gz - 1) / gz + kXsRows - 1) / kXsRows * kXsRows;
     gz = (Rtot + per - 1) / per;
-    auto t = launch_begin(c, K_RED, 4.0 * (double)N3 * N * Rtot, 4.0 * (double)Rtot * N3);
-    k_vbar_slot_tc<<<dim3(gx, gy, (unsigned)gz), kVbThreads, 0, c->stream>>>(
-        N, Np, nb, Rld, (Np % 32) == 0 ? 1 : 0, per, Sbar, transposeS, (const float*)c->X13, out);
+    xp.rows_per_z = per;
+    auto t = launch_begin(c, cls, 2.0 * (double)N3 * xp.A * Rtot, bytes);
+    k_xslot_tc<<<dim3(gx, gy, (unsigned)gz), kXsThreads, 0, c->stream>>>(xp);
     return launch_end(c, t);
 }
+
+gkba_status vbar_slot_tf32(gkba_ctx* c, int nb, const double2* Sbar, int transposeS, double* out) {
+    const long long N = c->N;
+    XSlotParams xp{};
+    xp.A = (int)N;
+    xp.mode = 0;
+    xp.S = Sbar;
+    xp.transposeS = transposeS;
+    xp.out = out;
+    xp.SJ = N * N * N;
+    xp.SC = 0;
+    xp.SN = N * N;
+    xp.SR = N;
+    return xslot_launch(c, nb, xp, K_RED, 4.0 * 2.0 * N * nb * N * N * N);
+}
+
+// One complex one-index transform of a single unit on the stage kernel (S2 /
+// S3 form): A planar [rows][c][Np] FP32 at `in`, B the TF32 forms of unit
+// `bunit` in formsG3, output through `map` into `out`.
+static gkba_status tl_stage(gkba_ctx* c, const float* in, int bunit, float* out, StageMap map,
+                            long long out_unit) {
+    const int Np = c->Np;
+    const long long N3 = (long long)Np * Np * Np, N4 = N3 * Np;
+    const long long per = 2LL * Np * Np;
+    const float* Bhi = (const float*)c->formsG3 + 2 * per * bunit;
+    const float* Blo = (const float*)c->formsG3 + 2 * per * c->ub_cap + 2 * per * bunit;
+    CUtensorMap mA, mBh, mBl;
+    {
+        cuuint64_t d[4] = {(cuuint64_t)Np, 2, (cuuint64_t)N3, 1};
+        cuuint64_t s[3] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * Np * 4, (cuuint64_t)(2 * N4 * 4)};
+        cuuint32_t b[4] = {kKC, 1, kBM, 1};
+        GKBA_TRY(make_map(c, &mA, in, 4, d, s, b));
+    }
+    {
+        cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)4 * Np, 1};
+        cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * per * 4};
+        cuuint32_t b[3] = {kKC, (cuuint32_t)Np, 1};
+        GKBA_TRY(make_map(c, &mBh, Bhi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &mBl, Blo, 3, d, s, b));
+    }
+    StageParams sp = stage_base(c, 1);
+    sp.planes = 2;
+    sp.a_unit = 1;
+    sp.out = out;
+    sp.out_unit = out_unit;
+    sp.map = map;
+    const double Nr = c->N;
+    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_pair<true> : k_tc_pair<false>;
+    auto t = launch_begin(c, K_TL, 8.0 * Nr * Nr * Nr * Nr * Nr, 4.0 * 4 * Nr * Nr * Nr * Nr);
+    stage_kernel<<<stage_grid(c, 1), kStageThreads, stage_smem_bytes(Np), c->stream>>>(mA, mBh, mBl, sp);
+    return launch_end(c, t);
+}
+
+// The time-linear collision's tensor contractions on the tensor cores:
+//   S = sum_{npr} v_irpn (Ucal x_n Ucal x_p conj(Ucal) x_r Lambda)_{j n r p} -> c->Su
+// with Ucal = W^+ and Lambda FP64 [j][n][r][c][p] (N basis).  Lambda is
+// rounded to FP32 (it is a sum that is already final), the three one-index
+// transforms run on the stage kernel and the last writes X3 in stage S4's
+// layout:
+//   x_p, Ucal:       rows (j, n, r)  -> [j][n][p'][c'][r]
+//   x_r, conj(Ucal): rows (j, n, p') -> [j][r'][p'][c'][n]
+//   x_n, Ucal:       rows (j, r', p') -> X3 (rows (c', j), K (n', r', p'))
+gkba_status tl_apply_tf32(gkba_ctx* c, const double2* W, const double* lam) {
+    const int N = c->N, Np = c->Np;
+    const long long NN = (long long)N * N;
+    const long long N2 = (long long)Np * Np, N3 = N2 * Np, N4 = N3 * Np;
+    double2* UU = c->Yu;  // Ucal, conj(Ucal)
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_tl_ucal2<<<grid1(NN, 256), 256, 0, c->stream>>>(N, W, UU);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_forms_tf32<<<grid1(2LL * Np * Np * 2, 256), 256, 0, c->stream>>>(N, Np, 2, c->ub_cap, UU, nullptr,
+                                                                        nullptr, (float*)c->formsG3);
+    GKBA_TRY(launch_end(c, t));
+    float* X2 = (float*)c->X2;
+    float* X13 = (float*)c->X13;
+    t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_tl_lam32<<<grid1(2 * N4, 256), 256, 0, c->stream>>>(N, Np, lam, X2);
+    GKBA_TRY(launch_end(c, t));
+    GKBA_TRY(tl_stage(c, X2, 0, X13, StageMap{2 * N3, 2 * N2, 1, Np, 2 * Np, Np, Np, Np}, 2 * N4));
+    GKBA_TRY(tl_stage(c, X13, 1, X2, StageMap{2 * N3, 1, 2 * Np, Np, 2 * N2, Np, Np, Np}, 2 * N4));
+    const long long Rld = 2 * kBM;  // one unit: 2 Np <= 256 rows
+    const bool blocked = (Np % 32) == 0;
+    if (blocked && (size_t)(N3 * Rld * 4) > c->x13_bytes)
+        return fail(c, GKBA_ESTATE, "X3 buffer too small for the K-blocked layout");
+    if (blocked)
+        GKBA_TRY(tl_stage(c, X2, 0, X13, StageMap{32, Np * Rld, 0, 32 * Np, N2 * Rld, Np, Np, Np, 32 * Rld},
+                          2LL * Np * 32));
+    else
+        GKBA_TRY(tl_stage(c, X2, 0, X13, StageMap{N3, Np, 1, N4, N2, Np, Np, Np}, 2 * N4));
+    return tf32_final(c, 1);
+}
+
+// Time-linear terms on the tensor cores (forms of the nb = 2 nk units built):
+// stages S1-S3 give Z(X_k, Xb_k) and Z(Xb_k, X_k) as X3; the accumulator
+// contraction over j writes D = sum_k c_k [Z(Xb_k, X_k) x_j X_k^+ - Z(X_k, Xb_k) x_j Xb_k^+]
+// as FP64 [j2][n][r][c2][p] (planar complex).
+gkba_status tl_terms_tf32(gkba_ctx* c, int nb, const double2* Gb, int k0, double w_first,
+                          double w_rest, double* D) {
+    const long long N = c->N;
+    GKBA_TRY(tf32_chain(c, nb, c->wS32, false));
+    GKBA_CUDA(c, cudaMemsetAsync(D, 0, 2 * N * N * N * N * 8, c->stream));
+    XSlotParams xp{};
+    xp.A = (int)(2 * N);
+    xp.mode = 1;
+    xp.S = Gb;
+    xp.k0 = k0;
+    xp.w_first = w_first;
+    xp.w_rest = w_rest;
+    xp.out = D;
+    xp.SJ = 2 * N * N * N;
+    xp.SC = N;
+    xp.SN = 2 * N * N;
+    xp.SR = 2 * N;
+    return xslot_launch(c, nb, xp, K_TL, 4.0 * 2.0 * N * nb * N * N * N + 8.0 * 2 * N * N * N * N);
+}
+
 
 gkba_status wait_selftest(gkba_ctx* c, double limit_ms, double* elapsed_ms) {
     unsigned long long* el = nullptr;

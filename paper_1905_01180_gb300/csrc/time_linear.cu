@@ -1,5 +1,6 @@
 // time_linear.cu - the history sum of Eq. (collint) in time-linear form (an
-// extension of the method; FP64 on the CUDA cores).
+// extension of the method): FP64 on the CUDA cores, or its contractions on the
+// tensor cores (split-TF32 contexts; Lambda_acc stays FP64).
 //
 // With the HF propagator of Eq. (prop) written as a product of the step
 // unitaries, T(t_n, t_k) = Ucal_n Ucal_k^+ (Ucal_{k+1} = U_k Ucal_k), the GKBA
@@ -121,6 +122,12 @@ gkba_status tl_terms(gkba_ctx* c, int nk, const double2* rho, const double2* W, 
     auto t = launch_begin(c, K_PREP, 0.0, 0.0);
     k_tl_points<<<grid1(nk * NN, 256), 256, 0, c->stream>>>(N, nk, W, sW, G, Gb);
     GKBA_TRY(launch_end(c, t));
+    if (tensor_core_path(c)) {
+        // split-TF32 chain on the tensor cores, FP64 accumulation of D
+        GKBA_TRY(build_forms_tf32(c, nb, G, Gb));
+        c->sep_A = false;
+        return tl_terms_tf32(c, nb, Gb, k0, w_first, w_rest, (double*)c->X2);
+    }
     GKBA_TRY(build_forms_fp64(c, nb, G, Gb));
     double* M = (double*)c->formsG3;  // 4 N^2 nb doubles; unused by this chain (sep_A off)
     t = launch_begin(c, K_PREP, 0.0, 0.0);
@@ -153,6 +160,11 @@ gkba_status tl_apply(gkba_ctx* c, const double2* W, double2* I_out) {
     const int N = c->N;
     const long long NN = (long long)N * N, N2 = NN, N3 = N2 * N, N4 = N3 * N;
     GKBA_TRY(ensure_workspace(c, 2));
+    if (tensor_core_path(c)) {
+        GKBA_TRY(tl_apply_tf32(c, W, c->tl_s));
+        return zgemm_batched(c, K_RED, N, 'N', 'N', make_double2(1.0, 0.0), c->Su, 0, W, 0,
+                             make_double2(0.0, 0.0), I_out, 0, 1, 0);
+    }
     double* Ur = c->tl_uf;
     double* Urc = c->tl_uf + 4 * NN;
     auto t = launch_begin(c, K_PREP, 0.0, 0.0);

@@ -6,6 +6,8 @@ so every step must reproduce the history-sum stepper (FP64 GPU path) and the
 oracle's propagation to rounding.  Tolerances: 1e-11 on rho and the energies
 against the history-sum stepper, 1e-10 against the oracle, 1e-9 on the
 collision integral (it carries the cancellation of Sigma^> G^< - Sigma^< G^>).
+On a split-TF32 context the same steps run their contractions on the tensor
+cores: 1e-5 on rho and 2e-5 on I against the oracle and the FP64 path.
 """
 import numpy as np
 import pytest
@@ -197,3 +199,70 @@ def test_config1_time_linear_full_run(P):
     assert np.abs(tr - 6.0).max() < 1e-11
     assert herm < 1e-12
     assert ec[-1] < 0.0
+
+
+@pytest.mark.parametrize("precision", ["tf32", "tf32acc"])
+def test_time_linear_split_tf32_matches_oracle(P, precision):
+    # terms, their accumulation over j, the three back-transforms and stage S4
+    # on the tensor cores; Lambda_acc in FP64.  Against the oracle's history-sum
+    # propagation (Eq. (2b-opt) contraction) step by step.
+    N, n, dt = 6, 15, 0.05
+    s = gi.system(N, 8, seed=2)
+    E = field(n, dt)
+    ref = O.propagate(s["h"], s["v"], s["d"], s["rho0"], dt, n, E, route="paper")
+    ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear",
+                    precision=precision)
+    wr = wi = 0.0
+    for k in range(n):
+        rho, I, diag = ctx.step(E[k], E[k + 1])
+        wr = max(wr, check(rho, ref.rho[k + 1], 1e-5, f"rho step {k + 1}"))
+        if k > 0:
+            wi = max(wi, check(I, ref.I[k], 2e-5, f"I step {k}"))
+    print(f"time-linear {precision} N={N}: rho vs oracle {wr:.2e}, I {wi:.2e}")
+    ctx.close()
+
+
+@pytest.mark.parametrize("N,n", [(13, 12), (32, 8), (34, 6)])
+def test_time_linear_split_tf32_matches_fp64(P, N, n):
+    # Np = 16, 32 (K-blocked X3) and 48: the split-TF32 time-linear steps
+    # against the FP64 history-sum stepper (dt = 0.02: with dt = 0.05 the
+    # seeded systems from N = 40 on leave Heun's stability region in FP64 too)
+    dt = 0.02
+    s = gi.system(N, 8, seed=N)
+    E = field(n, dt)
+    a = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n)
+    b = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, history="time_linear",
+                  precision="tf32")
+    wr = wi = 0.0
+    for k in range(n):
+        ra, Ia, da = a.step(E[k], E[k + 1])
+        rb, Ib, db = b.step(E[k], E[k + 1])
+        wr = max(wr, check(rb, ra, 1e-5, f"rho step {k + 1}"))
+        if k > 0:
+            wi = max(wi, check(Ib, Ia, 2e-5, f"I step {k}"))
+        assert abs(db[0] - da[0]) < 1e-6  # particle number (split-TF32 Re Tr I)
+    print(f"time-linear split-TF32 N={N}: rho vs FP64 history sum {wr:.2e}, I {wi:.2e}")
+    a.close()
+    b.close()
+
+
+def test_time_linear_split_tf32_set_history(P):
+    # the accumulator rebuilt over 9 history points in one batch, then steps,
+    # against the FP64 history-sum stepper
+    N, n0, n1, dt = 16, 9, 4, 0.05
+    s = gi.system(N, 8, seed=7)
+    E = field(n0 + n1, dt)
+    a = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n0 + n1)
+    for k in range(n0):
+        a.step(E[k], E[k + 1])
+    n, rho_hist, T_hist = a.get_history()
+    b = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n0 + n1, history="time_linear",
+                  precision="tf32")
+    b.set_history(n, rho_hist, T_hist)
+    for k in range(n0, n0 + n1):
+        ra, Ia, _ = a.step(E[k], E[k + 1])
+        rb, Ib, _ = b.step(E[k], E[k + 1])
+        check(rb, ra, 1e-5, f"rho step {k + 1}")
+        check(Ib, Ia, 2e-5, f"I step {k}")
+    a.close()
+    b.close()
