@@ -338,9 +338,10 @@ gkba_status gkba_collision_vjp(gkba_ctx* ctx, int L, const double* rho_hist, con
 /*
  * Stacked batches of systems: many systems of uneven basis size and history
  * length advanced together.  The (t_k, component) units of all systems of the
- * same N share each launch of the contraction kernels (per system only the w
- * and v layouts differ, and the kernels select them per unit); the per-system
- * N^2 / N^3 work (mean field, propagator, Heun update) runs per system.
+ * same N are stacked (per system only the w and v layouts differ, and the
+ * kernels select them per unit), and the groups of different N share each
+ * stage launch; the per-system N^2 / N^3 work (mean field, propagator, Heun
+ * update) runs per system.
  *
  * gkba_batch_create - ctxs: n_ctx distinct contexts made by gkba_init with
  *   the same split-TF32 precision and acc_window, the general interaction and
@@ -364,6 +365,36 @@ gkba_status gkba_batch_step(gkba_batch* batch, const double* E_n, const double* 
                             double* const* rho_out, double* const* diag_out);
 const char* gkba_batch_last_error(const gkba_batch* batch);
 void gkba_batch_destroy(gkba_batch* batch);
+
+/*
+ * How a stacked batch runs (the paper has no counterpart; properties of this
+ * implementation).
+ *
+ * Every round of gkba_batch_step's collision integrals puts the batches of
+ * all basis-size groups into one launch per contraction stage: the launch's
+ * CTA pairs are split between the groups in proportion to their estimated
+ * cost, each group with its own tensor maps and parameters.
+ *
+ * gkba_batch_set_options - use_graph = 1: each gkba_batch_step captures its
+ *   device work (all members, both collision integrals) on the batch's stream
+ *   and launches it as one CUDA graph; the previous step's executable graph is
+ *   updated in place when the step's launch sequence kept its shape, else
+ *   instantiated anew.  use_graph = 0 (default): launched one by one.  The
+ *   results are the same either way (same kernels, same order).
+ * gkba_batch_autotune - chooses per group, by timing contraction rounds on
+ *   the device over units built from the members' current histories (it reads
+ *   them, changes no member state): the K length of a stage-S4 work item
+ *   (4096, 8192 or 16384), the accumulation window of the windowed stage
+ *   kernel (acc_window 8 or 16; both keep the split-TF32 tolerance) and the
+ *   units per round (from the workspace's down by halves while each stage
+ *   launch keeps two 256-row tiles per CTA pair), coordinate by coordinate,
+ *   fastest per unit.  The choices stay with the batch and are returned per
+ *   group (arrays of at least 8 entries, NULL to skip): N, units per round,
+ *   acc_window, S4 item K and the measured microseconds per unit.
+ */
+gkba_status gkba_batch_set_options(gkba_batch* batch, int use_graph);
+gkba_status gkba_batch_autotune(gkba_batch* batch, int* n_groups, int* N, int* units,
+                                int* acc_window, int* s4_item_k, double* us_per_unit);
 
 /*
  * gkba_selftest_timeout - failure detection without a GPU fault: runs a

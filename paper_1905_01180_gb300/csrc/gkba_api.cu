@@ -1215,6 +1215,8 @@ void gkba_destroy(gkba_ctx* c) { free_ctx(c); }
 // (G = Gbar = 0, coefficient 0) to a multiple of 256 / gcd(256, 2 Np) so that
 // no 256-row group of S4 straddles two systems.
 // ---------------------------------------------------------------------------
+constexpr int kMaxBatchLaunchGroups = 8;  // groups per stage launch (the kernels' limit)
+
 struct gkba_batch {
     int device = -1;
     cudaStream_t stream = nullptr;
@@ -1228,8 +1230,13 @@ struct gkba_batch {
         int* sys_dev = nullptr;    // unit -> system (group-local index), per collision
         int* sys_host[2] = {nullptr, nullptr};  // pinned staging, one per collision of a step
         long long sys_cap = 0;
+        // autotuner record (gkba_batch_autotune)
+        double us_per_unit = 0.0;
     };
     std::vector<Group> groups;
+    bool use_graph = false;          // gkba_batch_set_options
+    cudaGraphExec_t gexec = nullptr; // the last step's executable graph (updated in place)
+    long long graph_steps = 0, graph_rebuilds = 0;
 };
 
 namespace {
@@ -1259,17 +1266,15 @@ void free_batch(gkba_batch* b) {
             free_ctx(g.sh);
         }
     }
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
 
-// Collision integrals of every member of group g over its own history (L =
-// n + 1 points with T = T_a, or n + 2 points with T = T_b), into Ia or Ib.
-gkba_status batch_collision(gkba_batch* b, gkba_batch::Group& g, int which) {
-    NvtxRange nr("gkba batch collision");
-    gkba_ctx* sh = g.sh;
-    const int N = g.N;
-    const long long NN = (long long)N * N;
+// The stacked (t_k, component) units of one collision of every member, per
+// group: each member's units padded to the group's quantum, a unit -> system
+// table on the device.
+struct CollisionPlan {
     struct Seg {
         gkba_ctx* c;
         int L;
@@ -1279,79 +1284,272 @@ gkba_status batch_collision(gkba_batch* b, gkba_batch::Group& g, int which) {
         long long nu;   // real units 2 L
         long long np;   // padded units
     };
-    std::vector<Seg> segs;
-    long long total = 0;
-    for (int m : g.members) {
-        gkba_ctx* c = b->ctx[m];
-        Seg s;
-        s.c = c;
-        s.L = which == 0 ? c->n + 1 : c->n + 2;
-        s.T = which == 0 ? c->T_a : c->T_b;
-        s.I = which == 0 ? c->Ia : c->Ib;
-        s.u0 = total;
-        s.nu = 2LL * s.L;
-        s.np = ((s.nu + g.pu - 1) / g.pu) * g.pu;
-        total += s.np;
-        GKBA_CUDA(sh, cudaMemsetAsync(s.I, 0, NN * sizeof(double2), sh->stream));
-        segs.push_back(s);
+    std::vector<std::vector<Seg>> segs;
+    std::vector<long long> total;
+    std::vector<int*> dev;
+};
+
+// Collision `which` of a step: L = n + 1 points with T = T_a (into Ia), or
+// n + 2 points with T = T_b (into Ib).  Zeroes the members' I.
+gkba_status plan_collision(gkba_batch* b, int which, CollisionPlan& P, bool zero_I = true) {
+    const int G = (int)b->groups.size();
+    P.segs.assign(G, {});
+    P.total.assign(G, 0);
+    P.dev.assign(G, nullptr);
+    for (int gi = 0; gi < G; ++gi) {
+        gkba_batch::Group& g = b->groups[gi];
+        gkba_ctx* sh = g.sh;
+        const long long NN = (long long)g.N * g.N;
+        for (int m : g.members) {
+            gkba_ctx* c = b->ctx[m];
+            CollisionPlan::Seg sg;
+            sg.c = c;
+            sg.L = which == 0 ? c->n + 1 : c->n + 2;
+            sg.T = which == 0 ? c->T_a : c->T_b;
+            sg.I = which == 0 ? c->Ia : c->Ib;
+            sg.u0 = P.total[gi];
+            sg.nu = 2LL * sg.L;
+            sg.np = ((sg.nu + g.pu - 1) / g.pu) * g.pu;
+            P.total[gi] += sg.np;
+            if (zero_I) GKBA_CUDA(sh, cudaMemsetAsync(sg.I, 0, NN * sizeof(double2), sh->stream));
+            P.segs[gi].push_back(sg);
+        }
+        const long long total = P.total[gi];
+        if (total > g.sys_cap) {
+            if (g.sys_dev) cudaFree(g.sys_dev);
+            for (int i = 0; i < 2; ++i)
+                if (g.sys_host[i]) cudaFreeHost(g.sys_host[i]);
+            g.sys_dev = nullptr;
+            g.sys_host[0] = g.sys_host[1] = nullptr;
+            g.sys_cap = 0;
+            // one device table per collision of a step (the first may still be read)
+            if (cudaMalloc(&g.sys_dev, 2 * total * sizeof(int)) != cudaSuccess ||
+                cudaMallocHost(&g.sys_host[0], total * sizeof(int)) != cudaSuccess ||
+                cudaMallocHost(&g.sys_host[1], total * sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(sh, GKBA_ENOMEM, "batch: unit table allocation failed");
+            }
+            g.sys_cap = total;
+        }
+        int* host = g.sys_host[which];
+        P.dev[gi] = g.sys_dev + (long long)which * g.sys_cap;
+        for (size_t i = 0; i < P.segs[gi].size(); ++i)
+            for (long long u = 0; u < P.segs[gi][i].np; ++u) host[P.segs[gi][i].u0 + u] = (int)i;
+        GKBA_CUDA(sh, cudaMemcpyAsync(P.dev[gi], host, total * sizeof(int), cudaMemcpyHostToDevice,
+                                      sh->stream));
     }
-    if (total > g.sys_cap) {
+    return GKBA_OK;
+}
+
+// Grow every group's unit tables to the larger collision of the coming step
+// (n + 2 points per member) before a graph capture, so that none is
+// allocated while the stream is captured.
+gkba_status ensure_tables(gkba_batch* b) {
+    for (auto& g : b->groups) {
+        long long total = 0;
+        for (int m : g.members)
+            total += ((2LL * (b->ctx[m]->n + 2) + g.pu - 1) / g.pu) * g.pu;
+        if (total <= g.sys_cap) continue;
         if (g.sys_dev) cudaFree(g.sys_dev);
         for (int i = 0; i < 2; ++i)
             if (g.sys_host[i]) cudaFreeHost(g.sys_host[i]);
         g.sys_dev = nullptr;
         g.sys_host[0] = g.sys_host[1] = nullptr;
         g.sys_cap = 0;
-        // one device table per collision of a step (the first may still be read)
         if (cudaMalloc(&g.sys_dev, 2 * total * sizeof(int)) != cudaSuccess ||
             cudaMallocHost(&g.sys_host[0], total * sizeof(int)) != cudaSuccess ||
             cudaMallocHost(&g.sys_host[1], total * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
-            return fail(sh, GKBA_ENOMEM, "batch: unit table allocation failed");
+            return fail(g.sh, GKBA_ENOMEM, "batch: unit table allocation failed");
         }
         g.sys_cap = total;
     }
-    int* host = g.sys_host[which];
-    int* dev = g.sys_dev + (long long)which * g.sys_cap;
-    for (size_t i = 0; i < segs.size(); ++i)
-        for (long long u = 0; u < segs[i].np; ++u) host[segs[i].u0 + u] = (int)i;
-    GKBA_CUDA(sh, cudaMemcpyAsync(dev, host, total * sizeof(int), cudaMemcpyHostToDevice, sh->stream));
-    const long long ub = sh->ub;
-    for (long long U0 = 0; U0 < total; U0 += ub) {
-        const long long nb = std::min(ub, total - U0);
-        for (auto& s : segs) {
-            const long long a = std::max(U0, s.u0), e = std::min(U0 + nb, s.u0 + s.np);
-            if (a >= e) continue;
-            const long long ra = a - s.u0, re = e - s.u0;  // units of this system in the batch
-            const long long off = a - U0;                  // their offset in the batch
-            const long long real_end = std::min(re, s.nu);
-            if (ra < real_end) {
-                const int k0 = (int)(ra / 2), nk = (int)((real_end - ra) / 2);
-                GKBA_TRY(units_from_history(sh, N, k0, nk, s.L, s.c->dt, s.c->rho_hist, s.T,
-                                            nullptr, sh->Su + off * NN, sh->Mb + off * NN,
-                                            sh->coef + off));
+    return GKBA_OK;
+}
+
+// Units per round of group g: the workspace's, or the autotuner's choice.
+long long round_units(const gkba_batch::Group& g) {
+    const gkba_ctx* sh = g.sh;
+    return sh->ub_limit > 0 ? std::min(sh->ub, sh->ub_limit) : sh->ub;
+}
+
+// Stage units [U0, U0 + nb) of group gi in its workspace (G, Gbar, weights,
+// forms) and point its unit table at them.
+gkba_status stage_round(gkba_batch* b, int gi, const CollisionPlan& P, long long U0, long long nb) {
+    gkba_batch::Group& g = b->groups[gi];
+    gkba_ctx* sh = g.sh;
+    const int N = g.N;
+    const long long NN = (long long)N * N;
+    for (const auto& sg : P.segs[gi]) {
+        const long long a = std::max(U0, sg.u0), e = std::min(U0 + nb, sg.u0 + sg.np);
+        if (a >= e) continue;
+        const long long ra = a - sg.u0, re = e - sg.u0;  // units of this system in the batch
+        const long long off = a - U0;                    // their offset in the batch
+        const long long real_end = std::min(re, sg.nu);
+        if (ra < real_end) {
+            const int k0 = (int)(ra / 2), nk = (int)((real_end - ra) / 2);
+            GKBA_TRY(units_from_history(sh, N, k0, nk, sg.L, sg.c->dt, sg.c->rho_hist, sg.T, nullptr,
+                                        sh->Su + off * NN, sh->Mb + off * NN, sh->coef + off));
+        }
+        const long long pad0 = std::max(ra, sg.nu);
+        if (pad0 < re) {
+            const long long po = off + (pad0 - ra), pn = re - pad0;
+            GKBA_CUDA(sh, cudaMemsetAsync(sh->Su + po * NN, 0, pn * NN * sizeof(double2), sh->stream));
+            GKBA_CUDA(sh, cudaMemsetAsync(sh->Mb + po * NN, 0, pn * NN * sizeof(double2), sh->stream));
+            GKBA_CUDA(sh, cudaMemsetAsync(sh->coef + po, 0, pn * sizeof(double), sh->stream));
+        }
+    }
+    GKBA_TRY(build_forms_tf32(sh, (int)nb, sh->Su, sh->Mb));
+    sh->unit_sys = P.dev[gi] + U0;
+    return GKBA_OK;
+}
+
+// Collision integrals of every member of every group over its own history.
+// The groups advance together in rounds: in each round every group with
+// units left stages its next batch, and one launch per stage covers the
+// batches of all of them (contract_batch_tf32_multi).
+gkba_status batch_collision(gkba_batch* b, int which) {
+    NvtxRange nr("gkba batch collision");
+    CollisionPlan P;
+    GKBA_TRY(plan_collision(b, which, P));
+    const int G = (int)b->groups.size();
+    std::vector<long long> U0(G, 0);
+    for (;;) {
+        std::vector<int> act;
+        for (int gi = 0; gi < G; ++gi)
+            if (U0[gi] < P.total[gi]) act.push_back(gi);
+        if (act.empty()) break;
+        for (size_t a0 = 0; a0 < act.size(); a0 += kMaxBatchLaunchGroups) {
+            const int na = (int)std::min<size_t>(kMaxBatchLaunchGroups, act.size() - a0);
+            gkba_ctx* cs[kMaxBatchLaunchGroups];
+            int nbs[kMaxBatchLaunchGroups];
+            for (int k = 0; k < na; ++k) {
+                const int gi = act[a0 + k];
+                const long long nb = std::min(round_units(b->groups[gi]), P.total[gi] - U0[gi]);
+                GKBA_TRY(stage_round(b, gi, P, U0[gi], nb));
+                cs[k] = b->groups[gi].sh;
+                nbs[k] = (int)nb;
             }
-            const long long pad0 = std::max(ra, s.nu);
-            if (pad0 < re) {
-                const long long po = off + (pad0 - ra), pn = re - pad0;
-                GKBA_CUDA(sh, cudaMemsetAsync(sh->Su + po * NN, 0, pn * NN * sizeof(double2), sh->stream));
-                GKBA_CUDA(sh, cudaMemsetAsync(sh->Mb + po * NN, 0, pn * NN * sizeof(double2), sh->stream));
-                GKBA_CUDA(sh, cudaMemsetAsync(sh->coef + po, 0, pn * sizeof(double), sh->stream));
+            const gkba_status st = contract_batch_tf32_multi(cs, nbs, na);
+            for (int k = 0; k < na; ++k) cs[k]->unit_sys = nullptr;
+            GKBA_TRY(st);
+            for (int k = 0; k < na; ++k) {
+                const int gi = act[a0 + k];
+                gkba_ctx* sh = cs[k];
+                const int N = b->groups[gi].N;
+                const long long NN = (long long)N * N;
+                const long long nb = nbs[k];
+                GKBA_TRY(zgemm_batched(sh, K_RED, N, 'N', 'N', make_double2(1.0, 0.0), sh->Su, NN, sh->Mb,
+                                       NN, make_double2(0.0, 0.0), sh->Yu, NN, (int)nb, 0));
+                for (const auto& sg : P.segs[gi]) {
+                    const long long a = std::max(U0[gi], sg.u0), e = std::min(U0[gi] + nb, sg.u0 + sg.nu);
+                    if (a >= e) continue;
+                    GKBA_TRY(weighted_sum_units(sh, N, (int)(e - a), sh->coef + (a - U0[gi]),
+                                                sh->Yu + (a - U0[gi]) * NN, sg.I));
+                }
+                U0[gi] += nb;
             }
         }
-        GKBA_TRY(build_forms_tf32(sh, (int)nb, sh->Su, sh->Mb));
-        sh->unit_sys = dev + U0;
-        const gkba_status st = contract_batch_tf32(sh, (int)nb);
-        sh->unit_sys = nullptr;
-        GKBA_TRY(st);
-        GKBA_TRY(zgemm_batched(sh, K_RED, N, 'N', 'N', make_double2(1.0, 0.0), sh->Su, NN, sh->Mb,
-                               NN, make_double2(0.0, 0.0), sh->Yu, NN, (int)nb, 0));
-        for (auto& s : segs) {
-            const long long a = std::max(U0, s.u0), e = std::min(U0 + nb, s.u0 + s.nu);
-            if (a >= e) continue;
-            GKBA_TRY(weighted_sum_units(sh, N, (int)(e - a), sh->coef + (a - U0),
-                                        sh->Yu + (a - U0) * NN, s.I));
+    }
+    return GKBA_OK;
+}
+
+// Device time per unit of one contraction round of group gi at the group's
+// current parameters: nb units of the plan, staged once, contracted twice
+// (the second run timed with events on the batch stream).
+gkba_status tune_round(gkba_batch* b, int gi, const CollisionPlan& P, long long nb, double* us_per_unit) {
+    gkba_ctx* sh = b->groups[gi].sh;
+    GKBA_TRY(stage_round(b, gi, P, 0, nb));
+    gkba_status st = contract_batch_tf32(sh, (int)nb);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == GKBA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        cudaGetLastError();
+        st = fail(sh, GKBA_ECUDA, "autotune: event creation failed");
+    }
+    if (st == GKBA_OK) {
+        cudaEventRecord(e0, sh->stream);
+        st = contract_batch_tf32(sh, (int)nb);
+        cudaEventRecord(e1, sh->stream);
+    }
+    sh->unit_sys = nullptr;
+    float ms = 0.0f;
+    if (st == GKBA_OK) {
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(sh, GKBA_ECUDA, "autotune: timing failed");
         }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    GKBA_TRY(st);
+    *us_per_unit = 1e3 * ms / (double)nb;
+    return GKBA_OK;
+}
+
+// Per group, a coordinate search over the launch parameters that change
+// neither the result beyond the split-TF32 tolerance nor the memory held:
+// the S4 work-item length (4096, 8192, 16384 K; fewer partial sums, fewer
+// and longer items), the accumulation window of the windowed stage kernel
+// (8 or 16 K, both within the tolerance), then the units per round (from
+// the workspace's down by halves while the stage launches keep two 256-row
+// tiles per cluster; smaller rounds keep the intermediates in L2).  The
+// fastest time per unit wins each coordinate.
+gkba_status autotune(gkba_batch* b) {
+    CollisionPlan P;
+    GKBA_TRY(plan_collision(b, 0, P, false));
+    for (int gi = 0; gi < (int)b->groups.size(); ++gi) {
+        gkba_batch::Group& g = b->groups[gi];
+        gkba_ctx* sh = g.sh;
+        const long long Np = sh->Np, N3 = Np * Np * Np;
+        const long long n0 = std::min<long long>(sh->ub, (P.total[gi] / g.pu) * g.pu);
+        if (n0 < g.pu) continue;
+        sh->ub_limit = 0;
+        double best = 0.0;
+        GKBA_TRY(tune_round(b, gi, P, n0, &best));
+        // S4 work-item length
+        if (N3 > kTcItemK) {
+            int best_kw = sh->fin_kw;
+            for (int kw : {kTcItemK, 2 * kTcItemK, 4 * kTcItemK}) {
+                if (kw == best_kw || kw > 2 * N3) continue;
+                const int keep = sh->fin_kw;
+                sh->fin_kw = kw;
+                double t = 0.0;
+                GKBA_TRY(tune_round(b, gi, P, n0, &t));
+                if (t < best) {
+                    best = t;
+                    best_kw = kw;
+                } else {
+                    sh->fin_kw = keep;
+                }
+            }
+            sh->fin_kw = best_kw;
+        }
+        // accumulation window of the windowed stage kernel (2 Np <= 96)
+        if (2 * Np <= 96) {
+            const int keep = sh->acc_window;
+            const int other = keep == 8 ? 16 : 8;
+            sh->acc_window = other;
+            double t = 0.0;
+            GKBA_TRY(tune_round(b, gi, P, n0, &t));
+            if (t < best) best = t;
+            else sh->acc_window = keep;
+        }
+        // units per round
+        // two 256-row tiles per cluster at least: nb Np^3 / 256 >= 2 clusters
+        const long long need = (2LL * sh->pair_clusters * 256 + N3 - 1) / N3;
+        const long long min_units = std::max<long long>(g.pu, (need + g.pu - 1) / g.pu * g.pu);
+        long long best_nb = n0;
+        for (long long nb = ((n0 / 2) / g.pu) * g.pu; nb >= min_units; nb = ((nb / 2) / g.pu) * g.pu) {
+            double t = 0.0;
+            GKBA_TRY(tune_round(b, gi, P, nb, &t));
+            if (t < best) {
+                best = t;
+                best_nb = nb;
+            }
+            if (nb == g.pu) break;
+        }
+        sh->ub_limit = best_nb < sh->ub ? (int)best_nb : 0;
+        g.us_per_unit = best;
     }
     return GKBA_OK;
 }
@@ -1365,7 +1563,7 @@ gkba_status batch_step(gkba_batch* b, const double* E_n, const double* E_np1,
         const long long NN = (long long)c->N * c->N;
         GKBA_TRY(h_hf(c, E_n[i], c->rho_hist + c->n * NN, c->hhf_n));
     }
-    for (auto& g : b->groups) GKBA_TRY(batch_collision(b, g, 0));
+    GKBA_TRY(batch_collision(b, 0));
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         gkba_ctx* c = b->ctx[i];
         const int n = c->n;
@@ -1387,7 +1585,7 @@ gkba_status batch_step(gkba_batch* b, const double* E_n, const double* E_np1,
                                NN, make_double2(0.0, 0.0), c->T_b, NN, n + 1, 0));
         GKBA_TRY(set_identity(c, c->T_b + (n + 1) * NN, 1));
     }
-    for (auto& g : b->groups) GKBA_TRY(batch_collision(b, g, 1));
+    GKBA_TRY(batch_collision(b, 1));
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         gkba_ctx* c = b->ctx[i];
         const int n = c->n;
@@ -1538,7 +1736,57 @@ gkba_status gkba_batch_step(gkba_batch* b, const double* E_n, const double* E_np
     gkba_status st;
     {
         NvtxRange nr("gkba_batch_step");
-        st = batch_step(b, E_n, E_np1, rho_out, diag_out);
+        if (b->use_graph) {
+            // capture the step's device work and launch it as one graph; the
+            // previous step's executable graph is updated in place when the
+            // launch sequence kept its shape, else instantiated anew
+            st = ensure_tables(b);
+            if (st == GKBA_OK) {
+                if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                    cudaGetLastError();
+                    st = batch_fail(b, GKBA_ECUDA, "gkba_batch_step: stream capture could not begin");
+                } else {
+                    st = batch_step(b, E_n, E_np1, rho_out, diag_out);
+                    cudaGraph_t graph = nullptr;
+                    const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+                    if (st == GKBA_OK && ce != cudaSuccess) {
+                        cudaGetLastError();
+                        st = batch_fail(b, GKBA_ECUDA, "gkba_batch_step: stream capture failed: %s",
+                                        cudaGetErrorString(ce));
+                    }
+                    if (st == GKBA_OK) {
+                        bool ok = false;
+                        if (b->gexec) {
+                            cudaGraphExecUpdateResultInfo info;
+                            ok = cudaGraphExecUpdate(b->gexec, graph, &info) == cudaSuccess;
+                            if (!ok) {
+                                cudaGetLastError();
+                                cudaGraphExecDestroy(b->gexec);
+                                b->gexec = nullptr;
+                            }
+                        }
+                        if (!ok) {
+                            ++b->graph_rebuilds;
+                            if (cudaGraphInstantiate(&b->gexec, graph, 0) != cudaSuccess) {
+                                cudaGetLastError();
+                                b->gexec = nullptr;
+                                st = batch_fail(b, GKBA_ECUDA, "gkba_batch_step: graph instantiation failed");
+                            }
+                        }
+                        if (st == GKBA_OK) {
+                            if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) {
+                                cudaGetLastError();
+                                st = batch_fail(b, GKBA_ECUDA, "gkba_batch_step: graph launch failed");
+                            }
+                            ++b->graph_steps;
+                        }
+                    }
+                    if (graph) cudaGraphDestroy(graph);
+                }
+            }
+        } else {
+            st = batch_step(b, E_n, E_np1, rho_out, diag_out);
+        }
     }
     const cudaError_t se = cudaStreamSynchronize(b->stream);
     for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->stream = saved[i];
@@ -1571,5 +1819,56 @@ const char* gkba_batch_last_error(const gkba_batch* b) {
 }
 
 void gkba_batch_destroy(gkba_batch* b) { free_batch(b); }
+
+gkba_status gkba_batch_set_options(gkba_batch* b, int use_graph) {
+    if (!b) return batch_fail(nullptr, GKBA_EINVAL, "gkba_batch_set_options: NULL batch");
+    if (use_graph != 0 && use_graph != 1)
+        return batch_fail(b, GKBA_EINVAL, "gkba_batch_set_options: use_graph must be 0 or 1");
+    b->use_graph = use_graph != 0;
+    return GKBA_OK;
+}
+
+gkba_status gkba_batch_autotune(gkba_batch* b, int* n_groups, int* N_out, int* units, int* acc_window,
+                                int* s4_item_k, double* us_per_unit) {
+    if (!b) return batch_fail(nullptr, GKBA_EINVAL, "gkba_batch_autotune: NULL batch");
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+        cudaGetLastError();
+        return batch_fail(b, GKBA_ECUDA, "gkba_batch_autotune: cudaSetDevice failed");
+    }
+    std::vector<cudaStream_t> saved(b->ctx.size());
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        cudaStreamSynchronize(b->ctx[i]->stream);
+        saved[i] = b->ctx[i]->stream;
+        b->ctx[i]->stream = b->stream;
+    }
+    gkba_status st = autotune(b);
+    const cudaError_t se = cudaStreamSynchronize(b->stream);
+    for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->stream = saved[i];
+    if (st != GKBA_OK) {
+        for (auto& g : b->groups)
+            if (!g.sh->err.empty()) b->err = g.sh->err;
+        return st;
+    }
+    if (se != cudaSuccess) return batch_fail(b, GKBA_ECUDA, "gkba_batch_autotune: %s", cudaGetErrorString(se));
+    for (auto& g : b->groups) {
+        int errw = 0;
+        if (cudaMemcpy(&errw, g.sh->dint + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return batch_fail(b, GKBA_ECUDA, "gkba_batch_autotune: error word read failed");
+        if (errw != 0) {
+            cudaMemset(g.sh->dint + 1, 0, sizeof(int));
+            return batch_fail(b, GKBA_ETIMEOUT, "gkba_batch_autotune: device-side wait timed out (code %d)", errw);
+        }
+    }
+    if (n_groups) *n_groups = (int)b->groups.size();
+    for (size_t gi = 0; gi < b->groups.size() && gi < (size_t)kMaxBatchLaunchGroups; ++gi) {
+        const auto& g = b->groups[gi];
+        if (N_out) N_out[gi] = g.N;
+        if (units) units[gi] = (int)round_units(g);
+        if (acc_window) acc_window[gi] = g.sh->acc_window;
+        if (s4_item_k) s4_item_k[gi] = g.sh->fin_kw;
+        if (us_per_unit) us_per_unit[gi] = g.us_per_unit;
+    }
+    return GKBA_OK;
+}
 
 }  // extern "C"

@@ -117,6 +117,8 @@ struct gkba_ctx {
     size_t ws_bytes = 0;
     int ub = 0;                  // units per batch
     int ub_cap = 0;              // units the workspace was sized for
+    int ub_limit = 0;            // stacked batches: units per round chosen by the autotuner (0: ub)
+    int fin_kw = 4096;           // K length of an S4 work item (a multiple of 4096)
     // sub-buffers inside ws
     void* X13 = nullptr;
     size_t x13_bytes = 0;
@@ -264,6 +266,8 @@ gkba_status vbar_slot_tf32(gkba_ctx* c, int nb, const double2* Sbar, int transpo
 gkba_status tl_terms_tf32(gkba_ctx* c, int nb, const double2* Gb, int k0, double w_first,
                           double w_rest, double* D);
 gkba_status tl_apply_tf32(gkba_ctx* c, const double2* W, const double* lam);
+// Several contexts' batches in one launch per stage (forms built; shared stream).
+gkba_status contract_batch_tf32_multi(gkba_ctx* const* cs, const int* nbs, int n);
 gkba_status fp64_prepare_model(gkba_ctx* c);  // build wS64, vK64, hfK
 
 // Per-unit operand forms for a batch: units u = 0..nb-1 given (G_u, Gb_u) pointers

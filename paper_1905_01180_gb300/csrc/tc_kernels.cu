@@ -113,11 +113,6 @@ __device__ __forceinline__ uint32_t cluster_id_x() {
     asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
     return r;
 }
-__device__ __forceinline__ uint32_t cluster_count_x() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
 // Shared::cluster address of the same shared variable in CTA `rank` of the cluster.
 __device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
     uint32_t r;
@@ -342,6 +337,19 @@ struct StageParams {
     int as2;           // windowed: ring stride in columns (2 Np rounded up to 32)
 };
 
+// One launch of the stage kernel: up to kMaxLaunchGroups groups (problems of
+// different Np or operands), each with its own parameters and tensor maps; the
+// clusters [cl_begin[g], cl_begin[g + 1]) of the grid work on group g.
+constexpr int kMaxLaunchGroups = 8;
+struct StageLaunch {
+    CUtensorMap tmA[kMaxLaunchGroups];
+    CUtensorMap tmBhi[kMaxLaunchGroups];
+    CUtensorMap tmBlo[kMaxLaunchGroups];
+    StageParams p[kMaxLaunchGroups];
+    int cl_begin[kMaxLaunchGroups + 1];
+    int ngroups;
+};
+
 // Output address of row `row` of unit u through the stage's map (rows below
 // 2^31: 32-bit unsigned division).
 __device__ __forceinline__ float* stage_out_row(const StageParams& p, int u, uint32_t row) {
@@ -385,10 +393,19 @@ constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-
 // ---------------------------------------------------------------------------
 template <bool SPLIT_ACC>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
-    k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-              const __grid_constant__ CUtensorMap tmBlo, const StageParams p) {
+    k_tc_pair(const __grid_constant__ StageLaunch L) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // the group this cluster works on: the launch's clusters are split between
+    // its groups (problems of different Np or operands), each runs the
+    // pipeline below with its own parameters and tensor maps
+    const int cid_all = (int)cluster_id_x();
+    int grp = 0;
+    while (grp + 1 < L.ngroups && cid_all >= L.cl_begin[grp + 1]) ++grp;
+    const StageParams& p = L.p[grp];
+    const CUtensorMap* tmA = &L.tmA[grp];
+    const CUtensorMap* tmBhi = &L.tmBhi[grp];
+    const CUtensorMap* tmBlo = &L.tmBlo[grp];
     const int Np = p.Np;
     const int nchunk = p.planes * p.kch;                // K-chunks per tile
     const uint32_t chunkB = (uint32_t)(Np * 128);       // one K-chunk of this CTA's Np B rows
@@ -435,9 +452,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
         fence_barrier_init();
     }
     if (warp == 0 && lane == 0) {
-        prefetch_tmap(&tmA);
-        prefetch_tmap(&tmBhi);
-        prefetch_tmap(&tmBlo);
+        prefetch_tmap(tmA);
+        prefetch_tmap(tmBhi);
+        prefetch_tmap(tmBlo);
     }
     if (warp == 1) {
         tmem_alloc_pair(smem_u32(tmem_slot), 512);
@@ -463,7 +480,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
     // unsigned division, a short instruction sequence, in the per-tile paths
     const uint32_t ipu32 = (uint32_t)ipu;
     const long long total = (long long)p.units * ipu;
-    const long long ncl = cluster_count_x(), cid = cluster_id_x();
+    const long long ncl = L.cl_begin[grp + 1] - L.cl_begin[grp], cid = cid_all - L.cl_begin[grp];
     const long long t0 = total * cid / ncl;
     const long long t1 = total * (cid + 1) / ncl;
 
@@ -486,8 +503,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     for (int c = 0; c < nchunk; ++c) {
                         const int pl = c / p.kch, kc = c % p.kch;
                         const int y = (pl * 2 + (int)rank) * Np;
-                        tma_3d(smem_u32(sBhi + c * chunkB), &tmBhi, bar(BFULL), kc * kKC, y, u);
-                        tma_3d(smem_u32(sBlo + c * chunkB), &tmBlo, bar(BFULL), kc * kKC, y, u);
+                        tma_3d(smem_u32(sBhi + c * chunkB), tmBhi, bar(BFULL), kc * kKC, y, u);
+                        tma_3d(smem_u32(sBlo + c * chunkB), tmBlo, bar(BFULL), kc * kKC, y, u);
                     }
                     loaded_b = true;
                     cur_u = u;
@@ -499,9 +516,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                     if (!mbar_wait_cl(bar(AEMPTY + s), ph ^ 1, abort_flag, peer_abort, p.err, 2)) { ok = false; break; }
                     mbar_expect_tx(bar(AFULL + s), kTileBytes);
                     const uint32_t dst = smem_u32(sA + s * kTileBytes);
-                    if (p.a_unit) tma_4d(dst, &tmA, bar(AFULL + s), kc * kKC, pl, (int)row0, u);
-                    else if (p.unit_sys) tma_3d(dst, &tmA, bar(AFULL + s), kc * kKC, (int)row0, p.unit_sys[u]);
-                    else tma_2d(dst, &tmA, bar(AFULL + s), kc * kKC, (int)row0);
+                    if (p.a_unit) tma_4d(dst, tmA, bar(AFULL + s), kc * kKC, pl, (int)row0, u);
+                    else if (p.unit_sys) tma_3d(dst, tmA, bar(AFULL + s), kc * kKC, (int)row0, p.unit_sys[u]);
+                    else tma_2d(dst, tmA, bar(AFULL + s), kc * kKC, (int)row0);
                 }
             }
             if (*abort_flag) {
@@ -856,6 +873,16 @@ struct FinalParams {
 
 constexpr int kFinThreads = 448;  // 14 warps: see the S4 kernel
 
+// One launch of the S4 kernel over up to kMaxLaunchGroups groups (see StageLaunch).
+struct FinalLaunch {
+    CUtensorMap tmA[kMaxLaunchGroups];
+    CUtensorMap tmBhi[kMaxLaunchGroups];
+    CUtensorMap tmBlo[kMaxLaunchGroups];
+    FinalParams p[kMaxLaunchGroups];
+    int cl_begin[kMaxLaunchGroups + 1];
+    int ngroups;
+};
+
 // ---------------------------------------------------------------------------
 // Stage S4 on CTA pairs: D[(u,c,j)][i] = sum_K X3[(u,c,j)][K] vK[i][K].
 //
@@ -919,10 +946,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
-    k_tc_final_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-                    const __grid_constant__ CUtensorMap tmBlo, const FinalParams p) {
+    k_tc_final_pair(const __grid_constant__ FinalLaunch L) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // the group this cluster works on (see StageLaunch)
+    const int cid_all = (int)cluster_id_x();
+    int grp = 0;
+    while (grp + 1 < L.ngroups && cid_all >= L.cl_begin[grp + 1]) ++grp;
+    const FinalParams& p = L.p[grp];
+    const CUtensorMap* tmA = &L.tmA[grp];
+    const CUtensorMap* tmBhi = &L.tmBhi[grp];
+    const CUtensorMap* tmBlo = &L.tmBlo[grp];
     const int Np = p.Np, Nh = Np / 2;
     const uint32_t AS = (uint32_t)((Np + 31) & ~31);  // window accumulator stride in columns
     const uint32_t bbytes = (uint32_t)(Nh * 128);     // this CTA's B rows, one 32-wide box
@@ -957,9 +991,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
         fence_barrier_init();
     }
     if (warp == 0 && lane == 0) {
-        prefetch_tmap(&tmA);
-        prefetch_tmap(&tmBhi);
-        prefetch_tmap(&tmBlo);
+        prefetch_tmap(tmA);
+        prefetch_tmap(tmBhi);
+        prefetch_tmap(tmBlo);
     }
     if (warp == 1) {
         tmem_alloc_pair(smem_u32(tmem_slot), 512);
@@ -971,7 +1005,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const long long items = (long long)p.ngroups * p.nks;
-    const long long ncl = cluster_count_x(), cid = cluster_id_x();
+    const long long ncl = L.cl_begin[grp + 1] - L.cl_begin[grp], cid = cid_all - L.cl_begin[grp];
     // epilogue role e = 4 h + quarter: warps 8-11 (h = 0), 12, 13, 2, 3 (h = 1)
     const int epi = warp >= 8 ? warp - 8 : (warp == 2 || warp == 3) ? warp + 4 : -1;
 
@@ -993,14 +1027,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                     if (!mbar_wait_cl(bar(EMPTY + s), st.ph ^ 1, abort_flag, peer_abort, p.err, 11)) { ok = false; break; }
                     mbar_expect_tx(bar(FULL + s), stage_bytes);
                     const int kh = (int)k;
-                    if (p.blocked) tma_3d(smem_u32(stA(s)), &tmA, bar(FULL + s), 0, row0, kh >> 5);
-                    else tma_2d(smem_u32(stA(s)), &tmA, bar(FULL + s), kh, row0);
+                    if (p.blocked) tma_3d(smem_u32(stA(s)), tmA, bar(FULL + s), 0, row0, kh >> 5);
+                    else tma_2d(smem_u32(stA(s)), tmA, bar(FULL + s), kh, row0);
                     if (p.unit_sys) {
-                        tma_3d(smem_u32(stBhi(s)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh, sys);
-                        tma_3d(smem_u32(stBlo(s)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh, sys);
+                        tma_3d(smem_u32(stBhi(s)), tmBhi, bar(FULL + s), kh, (int)rank * Nh, sys);
+                        tma_3d(smem_u32(stBlo(s)), tmBlo, bar(FULL + s), kh, (int)rank * Nh, sys);
                     } else {
-                        tma_2d(smem_u32(stBhi(s)), &tmBhi, bar(FULL + s), kh, (int)rank * Nh);
-                        tma_2d(smem_u32(stBlo(s)), &tmBlo, bar(FULL + s), kh, (int)rank * Nh);
+                        tma_2d(smem_u32(stBhi(s)), tmBhi, bar(FULL + s), kh, (int)rank * Nh);
+                        tma_2d(smem_u32(stBlo(s)), tmBlo, bar(FULL + s), kh, (int)rank * Nh);
                     }
                 }
             }
@@ -1238,7 +1272,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
     volatile int* abort_flag = &abort_s;
     const uint32_t rank = cluster_rank();
     const uint32_t peer_abort = mapa_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < (kRateN / 2) * 32; i += blockDim.x)
         reinterpret_cast<float*>(sB)[i] = 0.0f;
     if (threadIdx.x == 0) {
@@ -1683,91 +1717,208 @@ static StageParams stage_base(gkba_ctx* c, int nb) {
     return sp;
 }
 
-// Persistent grid of a stage launch: one CTA pair per resident cluster, at
-// most one per 256-row tile.
-static int stage_grid(gkba_ctx* c, int nb) {
-    // callers keep nb * Np^3 / 256 below 2^31 (the kernel's 32-bit tile index):
-    // nb is at most the workspace's units, far below 2^31 / 3456 at N = 96
-    const long long pair_tiles = (long long)nb * ((long long)c->Np * c->Np * c->Np / kBM) / 2;
-    return 2 * (int)(pair_tiles < c->pair_clusters ? pair_tiles : c->pair_clusters);
+// ---------------------------------------------------------------------------
+// Launch plans: the tensor maps and parameters of one stage of one problem.
+// A launch takes up to kMaxLaunchGroups plans (problems of different Np or
+// operands, e.g. the basis-size groups of a stacked batch) and splits its
+// clusters between them by their estimated cost.
+// ---------------------------------------------------------------------------
+struct StagePlan {
+    CUtensorMap mA, mBh, mBl;
+    StageParams sp;
+    long long pair_tiles;  // 256-row tiles (an upper bound for the group's clusters)
+    double weight;         // relative cost for the cluster split
+    double flops, bytes;   // algorithmic counts for the statistics
+    int cls;
+};
+struct FinalPlan {
+    CUtensorMap mA, mBh, mBl;
+    FinalParams fp;
+    long long items;
+    double weight, flops, bytes;
+};
+
+// Relative cost of a stage: the pair's MMA issue sets the pace, three MMAs per
+// K step at about 85 clocks each up to N = 128 columns and proportionally
+// more beyond (measured with the rate probe), plus a per-tile epilogue share.
+static double stage_weight(const StageParams& sp, long long pair_tiles) {
+    const int ksteps = sp.planes * ((sp.Np + 7) / 8);
+    const double per_mma = std::max(1.0, 2.0 * sp.Np / 128.0);
+    return (double)pair_tiles * (3.0 * ksteps * per_mma + 8.0);
 }
 
-// Stage S4 and the reduction of nb units whose X3 stages S1-S3 (or the
-// time-linear back-transforms) left in X13: S_u -> c->Su.
-static gkba_status tf32_final(gkba_ctx* c, int nb) {
+// Split `avail` clusters between n groups in proportion to w (at least one
+// each, at most cap[g] useful): cl_begin[0..n]; returns the clusters used.
+static int split_clusters(int avail, const double* w, const long long* cap, int n, int* cl_begin) {
+    int cl[kMaxLaunchGroups];
+    double W = 0.0;
+    for (int g = 0; g < n; ++g) W += w[g];
+    int used = 0;
+    for (int g = 0; g < n; ++g) {
+        const long long want = W > 0.0 ? (long long)(avail * w[g] / W) : 1;
+        cl[g] = (int)std::max(1LL, std::min(cap[g], want));
+        used += cl[g];
+    }
+    // hand out what rounding left, to the groups with the most work per cluster
+    while (used < avail) {
+        int best = -1;
+        double bw = 0.0;
+        for (int g = 0; g < n; ++g)
+            if (cl[g] < cap[g] && w[g] / cl[g] > bw) {
+                bw = w[g] / cl[g];
+                best = g;
+            }
+        if (best < 0) break;
+        ++cl[best];
+        ++used;
+    }
+    // more groups than clusters can hold cannot occur (n <= 8 < clusters); trim otherwise
+    while (used > avail) {
+        int best = 0;
+        for (int g = 1; g < n; ++g)
+            if (cl[g] > cl[best]) best = g;
+        if (cl[best] == 1) break;
+        --cl[best];
+        --used;
+    }
+    cl_begin[0] = 0;
+    for (int g = 0; g < n; ++g) cl_begin[g + 1] = cl_begin[g] + cl[g];
+    return cl_begin[n];
+}
+
+// One launch of the stage kernel over n plans (same precision mode).
+static gkba_status launch_stage_group(gkba_ctx* c, const StagePlan* const* plans, int n, int cls) {
+    if (n < 1 || n > kMaxLaunchGroups) return fail(c, GKBA_EINVAL, "stage launch of %d groups", n);
+    StageLaunch L{};
+    double w[kMaxLaunchGroups];
+    long long cap[kMaxLaunchGroups];
+    size_t smem = 0;
+    double fl = 0.0, by = 0.0;
+    for (int g = 0; g < n; ++g) {
+        L.tmA[g] = plans[g]->mA;
+        L.tmBhi[g] = plans[g]->mBh;
+        L.tmBlo[g] = plans[g]->mBl;
+        L.p[g] = plans[g]->sp;
+        w[g] = plans[g]->weight;
+        cap[g] = std::max(1LL, plans[g]->pair_tiles);
+        smem = std::max(smem, stage_smem_bytes(plans[g]->sp.Np));
+        fl += plans[g]->flops;
+        by += plans[g]->bytes;
+    }
+    L.ngroups = n;
+    const int ncl = split_clusters(c->pair_clusters, w, cap, n, L.cl_begin);
+    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_pair<true> : k_tc_pair<false>;
+    auto t = launch_begin(c, cls, fl, by);
+    stage_kernel<<<2 * ncl, kStageThreads, smem, c->stream>>>(L);
+    return launch_end(c, t);
+}
+
+static gkba_status launch_final_group(gkba_ctx* c, const FinalPlan* const* plans, int n) {
+    if (n < 1 || n > kMaxLaunchGroups) return fail(c, GKBA_EINVAL, "S4 launch of %d groups", n);
+    FinalLaunch L{};
+    double w[kMaxLaunchGroups];
+    long long cap[kMaxLaunchGroups];
+    size_t smem = 0;
+    double fl = 0.0, by = 0.0;
+    for (int g = 0; g < n; ++g) {
+        L.tmA[g] = plans[g]->mA;
+        L.tmBhi[g] = plans[g]->mBh;
+        L.tmBlo[g] = plans[g]->mBl;
+        L.p[g] = plans[g]->fp;
+        w[g] = plans[g]->weight;
+        cap[g] = std::max(1LL, plans[g]->items);
+        smem = std::max(smem, final_pair_smem_bytes(plans[g]->fp.Np));
+        fl += plans[g]->flops;
+        by += plans[g]->bytes;
+    }
+    L.ngroups = n;
+    const int ncl = split_clusters(c->fin_pair_clusters, w, cap, n, L.cl_begin);
+    auto t = launch_begin(c, K_FIN, fl, by);
+    k_tc_final_pair<<<2 * ncl, kFinThreads, smem, c->stream>>>(L);
+    return launch_end(c, t);
+}
+
+// Plan of stage S4 for nb units whose X3 stages S1-S3 (or the time-linear
+// back-transforms) left in X13.
+static gkba_status plan_final(gkba_ctx* c, int nb, FinalPlan& F) {
     const int Np = c->Np;
     const long long N2 = (long long)Np * Np, N3 = N2 * Np, N4 = N3 * Np;
     float* X13 = (float*)c->X13;
-    int* err = c->dint + 1;
     const double Nr = c->N;
     const double fl_cr = 4.0 * Nr * Nr * Nr * Nr * Nr;
     const double N4r = Nr * Nr * Nr * Nr;
     const bool multi = c->unit_sys != nullptr;
     const long long rows = 2LL * Np * nb;
     const bool blocked = (Np % 32) == 0;
-    CUtensorMap mAf, mVh, mVl;
     if (blocked) {
         const long long Rl = ((2LL * Np * nb + 2 * kBM - 1) / (2 * kBM)) * (2 * kBM);
         cuuint64_t d[3] = {32, (cuuint64_t)Rl, (cuuint64_t)(N3 / 32)};
         cuuint64_t s[2] = {32 * 4, (cuuint64_t)(Rl * 32 * 4)};
         cuuint32_t b[3] = {kKC, kBM, 1};
-        GKBA_TRY(make_map(c, &mAf, X13, 3, d, s, b));
+        GKBA_TRY(make_map(c, &F.mA, X13, 3, d, s, b));
     } else {
         cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)(2LL * Np * nb)};
         cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
         cuuint32_t b[2] = {kKC, kBM};
-        GKBA_TRY(make_map(c, &mAf, X13, 2, d, s, b));
+        GKBA_TRY(make_map(c, &F.mA, X13, 2, d, s, b));
     }
     if (multi) {
         cuuint64_t d[3] = {(cuuint64_t)N3, (cuuint64_t)Np, (cuuint64_t)c->nsys};
         cuuint64_t s[2] = {(cuuint64_t)N3 * 4, (cuuint64_t)(N4 * 4)};
         cuuint32_t b[3] = {kKC, (cuuint32_t)(Np / 2), 1};
-        GKBA_TRY(make_map(c, &mVh, c->vKhi, 3, d, s, b));
-        GKBA_TRY(make_map(c, &mVl, c->vKlo, 3, d, s, b));
+        GKBA_TRY(make_map(c, &F.mBh, c->vKhi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &F.mBl, c->vKlo, 3, d, s, b));
     } else {
         // each CTA of an S4 pair loads Np/2 rows of vK
         cuuint64_t d[2] = {(cuuint64_t)N3, (cuuint64_t)Np};
         cuuint64_t s[1] = {(cuuint64_t)N3 * 4};
         cuuint32_t b[2] = {kKC, (cuuint32_t)(Np / 2)};
-        GKBA_TRY(make_map(c, &mVh, c->vKhi, 2, d, s, b));
-        GKBA_TRY(make_map(c, &mVl, c->vKlo, 2, d, s, b));
+        GKBA_TRY(make_map(c, &F.mBh, c->vKhi, 2, d, s, b));
+        GKBA_TRY(make_map(c, &F.mBl, c->vKlo, 2, d, s, b));
     }
     // split-K over (n,r,p)
-    FinalParams fp{};
+    FinalParams& fp = F.fp;
+    fp = FinalParams{};
     fp.Np = Np;
     fp.K = N3;
     fp.KS = c->acc_window;
-    fp.KW = kTcItemK;
+    fp.KW = c->fin_kw >= kTcItemK ? c->fin_kw : kTcItemK;
     fp.nks = (int)((N3 + fp.KW - 1) / fp.KW);
     fp.rows = rows;
     fp.ngroups = (int)((rows + 2 * kBM - 1) / (2 * kBM));
     fp.Rld = (long long)fp.ngroups * 2 * kBM;
     fp.blocked = blocked ? 1 : 0;
     fp.part = (float*)c->part;
-    fp.err = err;
+    fp.err = c->dint + 1;
     fp.unit_sys = c->unit_sys;
     if ((size_t)fp.nks * Np * fp.Rld * 4 > c->part_bytes)
         return fail(c, GKBA_ESTATE, "partial buffer too small");
-    {
-        const long long items = (long long)fp.ngroups * fp.nks;
-        const int g = 2 * (int)(items < c->fin_pair_clusters ? items : c->fin_pair_clusters);
-        auto t = launch_begin(c, K_FIN, fl_cr * nb, 4.0 * (2 * N4r * nb + 2 * N4r));
-        k_tc_final_pair<<<g, kFinThreads, final_pair_smem_bytes(Np), c->stream>>>(mAf, mVh, mVl, fp);
-        GKBA_TRY(launch_end(c, t));
-    }
-    return reduce_partials_launch(c, nb, fp.nks, (long long)Np * fp.Rld, fp.Rld, c->part, true, c->Su);
+    F.items = (long long)fp.ngroups * fp.nks;
+    F.weight = (double)F.items * (Np + 32);
+    F.flops = fl_cr * nb;
+    F.bytes = 4.0 * (2 * N4r * nb + 2 * N4r);
+    return GKBA_OK;
 }
 
-// Stages S1-S3 of one batch (forms built) with A1 as S1's A operand (wS32,
-// or the omega layout of v for dL/dv): X3 lands in X13, K-blocked when
-// Np % 32 == 0.  With do_final, stage S4 and the reduction follow: S_u -> c->Su.
-static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_final) {
+// Stage S4 and the reduction of nb units whose X3 stages S1-S3 (or the
+// time-linear back-transforms) left in X13: S_u -> c->Su.
+static gkba_status tf32_final(gkba_ctx* c, int nb) {
+    FinalPlan F;
+    GKBA_TRY(plan_final(c, nb, F));
+    const FinalPlan* fpl = &F;
+    GKBA_TRY(launch_final_group(c, &fpl, 1));
+    return reduce_partials_launch(c, nb, F.fp.nks, (long long)c->Np * F.fp.Rld, F.fp.Rld, c->part, true,
+                                  c->Su);
+}
+
+// Plans of stages S1-S3 of one batch (forms built) with A1 as S1's A operand
+// (wS32, or the omega layout of v for dL/dv): X3 lands in X13, K-blocked when
+// Np % 32 == 0.
+static gkba_status plan_chain(gkba_ctx* c, int nb, const float* A1, StagePlan (&P)[3]) {
     const int Np = c->Np;
     const long long N2 = (long long)Np * Np, N3 = N2 * Np, N4 = N3 * Np;
     if ((long long)nb * (N3 / kBM) >= (1LL << 31))
         return fail(c, GKBA_EINVAL, "%d units exceed the stage kernel's 32-bit tile index", nb);
-    const int kch = (Np + kKC - 1) / kKC;
-    const int mtiles = (int)(N3 / kBM);
     float* X13 = (float*)c->X13;
     float* X2 = (float*)c->X2;
     const long long per = 2LL * Np * Np;
@@ -1777,49 +1928,45 @@ static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_fina
     float* Gslo = Gshi + 2 * per * c->ub_cap;
     float* G3hi = (float*)(c->sep_A ? c->formsG3 : c->formsG);  // stage S3's slot
     float* G3lo = G3hi + 2 * per * c->ub_cap;
-    int* err = c->dint + 1;
     // Flops below are the algorithmic counts of the N-basis problem (padding excluded).
     const double Nr = c->N;
     const double fl_cr = 4.0 * Nr * Nr * Nr * Nr * Nr, fl_cc = 2.0 * fl_cr;
     const double N4r = Nr * Nr * Nr * Nr;
 
-    CUtensorMap mA1, mA23_in1, mA23_in2, mB1h, mB1l, mGh, mGl, mG3h, mG3l;
     const bool multi = c->unit_sys != nullptr;  // several systems: w and v per system
     if (multi) {
         cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)N3, (cuuint64_t)c->nsys};
         cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)(N4 * 4)};
         cuuint32_t b[3] = {kKC, kBM, 1};
-        GKBA_TRY(make_map(c, &mA1, A1, 3, d, s, b));
+        GKBA_TRY(make_map(c, &P[0].mA, A1, 3, d, s, b));
     } else {
         cuuint64_t d[2] = {(cuuint64_t)Np, (cuuint64_t)N3};
         cuuint64_t s[1] = {(cuuint64_t)Np * 4};
         cuuint32_t b[2] = {kKC, kBM};
-        GKBA_TRY(make_map(c, &mA1, A1, 2, d, s, b));
+        GKBA_TRY(make_map(c, &P[0].mA, A1, 2, d, s, b));
     }
     {
         cuuint64_t d[4] = {(cuuint64_t)Np, 2, (cuuint64_t)N3, (cuuint64_t)nb};
         cuuint64_t s[3] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * Np * 4, (cuuint64_t)(2 * N4 * 4)};
         cuuint32_t b[4] = {kKC, 1, kBM, 1};
-        GKBA_TRY(make_map(c, &mA23_in1, X13, 4, d, s, b));
-        GKBA_TRY(make_map(c, &mA23_in2, X2, 4, d, s, b));
+        GKBA_TRY(make_map(c, &P[1].mA, X13, 4, d, s, b));
+        GKBA_TRY(make_map(c, &P[2].mA, X2, 4, d, s, b));
     }
     {
         // B1[u][(c,r)][s]; Gs[u][4 blocks][p][q]; each CTA of a pair loads Np rows
         cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)2 * Np, (cuuint64_t)nb};
         cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)per * 4};
         cuuint32_t b[3] = {kKC, (cuuint32_t)Np, 1};
-        GKBA_TRY(make_map(c, &mB1h, B1hi, 3, d, s, b));
-        GKBA_TRY(make_map(c, &mB1l, B1lo, 3, d, s, b));
+        GKBA_TRY(make_map(c, &P[0].mBh, B1hi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &P[0].mBl, B1lo, 3, d, s, b));
         cuuint64_t dg[3] = {(cuuint64_t)Np, (cuuint64_t)4 * Np, (cuuint64_t)nb};
         cuuint64_t sg[2] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * per * 4};
-        GKBA_TRY(make_map(c, &mGh, Gshi, 3, dg, sg, b));
-        GKBA_TRY(make_map(c, &mGl, Gslo, 3, dg, sg, b));
-        GKBA_TRY(make_map(c, &mG3h, G3hi, 3, dg, sg, b));
-        GKBA_TRY(make_map(c, &mG3l, G3lo, 3, dg, sg, b));
+        GKBA_TRY(make_map(c, &P[1].mBh, Gshi, 3, dg, sg, b));
+        GKBA_TRY(make_map(c, &P[1].mBl, Gslo, 3, dg, sg, b));
+        GKBA_TRY(make_map(c, &P[2].mBh, G3hi, 3, dg, sg, b));
+        GKBA_TRY(make_map(c, &P[2].mBl, G3lo, 3, dg, sg, b));
     }
-    const size_t ssm = stage_smem_bytes(Np);
-    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_pair<true> : k_tc_pair<false>;
-    const int grid = stage_grid(c, nb);
+    const long long pair_tiles = (long long)nb * (N3 / kBM) / 2;
     StageParams sp = stage_base(c, nb);
     // S1: rows (j,m,q), cols (c,r) -> X1[j][r][m][c][q]
     sp.planes = 1;
@@ -1827,22 +1974,20 @@ static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_fina
     sp.unit_sys = c->unit_sys;
     sp.out = X13;
     sp.map = StageMap{2 * N3, 2 * Np, 1, Np, 2 * N2, Np, Np, Np};
-    {
-        auto t = launch_begin(c, K_W1, fl_cr * nb, 4.0 * (N4r + 2 * N4r * nb));
-        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA1, mB1h, mB1l, sp);
-        GKBA_TRY(launch_end(c, t));
-    }
+    P[0].sp = sp;
+    P[0].flops = fl_cr * nb;
+    P[0].bytes = 4.0 * (N4r + 2 * N4r * nb);
+    P[0].cls = K_W1;
     // S2: rows (j,r,m), K (c,q), cols (c',p) -> X2[j][r][p][c'][m]
     sp.planes = 2;
     sp.a_unit = 1;
     sp.unit_sys = nullptr;
     sp.out = X2;
     sp.map = StageMap{2 * N3, 2 * N2, 1, Np, 2 * Np, Np, Np, Np};
-    {
-        auto t = launch_begin(c, K_W2, fl_cc * nb, 4.0 * 4 * N4r * nb);
-        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in1, mGh, mGl, sp);
-        GKBA_TRY(launch_end(c, t));
-    }
+    P[1].sp = sp;
+    P[1].flops = fl_cc * nb;
+    P[1].bytes = 4.0 * 4 * N4r * nb;
+    P[1].cls = K_W2;
     // S3: rows (j,r,p), K (c,m), cols (c',n) -> X3 with rows (u,c',j) and K (n,r,p):
     // K-blocked X3[K/32][Rld][32] when Np % 32 == 0 (one contiguous 16 KB block
     // per 128 x 32 tile of the last stage), else X3[u][c'][j][n][r][p].
@@ -1858,10 +2003,25 @@ static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_fina
     } else {
         sp.map = StageMap{N3, Np, 1, N4, N2, Np, Np, Np};
     }
-    {
-        auto t = launch_begin(c, K_W3, fl_cc * nb, 4.0 * 4 * N4r * nb);
-        stage_kernel<<<grid, kStageThreads, ssm, c->stream>>>(mA23_in2, mG3h, mG3l, sp);
-        GKBA_TRY(launch_end(c, t));
+    P[2].sp = sp;
+    P[2].flops = fl_cc * nb;
+    P[2].bytes = 4.0 * 4 * N4r * nb;
+    P[2].cls = K_W3;
+    for (int k = 0; k < 3; ++k) {
+        P[k].pair_tiles = pair_tiles;
+        P[k].weight = stage_weight(P[k].sp, pair_tiles);
+    }
+    return GKBA_OK;
+}
+
+// Stages S1-S3 of one batch; with do_final, stage S4 and the reduction follow:
+// S_u -> c->Su.
+static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_final) {
+    StagePlan P[3];
+    GKBA_TRY(plan_chain(c, nb, A1, P));
+    for (int k = 0; k < 3; ++k) {
+        const StagePlan* pk = &P[k];
+        GKBA_TRY(launch_stage_group(c, &pk, 1, P[k].cls));
     }
     if (!do_final) return GKBA_OK;
     return tf32_final(c, nb);
@@ -1869,6 +2029,33 @@ static gkba_status tf32_chain(gkba_ctx* c, int nb, const float* A1, bool do_fina
 
 // Tensor-core contraction of one batch (forms built): S_u -> c->Su.
 gkba_status contract_batch_tf32(gkba_ctx* c, int nb) { return tf32_chain(c, nb, c->wS32, true); }
+
+// Several problems at once (each context's forms built, its batch of nbs[i]
+// units): one launch per stage for all of them, the clusters split by cost;
+// then each context's reduction: S_u -> cs[i]->Su.  The contexts share c0's
+// stream and precision mode.
+gkba_status contract_batch_tf32_multi(gkba_ctx* const* cs, const int* nbs, int n) {
+    if (n < 1 || n > kMaxLaunchGroups) return fail(cs[0], GKBA_EINVAL, "%d problems in one launch", n);
+    gkba_ctx* c0 = cs[0];
+    StagePlan P[kMaxLaunchGroups][3];
+    for (int i = 0; i < n; ++i) GKBA_TRY(plan_chain(cs[i], nbs[i], cs[i]->wS32, P[i]));
+    for (int k = 0; k < 3; ++k) {
+        const StagePlan* pk[kMaxLaunchGroups];
+        for (int i = 0; i < n; ++i) pk[i] = &P[i][k];
+        GKBA_TRY(launch_stage_group(c0, pk, n, P[0][k].cls));
+    }
+    FinalPlan F[kMaxLaunchGroups];
+    const FinalPlan* fk[kMaxLaunchGroups];
+    for (int i = 0; i < n; ++i) {
+        GKBA_TRY(plan_final(cs[i], nbs[i], F[i]));
+        fk[i] = &F[i];
+    }
+    GKBA_TRY(launch_final_group(c0, fk, n));
+    for (int i = 0; i < n; ++i)
+        GKBA_TRY(reduce_partials_launch(cs[i], nbs[i], F[i].fp.nks, (long long)cs[i]->Np * F[i].fp.Rld,
+                                        F[i].fp.Rld, cs[i]->part, true, cs[i]->Su));
+    return GKBA_OK;
+}
 
 // dL/dv on the tensor-core path: the omega layout of v (once per context).
 gkba_status tf32_prepare_vgrad(gkba_ctx* c) {
@@ -1936,31 +2123,34 @@ static gkba_status tl_stage(gkba_ctx* c, const float* in, int bunit, float* out,
     const long long per = 2LL * Np * Np;
     const float* Bhi = (const float*)c->formsG3 + 2 * per * bunit;
     const float* Blo = (const float*)c->formsG3 + 2 * per * c->ub_cap + 2 * per * bunit;
-    CUtensorMap mA, mBh, mBl;
+    StagePlan P;
     {
         cuuint64_t d[4] = {(cuuint64_t)Np, 2, (cuuint64_t)N3, 1};
         cuuint64_t s[3] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * Np * 4, (cuuint64_t)(2 * N4 * 4)};
         cuuint32_t b[4] = {kKC, 1, kBM, 1};
-        GKBA_TRY(make_map(c, &mA, in, 4, d, s, b));
+        GKBA_TRY(make_map(c, &P.mA, in, 4, d, s, b));
     }
     {
         cuuint64_t d[3] = {(cuuint64_t)Np, (cuuint64_t)4 * Np, 1};
         cuuint64_t s[2] = {(cuuint64_t)Np * 4, (cuuint64_t)2 * per * 4};
         cuuint32_t b[3] = {kKC, (cuuint32_t)Np, 1};
-        GKBA_TRY(make_map(c, &mBh, Bhi, 3, d, s, b));
-        GKBA_TRY(make_map(c, &mBl, Blo, 3, d, s, b));
+        GKBA_TRY(make_map(c, &P.mBh, Bhi, 3, d, s, b));
+        GKBA_TRY(make_map(c, &P.mBl, Blo, 3, d, s, b));
     }
-    StageParams sp = stage_base(c, 1);
-    sp.planes = 2;
-    sp.a_unit = 1;
-    sp.out = out;
-    sp.out_unit = out_unit;
-    sp.map = map;
+    P.sp = stage_base(c, 1);
+    P.sp.planes = 2;
+    P.sp.a_unit = 1;
+    P.sp.out = out;
+    P.sp.out_unit = out_unit;
+    P.sp.map = map;
+    P.pair_tiles = N3 / kBM / 2;
+    P.weight = stage_weight(P.sp, P.pair_tiles);
     const double Nr = c->N;
-    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_pair<true> : k_tc_pair<false>;
-    auto t = launch_begin(c, K_TL, 8.0 * Nr * Nr * Nr * Nr * Nr, 4.0 * 4 * Nr * Nr * Nr * Nr);
-    stage_kernel<<<stage_grid(c, 1), kStageThreads, stage_smem_bytes(Np), c->stream>>>(mA, mBh, mBl, sp);
-    return launch_end(c, t);
+    P.flops = 8.0 * Nr * Nr * Nr * Nr * Nr;
+    P.bytes = 4.0 * 4 * Nr * Nr * Nr * Nr;
+    P.cls = K_TL;
+    const StagePlan* pp = &P;
+    return launch_stage_group(c, &pp, 1, K_TL);
 }
 
 // The time-linear collision's tensor contractions on the tensor cores:

@@ -35,7 +35,7 @@ EXPORTED = ["gkba_init", "gkba_sigma", "gkba_collision", "gkba_step", "gkba_set_
             "gkba_get_stats", "gkba_last_error", "gkba_destroy", "gkba_sigma_noalloc",
             "gkba_batch_create", "gkba_batch_step", "gkba_batch_last_error", "gkba_batch_destroy",
             "gkba_selftest_timeout", "gkba_sigma3", "gkba_collision_vjp",
-            "gkba_measure_tf32_mma"]
+            "gkba_measure_tf32_mma", "gkba_batch_set_options", "gkba_batch_autotune"]
 
 
 class GKBAError(RuntimeError):
@@ -92,6 +92,8 @@ def load():
     L.gkba_sigma3.argtypes = [P, I, P, P, P, P, I]
     L.gkba_collision_vjp.argtypes = [P, I, P, P, P, P, P, P, P, I]
     L.gkba_batch_step.argtypes = [P, P, P, P, P]
+    L.gkba_batch_set_options.argtypes = [P, I]
+    L.gkba_batch_autotune.argtypes = [P, P, P, P, P, P, P]
     L.gkba_batch_last_error.argtypes = [P]
     L.gkba_batch_last_error.restype = ctypes.c_char_p
     L.gkba_batch_destroy.argtypes = [P]
@@ -343,8 +345,9 @@ class Context:
 
 class Batch:
     """Several Contexts (split-TF32, general interaction) advanced together:
-    the history contractions of all systems of the same N share each kernel
-    launch (gkba_batch_*).  The contexts stay usable on their own afterwards."""
+    the history contractions of all systems share each stage launch, split
+    by basis-size group (gkba_batch_*).  The contexts stay usable on their own
+    afterwards."""
 
     def __init__(self, contexts, workspace_bytes=0):
         L = load()
@@ -372,6 +375,27 @@ class Batch:
         if st != OK:
             raise GKBAError(st, L.gkba_batch_last_error(self._h).decode())
         return rhos, diags
+
+    def set_options(self, use_graph=False):
+        """use_graph: capture each step's device work and launch it as one CUDA graph."""
+        L = load()
+        st = L.gkba_batch_set_options(self._h, 1 if use_graph else 0)
+        if st != OK:
+            raise GKBAError(st, L.gkba_batch_last_error(self._h).decode())
+
+    def autotune(self):
+        """Choose the launch parameters per basis-size group by timing them on
+        the device (gkba_batch_autotune); returns one dict per group."""
+        L = load()
+        n = ctypes.c_int()
+        Ns, units, aw, kw = (np.zeros(8, np.int32) for _ in range(4))
+        us = np.zeros(8, np.float64)
+        st = L.gkba_batch_autotune(self._h, ctypes.byref(n), Ns.ctypes.data, units.ctypes.data,
+                                   aw.ctypes.data, kw.ctypes.data, us.ctypes.data)
+        if st != OK:
+            raise GKBAError(st, L.gkba_batch_last_error(self._h).decode())
+        return [dict(N=int(Ns[g]), units_per_round=int(units[g]), acc_window=int(aw[g]),
+                     s4_item_k=int(kw[g]), us_per_unit=float(us[g])) for g in range(min(n.value, 8))]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -135,3 +135,48 @@ def test_batch_step_vs_oracle(P, precision):
               f"E_c {diags[i][2]:.6e} vs {ec_ref:.6e}")
     for c in batched:
         c.close()
+
+
+def test_batch_graph_steps_match_eager_steps(P):
+    # the same kernels in the same order, launched as one captured graph per
+    # step (the executable graph updated in place as the histories grow)
+    spec = [(8, 20, 31), (12, 14, 32), (24, 9, 33), (48, 5, 34)]
+    steps = 3
+    eager = [make(P, N, L, sd, steps) for N, L, sd in spec]
+    graph = [make(P, N, L, sd, steps) for N, L, sd in spec]
+    E = [0.02 * k for k in range(steps + 1)]
+    with P.Batch(eager) as a, P.Batch(graph) as g:
+        g.set_options(use_graph=True)
+        for k in range(steps):
+            ra, da = a.step(E[k], E[k + 1])
+            rg, dg = g.step(E[k], E[k + 1])
+            for i in range(len(spec)):
+                assert np.array_equal(ra[i], rg[i]), (k, spec[i])
+                assert np.array_equal(da[i], dg[i]), (k, spec[i])
+    for c in eager + graph:
+        c.close()
+
+
+def test_batch_autotune_records_choices_and_keeps_accuracy(P):
+    # the autotuner's choices per basis-size group, then a tuned (graph) step
+    # against the oracle's Heun step
+    spec = [(8, 30, 41), (16, 22, 42), (32, 12, 43), (48, 6, 44)]
+    dt, E_n, E_np1 = 0.02, 0.01, -0.03
+    ctxs = [make(P, N, L, sd, 1) for N, L, sd in spec]
+    with P.Batch(ctxs) as b:
+        tuned = b.autotune()
+        b.set_options(use_graph=True)
+        rhos, diags = b.step(E_n, E_np1)
+    print("autotuned:", tuned)
+    assert [t["N"] for t in tuned] == [8, 16, 32, 48]
+    for t in tuned:
+        assert t["units_per_round"] >= 1 and t["acc_window"] in (8, 16, 32)
+        assert t["s4_item_k"] in (4096, 8192, 16384) and t["us_per_unit"] > 0
+    for i, (N, L, sd) in enumerate(spec):
+        s, rho, T = member(N, L, sd)
+        r_ref, _, _ = O.heun_step(s["h"], s["v"], s["d"], list(rho), list(T), dt, E_n, E_np1,
+                                  route="paper")
+        check(rhos[i] - rho[-1], r_ref - rho[-1], 2e-5, f"tuned member N={N} increment")
+        check(rhos[i], r_ref, 1e-5, f"tuned member N={N} rho")
+    for c in ctxs:
+        c.close()
