@@ -331,15 +331,16 @@ def run_chains(a):
               flush=True)
 
 
-def time_linear_sample(P, s, N, dt, stream, warmup, steps):
-    """gkba_step with cfg.history = GKBA_HISTORY_TIME_LINEAR (FP64) at N: the
-    history sum kept as one N^4 accumulator, so a step's cost does not depend
-    on the history length.  `warmup` steps from the initial state, then
-    `steps` timed steps (CUDA events on the context's stream); the per-step
-    work is the same at any step index."""
+def time_linear_sample(P, s, N, dt, stream, warmup, steps, precision="fp64"):
+    """gkba_step with cfg.history = GKBA_HISTORY_TIME_LINEAR at N: the history
+    sum kept as one N^4 accumulator (FP64), so a step's cost does not depend on
+    the history length; its contractions in FP64 or on the tensor cores
+    (split-TF32).  `warmup` steps from the initial state, then `steps` timed
+    steps (CUDA events on the context's stream); the per-step work is the same
+    at any step index."""
     import torch
     ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=warmup + steps + 1,
-                    precision="fp64", stream=stream.cuda_stream, timing=True,
+                    precision=precision, stream=stream.cuda_stream, timing=True,
                     history="time_linear")
     for _ in range(warmup):
         ctx.step(0.0, 0.0)
@@ -356,14 +357,14 @@ def time_linear_sample(P, s, N, dt, stream, warmup, steps):
     ctx.close()
     flops = sum(v["flops"] for v in stats.values()) / steps
     return {"ms_per_step": ms, "flops_per_step": flops,
-            "fp64_tflops": flops / (ms * 1e-3) / 1e12, "gpu_launches": launches,
+            "tflops": flops / (ms * 1e-3) / 1e12, "gpu_launches": launches,
             "classes": {k: {"ms": v["ms"] / steps, "launches": v["launches"] // steps}
                         for k, v in stats.items() if v["launches"]},
             "trace": float(diag[0])}
 
 
 def run_time_linear(a):
-    """The time-linear step alone at N (see time_linear_sample)."""
+    """The time-linear step alone at N (see time_linear_sample), FP64 and split-TF32."""
     import torch
     import gkba_inputs as gi
     from paper_1905_01180_gb300 import build as b
@@ -371,11 +372,12 @@ def run_time_linear(a):
     import paper_1905_01180_gb300 as P
     N, dt = a.N, a.dt
     s = gi.system(N, a.nP, seed=0)
-    r = time_linear_sample(P, s, N, dt, torch.cuda.current_stream(), a.warmup, a.steps)
-    print(json.dumps({"workload": f"gkba_time_linear_step_N{N}", "metric": "GKBA Heun step time",
-                      "value": r["ms_per_step"] / 1e3, "unit": "s", "higher_is_better": False,
-                      "precision": "fp64", "history": "time_linear", "N": N, "n_P": a.nP,
-                      "steps": a.steps, "warmup": a.warmup, **r}), flush=True)
+    for prec in ("fp64", "tf32"):
+        r = time_linear_sample(P, s, N, dt, torch.cuda.current_stream(), a.warmup, a.steps, prec)
+        print(json.dumps({"workload": f"gkba_time_linear_step_N{N}", "metric": "GKBA Heun step time",
+                          "value": r["ms_per_step"] / 1e3, "unit": "s", "higher_is_better": False,
+                          "precision": prec, "history": "time_linear", "N": N, "n_P": a.nP,
+                          "steps": a.steps, "warmup": a.warmup, **r}), flush=True)
 
 
 def run_batch(a):
@@ -708,10 +710,13 @@ def main():
         # the same Heun step with the history sum kept as one N^4 accumulator
         # (FP64; its cost does not depend on L)
         r = time_linear_sample(P, s, N, dt, stream, 1, 2)
-        line["time_linear"] = {"ms_per_step": r["ms_per_step"], "precision": "fp64",
-                               "fp64_tflops": r["fp64_tflops"],
-                               "speedup_vs_history_sum_step": ms_step / r["ms_per_step"],
-                               "sample": f"2 steps after 1 warm-up from rho0 at N={N} "
+        r32 = time_linear_sample(P, s, N, dt, stream, 1, 3, a.precision)
+        line["time_linear"] = {"fp64": {"ms_per_step": r["ms_per_step"], "tflops": r["tflops"],
+                                        "speedup_vs_history_sum_step": ms_step / r["ms_per_step"]},
+                               "split_tf32": {"ms_per_step": r32["ms_per_step"], "tflops": r32["tflops"],
+                                              "precision": a.precision,
+                                              "speedup_vs_history_sum_step": ms_step / r32["ms_per_step"]},
+                               "sample": f"2-3 steps after 1 warm-up from rho0 at N={N} "
                                          "(per-step work independent of the history length)"}
 
     if rank == 0 and not a.no_cpu:

@@ -1492,8 +1492,11 @@ gkba_status tune_round(gkba_batch* b, int gi, const CollisionPlan& P, long long 
 // and longer items), the accumulation window of the windowed stage kernel
 // (8 or 16 K, both within the tolerance), then the units per round (from
 // the workspace's down by halves while the stage launches keep two 256-row
-// tiles per cluster; smaller rounds keep the intermediates in L2).  The
-// fastest time per unit wins each coordinate.
+// tiles per cluster; smaller rounds keep the intermediates in L2).  A
+// candidate replaces the incumbent only when it is at least kTuneGain faster
+// per unit (timing noise does not move the choice).
+constexpr double kTuneGain = 0.03;
+
 gkba_status autotune(gkba_batch* b) {
     CollisionPlan P;
     GKBA_TRY(plan_collision(b, 0, P, false));
@@ -1515,7 +1518,7 @@ gkba_status autotune(gkba_batch* b) {
                 sh->fin_kw = kw;
                 double t = 0.0;
                 GKBA_TRY(tune_round(b, gi, P, n0, &t));
-                if (t < best) {
+                if (t < best * (1.0 - kTuneGain)) {
                     best = t;
                     best_kw = kw;
                 } else {
@@ -1531,7 +1534,7 @@ gkba_status autotune(gkba_batch* b) {
             sh->acc_window = other;
             double t = 0.0;
             GKBA_TRY(tune_round(b, gi, P, n0, &t));
-            if (t < best) best = t;
+            if (t < best * (1.0 - kTuneGain)) best = t;
             else sh->acc_window = keep;
         }
         // units per round
@@ -1542,7 +1545,7 @@ gkba_status autotune(gkba_batch* b) {
         for (long long nb = ((n0 / 2) / g.pu) * g.pu; nb >= min_units; nb = ((nb / 2) / g.pu) * g.pu) {
             double t = 0.0;
             GKBA_TRY(tune_round(b, gi, P, nb, &t));
-            if (t < best) {
+            if (t < best * (1.0 - kTuneGain)) {
                 best = t;
                 best_nb = nb;
             }

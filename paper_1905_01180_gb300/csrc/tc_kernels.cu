@@ -335,8 +335,10 @@ struct StageParams {
     int wsteps;        // 0: one accumulator per tile; 1 or 2: windows of that many K steps
     int nring;         // windowed: accumulators in the ring (<= kStageRing)
     int as2;           // windowed: ring stride in columns (2 Np rounded up to 32)
+    int astages;       // A pipeline stages (4 .. kStageAStagesMax, set with the shared memory)
 };
 
+static_assert(sizeof(StageParams) % 4 == 0 && sizeof(StageParams) / 4 <= 384, "StageParams copy");
 // One launch of the stage kernel: up to kMaxLaunchGroups groups (problems of
 // different Np or operands), each with its own parameters and tensor maps; the
 // clusters [cl_begin[g], cl_begin[g + 1]) of the grid work on group g.
@@ -360,7 +362,13 @@ __device__ __forceinline__ float* stage_out_row(const StageParams& p, int u, uin
            (long long)(rb % Db) * p.map.SB + xo;
 }
 
-constexpr int kStageAStages = 4;
+// A pipeline stages (16 KB each): as many as shared memory holds next to the
+// resident B operand, up to kStageAStagesMax.  The loads of a stage kernel
+// are latency-bound: at a few microseconds of load latency under load, an
+// SM streams about (stages x 16 KB) per latency, so every stage counts.
+constexpr int kStageAStagesMax = 8;
+// dynamic shared memory of one CTA
+constexpr size_t kStageSmemMax = 227 * 1024;
 constexpr int kStageRing = 8;
 constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-11 epilogue
 
@@ -391,7 +399,7 @@ constexpr int kStageThreads = 384;  // warp 0 TMA, warp 1 MMA, 4-7 converter, 8-
 // single, not double-buffered, pair), summed in the epilogue; the main
 // accumulator then sees a third of the truncating accumulator additions.
 // ---------------------------------------------------------------------------
-template <bool SPLIT_ACC>
+template <bool SPLIT_ACC, bool GROUPED>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
     k_tc_pair(const __grid_constant__ StageLaunch L) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -399,22 +407,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
     // the group this cluster works on: the launch's clusters are split between
     // its groups (problems of different Np or operands), each runs the
     // pipeline below with its own parameters and tensor maps
+    // GROUPED = false: a one-group launch, whose parameters the loops read
+    // from the parameter block at constant offsets; a grouped launch indexes
+    // them by the cluster's group (generic loads).  Shared-memory copies of
+    // the parameters measured slower than either.
     const int cid_all = (int)cluster_id_x();
     int grp = 0;
-    while (grp + 1 < L.ngroups && cid_all >= L.cl_begin[grp + 1]) ++grp;
-    const StageParams& p = L.p[grp];
-    const CUtensorMap* tmA = &L.tmA[grp];
-    const CUtensorMap* tmBhi = &L.tmBhi[grp];
-    const CUtensorMap* tmBlo = &L.tmBlo[grp];
+    if (GROUPED)
+        while (grp + 1 < L.ngroups && cid_all >= L.cl_begin[grp + 1]) ++grp;
+    const StageParams& p = GROUPED ? L.p[grp] : L.p[0];
+    const CUtensorMap* tmA = GROUPED ? &L.tmA[grp] : &L.tmA[0];
+    const CUtensorMap* tmBhi = GROUPED ? &L.tmBhi[grp] : &L.tmBhi[0];
+    const CUtensorMap* tmBlo = GROUPED ? &L.tmBlo[grp] : &L.tmBlo[0];
     const int Np = p.Np;
     const int nchunk = p.planes * p.kch;                // K-chunks per tile
     const uint32_t chunkB = (uint32_t)(Np * 128);       // one K-chunk of this CTA's Np B rows
     uint8_t* sBhi = smem;
     uint8_t* sBlo = sBhi + nchunk * chunkB;
     uint8_t* sA = sBlo + nchunk * chunkB;
-    uint64_t* bars = (uint64_t*)(sA + kStageAStages * kTileBytes);
-    constexpr int BFULL = 0, BPEER = 1, BEMPTY = 2, AFULL = 3, AEMPTY = AFULL + kStageAStages,
-                  TFULL = AEMPTY + kStageAStages, TEMPTY = TFULL + 2, ACCF = TEMPTY + 2,
+    const int nas = p.astages;  // A stages of this launch (<= kStageAStagesMax)
+    uint64_t* bars = (uint64_t*)(sA + nas * kTileBytes);
+    constexpr int BFULL = 0, BPEER = 1, BEMPTY = 2, AFULL = 3, AEMPTY = AFULL + kStageAStagesMax,
+                  TFULL = AEMPTY + kStageAStagesMax, TEMPTY = TFULL + 2, ACCF = TEMPTY + 2,
                   ACCE = ACCF + 2, DRAIN = ACCE + 2, WF = DRAIN + 1, WE = WF + kStageRing,
                   NBARS = WE + kStageRing;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
@@ -422,7 +436,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
     // windowed mode: a 32 x 32 FP32 staging block per epilogue warp (after the
     // 512-byte barrier area) through which the epilogue turns its per-row
     // results into 16-byte stores
-    float* stage_out = (float*)(sA + kStageAStages * kTileBytes + 512);
+    float* stage_out = (float*)(sA + nas * kTileBytes + 512);
     auto bar = [&](int i) { return smem_u32(bars + i); };
 
     const uint32_t rank = cluster_rank();
@@ -433,7 +447,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
         mbar_init(bar(BFULL), 1);
         mbar_init(bar(BPEER), 1);
         mbar_init(bar(BEMPTY), 1);
-        for (int s = 0; s < kStageAStages; ++s) {
+        for (int s = 0; s < nas; ++s) {
             mbar_init(bar(AFULL + s), 1);
             mbar_init(bar(AEMPTY + s), 4);
         }
@@ -490,6 +504,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             int cur_u = -1;
             uint32_t bph = 0;
             long long it = 0;
+            Ring ar(nas);  // A stage and its phase
             bool ok = true, loaded_b = false;
             for (long long t = t0; t < t1 && ok; ++t) {
                 const int u = (int)((uint32_t)t / ipu32);
@@ -511,8 +526,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 }
                 for (int c = 0; c < nchunk && ok; ++c, ++it) {
                     const int pl = c / p.kch, kc = c % p.kch;
-                    const int s = (int)(it % kStageAStages);
-                    const uint32_t ph = (uint32_t)((it / kStageAStages) & 1);
+                    const int s = ar.i;
+                    const uint32_t ph = ar.ph;
+                    ar.next();
                     if (!mbar_wait_cl(bar(AEMPTY + s), ph ^ 1, abort_flag, peer_abort, p.err, 2)) { ok = false; break; }
                     mbar_expect_tx(bar(AFULL + s), kTileBytes);
                     const uint32_t dst = smem_u32(sA + s * kTileBytes);
@@ -522,10 +538,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 }
             }
             if (*abort_flag) {
-                for (int s = 0; s < kStageAStages; ++s) {
+                for (int s = 0; s < nas; ++s) {
                     if (it > s) {
-                        const long long last = it - 1 - ((it - 1 - s) % kStageAStages);
-                        const uint32_t ph = (uint32_t)((last / kStageAStages) & 1);
+                        const long long last = it - 1 - ((it - 1 - s) % nas);
+                        const uint32_t ph = (uint32_t)((last / nas) & 1);
                         const unsigned long long g0 = gtimer();
                         while (!mbar_try(bar(AFULL + s), ph) && gtimer() - g0 < kWaitLimitNs) {}
                     }
@@ -704,11 +720,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
         const int r = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
         long long it = 0;
+        Ring ar(nas);  // A stage and its phase
         bool ok = true;
         for (long long t = t0; t < t1 && ok; ++t) {
             for (int c = 0; c < nchunk; ++c, ++it) {
-                const int s = (int)(it % kStageAStages);
-                const uint32_t ph = (uint32_t)((it / kStageAStages) & 1);
+                const int s = ar.i;
+                const uint32_t ph = ar.ph;
+                ar.next();
                 if (!warp_wait_cl(bar(AFULL + s), ph, abort_flag, peer_abort, p.err, 6)) { ok = false; break; }
                 uint32_t hi[32], lo[32];
                 load_split_row(sA + s * kTileBytes, r, hi, lo);
@@ -873,6 +891,7 @@ struct FinalParams {
 
 constexpr int kFinThreads = 448;  // 14 warps: see the S4 kernel
 
+static_assert(sizeof(FinalParams) % 4 == 0 && sizeof(FinalParams) / 4 <= 448, "FinalParams copy");
 // One launch of the S4 kernel over up to kMaxLaunchGroups groups (see StageLaunch).
 struct FinalLaunch {
     CUtensorMap tmA[kMaxLaunchGroups];
@@ -945,6 +964,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                  : "memory");
 }
 
+template <bool GROUPED>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     k_tc_final_pair(const __grid_constant__ FinalLaunch L) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -952,11 +972,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     // the group this cluster works on (see StageLaunch)
     const int cid_all = (int)cluster_id_x();
     int grp = 0;
-    while (grp + 1 < L.ngroups && cid_all >= L.cl_begin[grp + 1]) ++grp;
-    const FinalParams& p = L.p[grp];
-    const CUtensorMap* tmA = &L.tmA[grp];
-    const CUtensorMap* tmBhi = &L.tmBhi[grp];
-    const CUtensorMap* tmBlo = &L.tmBlo[grp];
+    if (GROUPED)  // as in the stage kernel
+        while (grp + 1 < L.ngroups && cid_all >= L.cl_begin[grp + 1]) ++grp;
+    const FinalParams& p = GROUPED ? L.p[grp] : L.p[0];
+    const CUtensorMap* tmA = GROUPED ? &L.tmA[grp] : &L.tmA[0];
+    const CUtensorMap* tmBhi = GROUPED ? &L.tmBhi[grp] : &L.tmBhi[0];
+    const CUtensorMap* tmBlo = GROUPED ? &L.tmBlo[grp] : &L.tmBlo[0];
     const int Np = p.Np, Nh = Np / 2;
     const uint32_t AS = (uint32_t)((Np + 31) & ~31);  // window accumulator stride in columns
     const uint32_t bbytes = (uint32_t)(Nh * 128);     // this CTA's B rows, one 32-wide box
@@ -1616,12 +1637,20 @@ gkba_status make_map(gkba_ctx* c, CUtensorMap* m, const void* base, int rank, co
 }
 
 constexpr int kMaxTcNp = 96;  // largest padded basis of the tensor-core path
-size_t stage_smem_bytes(int Np) {
+// Shared memory of a stage launch with `astages` A stages.
+size_t stage_smem_bytes(int Np, int astages) {
     const int kch = (Np + kKC - 1) / kKC;
     // windowed mode (2 Np <= 96) adds the epilogue's 4 x 4 KB staging blocks
-    return 1024 + 2ull * kch * (2 * Np * 128) + kStageAStages * kTileBytes + 512 +
+    return 1024 + 2ull * kch * (2 * Np * 128) + (size_t)astages * kTileBytes + 512 +
            (2 * Np <= 96 ? 4 * 32 * 32 * 4 : 0);
 }
+// The most A stages that fit next to the B operand (at least 4).
+int stage_astages(int Np) {
+    int a = kStageAStagesMax;
+    while (a > 4 && stage_smem_bytes(Np, a) > kStageSmemMax) --a;
+    return a;
+}
+size_t stage_smem_bytes(int Np) { return stage_smem_bytes(Np, stage_astages(Np)); }
 size_t final_pair_smem_bytes(int Np) {
     return 1024 + (size_t)kFinPairStages * (kTileBytes + 2 * (Np / 2) * 128) + 512;
 }
@@ -1641,9 +1670,10 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
     GKBA_TRY(launch_end(c, t));
     // The shared-memory limit is a property of the kernel, not of a context:
     // set it for the largest basis so that contexts of different N coexist.
-    for (auto kfn : {k_tc_pair<false>, k_tc_pair<true>})
+    for (auto kfn : {k_tc_pair<false, false>, k_tc_pair<true, false>, k_tc_pair<false, true>,
+                     k_tc_pair<true, true>})
         GKBA_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)stage_smem_bytes(kMaxTcNp)));
+                                          (int)kStageSmemMax));
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(c->num_sms & ~1));
@@ -1651,12 +1681,13 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
         cfg.dynamicSmemBytes = stage_smem_bytes(c->Np);
         cfg.stream = c->stream;
         int ncl = 0;
-        GKBA_CUDA(c, cudaOccupancyMaxActiveClusters(&ncl, k_tc_pair<false>, &cfg));
+        GKBA_CUDA(c, cudaOccupancyMaxActiveClusters(&ncl, k_tc_pair<false, false>, &cfg));
         if (ncl < 1) return fail(c, GKBA_ECUDA, "no 2-CTA cluster of the stage kernel fits on an SM pair");
         c->pair_clusters = ncl;
     }
-    GKBA_CUDA(c, cudaFuncSetAttribute(k_tc_final_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)final_pair_smem_bytes(kMaxTcNp)));
+    for (auto kfn : {k_tc_final_pair<false>, k_tc_final_pair<true>})
+        GKBA_CUDA(c, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)final_pair_smem_bytes(kMaxTcNp)));
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(c->num_sms & ~1));
@@ -1664,7 +1695,7 @@ gkba_status tf32_prepare_model(gkba_ctx* c) {
         cfg.dynamicSmemBytes = final_pair_smem_bytes(c->Np);
         cfg.stream = c->stream;
         int ncl = 0;
-        GKBA_CUDA(c, cudaOccupancyMaxActiveClusters(&ncl, k_tc_final_pair, &cfg));
+        GKBA_CUDA(c, cudaOccupancyMaxActiveClusters(&ncl, k_tc_final_pair<false>, &cfg));
         if (ncl < 1) return fail(c, GKBA_ECUDA, "no 2-CTA cluster of the S4 kernel fits on an SM pair");
         c->fin_pair_clusters = ncl;
     }
@@ -1714,6 +1745,7 @@ static StageParams stage_base(gkba_ctx* c, int nb) {
     sp.as2 = ((2 * Np + 31) / 32) * 32;
     sp.wsteps = 2 * Np <= 96 ? std::max(1, std::min(2, c->acc_window / 8)) : 0;
     sp.nring = std::min(kStageRing, (512 - 128) / sp.as2);
+    sp.astages = stage_astages(Np);
     return sp;
 }
 
@@ -1801,13 +1833,15 @@ static gkba_status launch_stage_group(gkba_ctx* c, const StagePlan* const* plans
         L.p[g] = plans[g]->sp;
         w[g] = plans[g]->weight;
         cap[g] = std::max(1LL, plans[g]->pair_tiles);
-        smem = std::max(smem, stage_smem_bytes(plans[g]->sp.Np));
+        smem = std::max(smem, stage_smem_bytes(plans[g]->sp.Np, plans[g]->sp.astages));
         fl += plans[g]->flops;
         by += plans[g]->bytes;
     }
     L.ngroups = n;
     const int ncl = split_clusters(c->pair_clusters, w, cap, n, L.cl_begin);
-    auto stage_kernel = c->prec == GKBA_SPLIT_TF32_ACC ? k_tc_pair<true> : k_tc_pair<false>;
+    const bool acc = c->prec == GKBA_SPLIT_TF32_ACC;
+    auto stage_kernel = n > 1 ? (acc ? k_tc_pair<true, true> : k_tc_pair<false, true>)
+                              : (acc ? k_tc_pair<true, false> : k_tc_pair<false, false>);
     auto t = launch_begin(c, cls, fl, by);
     stage_kernel<<<2 * ncl, kStageThreads, smem, c->stream>>>(L);
     return launch_end(c, t);
@@ -1833,8 +1867,9 @@ static gkba_status launch_final_group(gkba_ctx* c, const FinalPlan* const* plans
     }
     L.ngroups = n;
     const int ncl = split_clusters(c->fin_pair_clusters, w, cap, n, L.cl_begin);
+    auto fin_kernel = n > 1 ? k_tc_final_pair<true> : k_tc_final_pair<false>;
     auto t = launch_begin(c, K_FIN, fl, by);
-    k_tc_final_pair<<<2 * ncl, kFinThreads, smem, c->stream>>>(L);
+    fin_kernel<<<2 * ncl, kFinThreads, smem, c->stream>>>(L);
     return launch_end(c, t);
 }
 
