@@ -425,7 +425,7 @@ void free_ctx(gkba_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->tl_acc, c->tl_s, c->tl_W, c->tl_Wn, c->tl_uf,
                     c->h, c->d, c->v, c->vm, c->vjp, c->rhot_hist, c->U_hist, c->adj_ws, c->vomega,
-                    c->vgrad, c->hfK, c->wS64, c->vK64, c->wS32, c->vO32, c->vKhi, c->vKlo,
+                    c->vgrad, c->hfK, c->wS64, c->vK64, c->wS32, c->vO32, c->xsw, c->vKhi, c->vKlo,
                     c->rho_hist, c->T_a, c->T_b, c->hhf_n, c->hhf_t, c->k1, c->k2, c->Ia, c->Ib,
                     c->U, c->ex0, c->ex1, c->ex2, c->tmp0, c->tmp1, c->dscal, c->dint, c->ws,
                     c->stage};

@@ -86,6 +86,8 @@ struct gkba_ctx {
     // split-TF32 contraction operands (padded Np, zero padding)
     float* wS32 = nullptr;    // raw FP32 [j][m][q][s]
     float* vO32 = nullptr;    // omega layout of v, FP32 [i][n][p][r] (dL/dv, made on demand)
+    float* xsw = nullptr;     // row weights of the slot contractions (dL/dv, time-linear)
+    size_t xsw_bytes = 0;
     float* vKhi = nullptr;    // TF32-rounded [i][(n,r,p)]
     float* vKlo = nullptr;    // TF32-rounded remainder
 

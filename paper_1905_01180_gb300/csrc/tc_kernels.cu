@@ -433,9 +433,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                   NBARS = WE + kStageRing;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    // windowed mode: a 32 x 32 FP32 staging block per epilogue warp (after the
-    // 512-byte barrier area) through which the epilogue turns its per-row
-    // results into 16-byte stores
+    // a 32 x 32 FP32 staging block per epilogue warp (after the 512-byte
+    // barrier area) through which the epilogue turns its per-row results into
+    // 16-byte stores
     float* stage_out = (float*)(sA + nas * kTileBytes + 512);
     auto bar = [&](int i) { return smem_u32(bars + i); };
 
@@ -834,6 +834,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
             const uint32_t row = ((uint32_t)t % ipu32) * (2 * kBM) + rank * kBM + rloc;
             const bool valid = (long long)row < p.M;
             float* o = stage_out_row(p, u, row);
+            // 16-byte stores through the warp's staging block (see the windowed path)
+            const uint32_t row4 = ((uint32_t)t % ipu32) * (2 * kBM) + rank * kBM + wq * 32 + 4 * (lane & 7);
+            float* o4 = vec_out ? stage_out_row(p, u, row4) : nullptr;
+            float* stg = stage_out + wq * 1024;
             for (int cc = 0; cc < ncc; ++cc) {
                 uint32_t v[32];
                 tmem_ld32(lane_base + (uint32_t)(ab * 256 + cc * 32), v);
@@ -847,7 +851,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kStageThreads, 1)
                 } else {
                     tmem_wait_ld();
                 }
-                if (valid) {
+                if (vec_out) {
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stg[j * 32 + lane] = __uint_as_float(v[j]);
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int cl = 4 * i + (lane >> 3);
+                        const int col = cc * 32 + cl;
+                        const int hc = col >= Np ? 1 : 0;
+                        const int y = col - hc * Np;
+                        const float4 v4 = *reinterpret_cast<const float4*>(stg + cl * 32 + 4 * (lane & 7));
+                        if ((long long)row4 + 3 < p.M)
+                            *reinterpret_cast<float4*>(o4 + hc * p.map.SC + (long long)y * p.map.SY) = v4;
+                    }
+                } else if (valid) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int col = cc * 32 + j;
@@ -1429,9 +1448,10 @@ __global__ void k_build_vO32(int N, int Np, const double* __restrict__ v, float*
 //     trapezoid weight of history point k0 + u / 2:
 //       (c2, c) = (0, 0): Re, (0, 1): -Im, (1, 0): Im, (1, 1): Re of coef_u Gb_u[b][j2].
 // A thread owns one K (in the N basis) and kXsA consecutive a; the rows are
-// split over blockIdx.z.  Products and short runs are FP32 (X3 is FP32), every
-// kXsFlush rows the run is added into an FP64 sum, and the block's sums go to
-// out by FP64 atomics.
+// split over blockIdx.z.  Products and the runs of one staged round (64 rows)
+// are FP32 (X3 is FP32), each round is added into an FP64 sum, and the
+// block's sums go to out (FP64 atomics when several blocks along z share an
+// output).
 struct XSlotParams {
     int N, Np, nb;
     long long Rld;         // rows of the K-blocked X3 layout
@@ -1449,10 +1469,37 @@ struct XSlotParams {
 };
 constexpr int kXsA = 32;       // a per thread (blockIdx.y picks the range)
 constexpr int kXsRows = 64;    // rows of weights staged in shared memory at a time
-constexpr int kXsFlush = 256;  // FP32 run length before the FP64 sum
 constexpr int kXsThreads = 128;
-__global__ void __launch_bounds__(kXsThreads) k_xslot_tc(const XSlotParams p) {
+// The per-row weights of k_xslot_tc, once per launch: W[R][a] (R the compact
+// row (u, c, b), a < A), FP32.
+__global__ void k_xslot_weights(const XSlotParams p, float* __restrict__ W) {
+    const int N = p.N;
+    const long long NN = (long long)N * N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long Rtot = 2LL * N * p.nb;
+    if (e >= Rtot * p.A) return;
+    const uint32_t Rc = (uint32_t)(e / p.A);
+    const int a = (int)(e - (long long)Rc * p.A);
+    const uint32_t uc = Rc / (uint32_t)N;
+    const int b = (int)(Rc - uc * (uint32_t)N), u = (int)(uc >> 1), cc = (int)(uc & 1);
+    float val;
+    if (p.mode == 0) {
+        const double2 sv = p.transposeS ? p.S[u * NN + (long long)b * N + a] : p.S[u * NN + (long long)a * N + b];
+        val = (float)(cc ? sv.y : sv.x);
+    } else {
+        const int c2 = a / N, j2 = a % N;
+        const double2 g = p.S[u * NN + (long long)b * N + j2];
+        const double wt = (p.k0 + u / 2 == 0) ? p.w_first : p.w_rest;
+        const double coef = (u & 1) ? wt : -wt;
+        const double re = coef * g.x, im = coef * g.y;
+        val = (float)(c2 == 0 ? (cc == 0 ? re : -im) : (cc == 0 ? im : re));
+    }
+    W[e] = val;
+}
+
+__global__ void __launch_bounds__(kXsThreads, 2) k_xslot_tc(const XSlotParams p, const float* __restrict__ W) {
     __shared__ float sW[kXsRows][kXsA];
+    __shared__ long long sOff[kXsRows];  // X3 offset of each staged row
     const int N = p.N, Np = p.Np;
     const long long NN = (long long)N * N, N3 = NN * N;
     const long long Np3 = (long long)Np * Np * Np;
@@ -1469,64 +1516,65 @@ __global__ void __launch_bounds__(kXsThreads) k_xslot_tc(const XSlotParams p) {
     float acc[kXsA];
     double sum[kXsA];
 #pragma unroll
-    for (int t = 0; t < kXsA; ++t) {
-        acc[t] = 0.0f;
-        sum[t] = 0.0;
-    }
-    int run = 0;
+    for (int t = 0; t < kXsA; ++t) sum[t] = 0.0;
     for (long long rs = R0; rs < R1; rs += kXsRows) {
         const int nrow = (int)(R1 - rs < kXsRows ? R1 - rs : kXsRows);
         __syncthreads();
         for (int e = threadIdx.x; e < kXsRows * kXsA; e += kXsThreads) {
             const int rr = e / kXsA, aa = e % kXsA, a = a0 + aa;
             float val = 0.0f;
-            if (rr < nrow && a < p.A) {
-                const long long Rc = rs + rr, uc = Rc / N;
-                const int b = (int)(Rc % N), u = (int)(uc >> 1), cc = (int)(uc & 1);
-                if (p.mode == 0) {
-                    const double2 sv = p.transposeS ? p.S[u * NN + (long long)b * N + a]
-                                                    : p.S[u * NN + (long long)a * N + b];
-                    val = (float)(cc ? sv.y : sv.x);
-                } else {
-                    const int c2 = a / N, j2 = a % N;
-                    const double2 g = p.S[u * NN + (long long)b * N + j2];
-                    const double wt = (p.k0 + u / 2 == 0) ? p.w_first : p.w_rest;
-                    const double coef = (u & 1) ? wt : -wt;
-                    const double re = coef * g.x, im = coef * g.y;
-                    val = (float)(c2 == 0 ? (cc == 0 ? re : -im) : (cc == 0 ? im : re));
+            if (rr < nrow) {
+                const long long R = rs + rr;
+                if (aa == 0) {
+                    // compact row (u, c, b) of X3; rows stay below 2^31 (host-checked)
+                    const uint32_t Rc = (uint32_t)R, uc = Rc / (uint32_t)N;
+                    sOff[rr] = ((long long)uc * Np + (int)(Rc - uc * (uint32_t)N)) * xstride;
                 }
+                if (a < p.A) val = W[R * p.A + a];
+            } else if (aa == 0) {
+                sOff[rr] = 0;
             }
             sW[rr][aa] = val;
         }
         __syncthreads();
         if (kok) {
-            long long uc = rs / N;
-            int b = (int)(rs % N);
-            for (int rr = 0; rr < nrow; ++rr) {
-                const float x = xk[(uc * Np + b) * xstride];
+            // one staged round (<= 64 rows) in FP32, then into the FP64 sums;
+            // the loads of four rows are issued together
 #pragma unroll
-                for (int t = 0; t < kXsA; ++t) acc[t] = fmaf(sW[rr][t], x, acc[t]);
-                if (++b == N) {
-                    b = 0;
-                    ++uc;
-                }
-                if (++run == kXsFlush) {
-                    run = 0;
+            for (int t = 0; t < kXsA; ++t) acc[t] = 0.0f;
+            int rr = 0;
+            for (; rr + 4 <= nrow; rr += 4) {
+                const float x0 = xk[sOff[rr]], x1 = xk[sOff[rr + 1]], x2 = xk[sOff[rr + 2]],
+                            x3 = xk[sOff[rr + 3]];
 #pragma unroll
-                    for (int t = 0; t < kXsA; ++t) {
-                        sum[t] += (double)acc[t];
-                        acc[t] = 0.0f;
-                    }
+                for (int t = 0; t < kXsA; ++t) {
+                    float v = fmaf(sW[rr][t], x0, acc[t]);
+                    v = fmaf(sW[rr + 1][t], x1, v);
+                    v = fmaf(sW[rr + 2][t], x2, v);
+                    acc[t] = fmaf(sW[rr + 3][t], x3, v);
                 }
             }
+            for (; rr < nrow; ++rr) {
+                const float x = xk[sOff[rr]];
+#pragma unroll
+                for (int t = 0; t < kXsA; ++t) acc[t] = fmaf(sW[rr][t], x, acc[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < kXsA; ++t) sum[t] += (double)acc[t];
         }
     }
     if (!kok) return;
     const long long ko = n * p.SN + r * p.SR + pp;
+    // one block along z: this thread owns its outputs (plain adds); else the
+    // blocks of a column share them (FP64 atomics)
+    const bool own = gridDim.z == 1;
 #pragma unroll
     for (int t = 0; t < kXsA; ++t) {
         const int a = a0 + t;
-        if (a < p.A) atomicAdd(p.out + (a % N) * p.SJ + (a / N) * p.SC + ko, sum[t] + (double)acc[t]);
+        if (a >= p.A) continue;
+        double* o = p.out + (a % N) * p.SJ + (a / N) * p.SC + ko;
+        if (own) *o += sum[t];
+        else atomicAdd(o, sum[t]);
     }
 }
 
@@ -1541,19 +1589,24 @@ __global__ void k_tl_ucal2(int N, const double2* __restrict__ W, double2* __rest
     out[NN + e] = w;
 }
 
-// Lambda (FP64, N basis, [j][n][r][c][p]) to FP32 in the Np basis, zero padded.
+// Lambda (FP64, N basis, [j][n][r][c][p]) to FP32 in the Np basis, zero
+// padded: one warp per row (j, n, r, c), its lanes over p (one index
+// decomposition per row instead of per element).
 __global__ void k_tl_lam32(int N, int Np, const double* __restrict__ lam, float* __restrict__ out) {
-    const long long Npl = Np;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * Npl * Npl * Npl * Npl) return;
-    const int pp = (int)(e % Np), cc = (int)((e / Np) % 2), r = (int)((e / (2 * Npl)) % Np),
-              n = (int)((e / (2 * Npl * Npl)) % Np), j = (int)(e / (2 * Npl * Npl * Npl));
-    float x = 0.0f;
-    if (pp < N && r < N && n < N && j < N) {
-        const long long Nl = N;
-        x = (float)lam[(((j * Nl + n) * Nl + r) * 2 + cc) * Nl + pp];
-    }
-    out[e] = x;
+    const long long rows = 2LL * Np * Np * Np;
+    const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const int lane = threadIdx.x & 31;
+    const int cc = (int)(row & 1);
+    long long q = row >> 1;
+    const int r = (int)(q % Np);
+    q /= Np;
+    const int n = (int)(q % Np);
+    const int j = (int)(q / Np);
+    float* o = out + row * Np;
+    const bool in = j < N && n < N && r < N;
+    const double* l = lam + ((((long long)j * N + n) * N + r) * 2 + cc) * N;
+    for (int pp = lane; pp < Np; pp += 32) o[pp] = (in && pp < N) ? (float)l[pp] : 0.0f;
 }
 
 // Per-unit B operands of the tensor-core path (padded to Np, zero padding),
@@ -1640,9 +1693,8 @@ constexpr int kMaxTcNp = 96;  // largest padded basis of the tensor-core path
 // Shared memory of a stage launch with `astages` A stages.
 size_t stage_smem_bytes(int Np, int astages) {
     const int kch = (Np + kKC - 1) / kKC;
-    // windowed mode (2 Np <= 96) adds the epilogue's 4 x 4 KB staging blocks
-    return 1024 + 2ull * kch * (2 * Np * 128) + (size_t)astages * kTileBytes + 512 +
-           (2 * Np <= 96 ? 4 * 32 * 32 * 4 : 0);
+    // plus the epilogue's 4 x 4 KB staging blocks
+    return 1024 + 2ull * kch * (2 * Np * 128) + (size_t)astages * kTileBytes + 512 + 4 * 32 * 32 * 4;
 }
 // The most A stages that fit next to the B operand (at least 4).
 int stage_astages(int Np) {
@@ -2121,6 +2173,7 @@ static gkba_status xslot_launch(gkba_ctx* c, int nb, XSlotParams xp, int cls, do
     xp.blocked = (Np % 32) == 0 ? 1 : 0;
     xp.X = (const float*)c->X13;
     const long long Rtot = 2LL * N * nb;
+    if (Rtot >= (1LL << 31)) return fail(c, GKBA_EINVAL, "slot contraction of %d units: too many rows", nb);
     const unsigned gx = grid1(N3, kXsThreads), gy = (unsigned)((xp.A + kXsA - 1) / kXsA);
     // enough blocks for about eight per SM, each over at least 1024 rows
     long long gz = std::max(1LL, std::min((Rtot + 1023) / 1024,
@@ -2128,8 +2181,22 @@ static gkba_status xslot_launch(gkba_ctx* c, int nb, XSlotParams xp, int cls, do
     const long long per = ((Rtot + gz - 1) / gz + kXsRows - 1) / kXsRows * kXsRows;
     gz = (Rtot + per - 1) / per;
     xp.rows_per_z = per;
-    auto t = launch_begin(c, cls, 2.0 * (double)N3 * xp.A * Rtot, bytes);
-    k_xslot_tc<<<dim3(gx, gy, (unsigned)gz), kXsThreads, 0, c->stream>>>(xp);
+    const size_t wbytes = (size_t)Rtot * xp.A * sizeof(float);
+    if (wbytes > c->xsw_bytes) {
+        if (c->xsw) cudaFree(c->xsw);
+        c->xsw = nullptr;
+        c->xsw_bytes = 0;
+        if (cudaMalloc(&c->xsw, wbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GKBA_ENOMEM, "slot contraction weights (%zu bytes) do not fit", wbytes);
+        }
+        c->xsw_bytes = wbytes;
+    }
+    auto t = launch_begin(c, K_PREP, 0.0, 0.0);
+    k_xslot_weights<<<grid1(Rtot * xp.A, 256), 256, 0, c->stream>>>(xp, c->xsw);
+    GKBA_TRY(launch_end(c, t));
+    t = launch_begin(c, cls, 2.0 * (double)N3 * xp.A * Rtot, bytes);
+    k_xslot_tc<<<dim3(gx, gy, (unsigned)gz), kXsThreads, 0, c->stream>>>(xp, c->xsw);
     return launch_end(c, t);
 }
 
@@ -2212,7 +2279,7 @@ gkba_status tl_apply_tf32(gkba_ctx* c, const double2* W, const double* lam) {
     float* X2 = (float*)c->X2;
     float* X13 = (float*)c->X13;
     t = launch_begin(c, K_PREP, 0.0, 0.0);
-    k_tl_lam32<<<grid1(2 * N4, 256), 256, 0, c->stream>>>(N, Np, lam, X2);
+    k_tl_lam32<<<grid1(2 * N3, 8), 256, 0, c->stream>>>(N, Np, lam, X2);  // 8 rows per block
     GKBA_TRY(launch_end(c, t));
     GKBA_TRY(tl_stage(c, X2, 0, X13, StageMap{2 * N3, 2 * N2, 1, Np, 2 * Np, Np, Np, Np}, 2 * N4));
     GKBA_TRY(tl_stage(c, X13, 1, X2, StageMap{2 * N3, 1, 2 * Np, Np, 2 * N2, Np, Np, Np}, 2 * N4));
