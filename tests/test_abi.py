@@ -128,6 +128,8 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert st == gkba.EINVAL and out.value is None
     assert b"NULL" in lib.gkba_batch_last_error(None)
     assert lib.gkba_batch_step(None, None, None, None, None) == gkba.EINVAL
+    assert lib.gkba_batch_set_options(None, 1) == gkba.EINVAL
+    assert lib.gkba_batch_autotune(None, None, None, None, None, None, None) == gkba.EINVAL
     lib.gkba_batch_destroy(None)
     assert lib.gkba_selftest_timeout(None, 10.0, None) == gkba.EINVAL
     # gradients and the trilinear form: NULL context or arrays are refused on the host
