@@ -944,11 +944,14 @@ struct FinalLaunch {
 // hi*hi products after them, so the only truncations at the scale of the
 // result are those of the four hi*hi MMAs.
 //
-// Tensor memory (512 columns, same address in both CTAs): three A slots (hi
-// in 32 columns, lo in the next 32) at 0, 64 and 128, so the converter works
-// up to two chunks ahead of the MMAs; three window accumulators of AS = Np
-// rounded up to 32 columns at 192 + b AS.  Chunk c uses slot and window
-// c mod 3.
+// Tensor memory (512 columns, same address in both CTAs): two A slots (hi
+// in 32 columns, lo in the next 32) at 0 and 64, so the converter works one
+// chunk ahead of the MMAs; four window accumulators of AS = Np rounded up to
+// 32 columns at 128 + w AS, so the MMAs run up to three windows ahead of the
+// epilogue.  Chunk c uses A slot c mod 2 and window c mod 4.  (Three slots
+// sharing one index with three windows coupled the converter and the
+// epilogue more tightly: per-role clock counters showed the MMA warp waiting
+// on both.)
 //
 // Warps: 0 TMA producer, 1 MMA issuer (even CTA; the whole warp, one elected
 // lane issues), 4-7 converter, and eight epilogue warps, two per tensor-
@@ -962,17 +965,18 @@ struct FinalLaunch {
 //                the chunk's MMAs are done (they read A, the MMAs read B);
 //   TFULL[slot]  the slot's hi / lo are in tensor memory (4 converter warps of
 //                each CTA arrive on the even CTA's barrier);
-//   DONE[slot]   one multicast commit per chunk once its MMAs are done: the
-//                window is full (epilogue), the slot and the stage's B are free
-//                (converter);
-//   WE[slot]     the window was drained (8 epilogue warps of each CTA).
+//   DONE[win]    one multicast commit per chunk once its MMAs are done: the
+//                window is full (epilogue); for chunk c the converter of chunk
+//                c + 2 reads it as "A slot and stage B of chunk c are free";
+//   WE[win]      the window was drained (8 epilogue warps of each CTA).
 // One commit per chunk: each tcgen05.commit costs the tensor pipe about 130
 // clocks (measured), a quarter of the chunk's MMA time.
 // ---------------------------------------------------------------------------
 constexpr int kFinPairStages = 8;
 constexpr int kFinKC = kKC;      // K per pipeline chunk and window: one 32-wide TMA box
 constexpr int kFinMaxNp = 96;
-constexpr int kFinSlots = 3;     // A (hi, lo) slots and window accumulators in tensor memory
+constexpr int kFinSlots = 2;     // A (hi, lo) slots in tensor memory
+constexpr int kFinWins = 4;      // window accumulators in tensor memory
 constexpr uint32_t kFinWinCol = 64u * kFinSlots;  // first window accumulator column
 constexpr int kFinEpiWarps = 8;
 
@@ -1003,7 +1007,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
     const uint32_t stage_bytes = kTileBytes + 2 * bbytes;  // A, Bhi, Blo
     uint64_t* bars = (uint64_t*)(smem + kFinPairStages * stage_bytes);
     constexpr int FULL = 0, EMPTY = FULL + kFinPairStages, TFULL = EMPTY + kFinPairStages,
-                  DONE = TFULL + kFinSlots, WE = DONE + kFinSlots, DRAIN = WE + kFinSlots,
+                  DONE = TFULL + kFinSlots, WE = DONE + kFinWins, DRAIN = WE + kFinWins,
                   NBARS = DRAIN + 1;
     uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -1021,10 +1025,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
             mbar_init(bar(FULL + s), 1);
             mbar_init(bar(EMPTY + s), 4);  // the 4 converter warps
         }
-        for (int s = 0; s < kFinSlots; ++s) {
-            mbar_init(bar(TFULL + s), 8);
-            mbar_init(bar(DONE + s), 1);
-            mbar_init(bar(WE + s), 2 * kFinEpiWarps);
+        for (int s = 0; s < kFinSlots; ++s) mbar_init(bar(TFULL + s), 8);
+        for (int w = 0; w < kFinWins; ++w) {
+            mbar_init(bar(DONE + w), 1);
+            mbar_init(bar(WE + w), 2 * kFinEpiWarps);
         }
         mbar_init(bar(DRAIN), 1);
         *abort_flag = 0;
@@ -1093,22 +1097,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
         if (rank == 0) {
             // ---------------- MMA issuer (even CTA, for the pair; warp-collective) ----------------
             const uint32_t id = idesc_tf32_pair(Np);
-            Ring st(kFinPairStages), sl(kFinSlots);
+            Ring st(kFinPairStages), sl(kFinSlots), sw(kFinWins);
             bool ok = true;
             for (long long item = cid; item < items && ok; item += ncl) {
                 const int ks = (int)(item / p.ngroups);
                 const long long k0 = (long long)ks * p.KW;
                 const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-                for (long long k = k0; k < k1 && ok; k += kFinKC, st.next(), sl.next()) {
-                    const int s = st.i, j = sl.i;
+                for (long long k = k0; k < k1 && ok; k += kFinKC, st.next(), sl.next(), sw.next()) {
+                    const int s = st.i, j = sl.i, w = sw.i;
                     if (!warp_wait_cl(bar(TFULL + j), sl.ph, abort_flag, peer_abort, p.err, 13)) { ok = false; break; }
-                    if (!warp_wait_cl(bar(WE + j), sl.ph ^ 1u, abort_flag, peer_abort, p.err, 12)) { ok = false; break; }
+                    if (!warp_wait_cl(bar(WE + w), sw.ph ^ 1u, abort_flag, peer_abort, p.err, 12)) { ok = false; break; }
                     tc_fence_after();
                     // a 32-byte K step adds 2 to the descriptor's start field
                     const unsigned long long dh = desc_sw128(smem_u32(stBhi(s)));
                     const unsigned long long dl = desc_sw128(smem_u32(stBlo(s)));
                     const uint32_t ahi = tmem + (uint32_t)(j * 64), alo = ahi + 32u;
-                    const uint32_t dw = tmem + kFinWinCol + (uint32_t)j * AS;
+                    const uint32_t dw = tmem + kFinWinCol + (uint32_t)w * AS;
                     // correction products first (the window starts from zero), then hi*hi
                     mma_tf32_pair(dw, ahi, dl, id, 0u);
                     mma_tf32_pair(dw, alo, dh, id, 1u);
@@ -1122,7 +1126,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                     mma_tf32_pair(dw, ahi + 8, dh + 2, id, 1u);
                     mma_tf32_pair(dw, ahi + 16, dh + 4, id, 1u);
                     mma_tf32_pair(dw, ahi + 24, dh + 6, id, 1u);
-                    mma_commit_pair(bar(DONE + j), (uint16_t)3);
+                    mma_commit_pair(bar(DONE + w), (uint16_t)3);
                 }
             }
             // closing commit: no CTA leaves while an MMA reads its memory
@@ -1138,11 +1142,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
         // Software-pipelined: the tensor-memory stores of chunk c complete
         // (tcgen05.wait::st, then TFULL) while chunk c + 1 is read and split,
         // unless chunk c + 1 has not landed yet.  A chunk's stage is released
-        // (EMPTY) once its MMAs are done, observed when its slot is reused.
+        // (EMPTY) once its MMAs are done, observed when its A slot is reused
+        // two chunks later (DONE of its window).
         const int wq = warp & 3;
         const int r = wq * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
-        Ring st(kFinPairStages), sl(kFinSlots), rel(kFinPairStages);
+        Ring st(kFinPairStages), sl(kFinSlots), rel(kFinPairStages), dn(kFinWins);
         long long it = 0;
         bool ok = true;
         int pend = -1;  // slot whose stores were issued but not yet waited for
@@ -1167,9 +1172,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                 load_split_row(stA(s), r, hi, lo);
                 finish_pending();
                 const int j = sl.i;
-                // the slot (and chunk c - 3's stage) is free once chunk c - 3's MMAs are done
-                if (!warp_wait_cl(bar(DONE + j), sl.ph ^ 1, abort_flag, peer_abort, p.err, 15)) { ok = false; break; }
+                // the slot (and chunk c - 2's stage) is free once chunk c - 2's MMAs
+                // are done: the DONE of chunk c - 2's window (dn trails by two chunks)
                 if (it >= kFinSlots) {
+                    if (!warp_wait_cl(bar(DONE + dn.i), dn.ph, abort_flag, peer_abort, p.err, 15)) { ok = false; break; }
+                    dn.next();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar(EMPTY + rel.i));
                     rel.next();
@@ -1191,7 +1198,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
         const int cw = Np / 2;                 // columns of this warp: [c0, c0 + cw)
         const int c0 = (epi >> 2) * cw;
         constexpr int kMaxC = kFinMaxNp / 2;   // 48
-        Ring sl(kFinSlots);
+        Ring sl(kFinWins);
         bool ok = true;
         for (long long item = cid; item < items && ok; item += ncl) {
             const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
