@@ -292,7 +292,7 @@ def run_chains(a):
     (1) Hubbard chain, diagonal basis, 5000 x 0.01; (2) Ohno chain, symmetric
     basis, 2000 x 0.025; (3) general basis (the seeded stand-in for the CH4
     integrals, 2 occupied orbitals), 1000 x 0.05, also with the time-linear
-    history (FP64).  One JSON line per run; the paper's single-core CPU times
+    history (FP64 and split-TF32).  One JSON line per run; the paper's single-core CPU times
     (Table I, tensor-contraction column) are context, not a target."""
     import torch
     import gkba_inputs as gi
@@ -303,7 +303,8 @@ def run_chains(a):
              ("ohno_chain_N10", "symmetric", 0.025, 2000, "fp64", "sum", 731.0),
              ("general_basis_N10", "general", 0.05, 1000, "fp64", "sum", 1333.0),
              ("general_basis_N10", "general", 0.05, 1000, "tf32acc", "sum", 1333.0),
-             ("general_basis_N10", "general", 0.05, 1000, "fp64", "time_linear", 1333.0)]
+             ("general_basis_N10", "general", 0.05, 1000, "fp64", "time_linear", 1333.0),
+             ("general_basis_N10", "general", 0.05, 1000, "tf32", "time_linear", 1333.0)]
     for name, kind, dt, n, prec, history, paper in cases:
         s = gi.system(10, 8, seed=0) if kind == "general" else gi.chain(10, kind)
         ctx = P.Context(s["h"], s["v"], s["d"], s["rho0"], dt, max_steps=n, precision=prec,
