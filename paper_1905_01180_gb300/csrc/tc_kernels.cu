@@ -11,12 +11,14 @@
 // real GEMM D[M][Nc] = sum_K A[M][K] B[Nc][K]:
 //   * A (the large, streamed operand) is FP32 in HBM; TMA stages 128 x 32
 //     tiles (128-byte swizzle) in shared memory, a converter warpgroup splits
-//     every element into TF32 hi and lo (x = hi + lo, see split_tf32) and
-//     writes both into tensor memory (tcgen05.st), where the MMA reads A;
+//     every element into TF32 hi and lo (x = hi + lo, see split_tf32 and, for
+//     S4, split_tf32_exact_lo) and writes both into tensor memory
+//     (tcgen05.st), where the MMA reads A;
 //   * B (the small per-unit matrix, or v for S4) is stored pre-split hi/lo;
 //   * each K-step issues hi*hi + hi*lo + lo*hi (3xTF32) into an FP32 TMEM
-//     accumulator; S4 is split over K in chunks (default 512) whose FP32 partial
-//     sums are added by the reduction kernel.
+//     accumulator; S4 accumulates every 32-wide K chunk in its own window,
+//     adds the windows of a work item (4096 K by default) with Kahan in FP32
+//     registers, and the reduction kernel adds the items' partial sums.
 // S1-S3 run on CTA pairs (cta_group::2, M = 256): B's rows are split between
 // the two CTAs' shared memory, which leaves room for the complex B' that
 // turns the planar (Re, Im) halves of A into one real K range:
@@ -297,6 +299,37 @@ __device__ __forceinline__ void load_split_row(const uint8_t* tile, int r, uint3
         split_tf32(v.y, hi[4 * j + 1], lo[4 * j + 1]);
         split_tf32(v.z, hi[4 * j + 2], lo[4 * j + 2]);
         split_tf32(v.w, hi[4 * j + 3], lo[4 * j + 3]);
+    }
+}
+
+// The split of the last contraction's streamed operand, on full-rate integer
+// and FP32 instructions only (the conversion instruction issues at a fraction
+// of that rate, and this split bounded the S4 converter):
+//   hi = x rounded to TF32, to nearest with ties away from zero: half a TF32
+//        ulp (bit 12) added to the sign-magnitude bits, the 13 dropped bits
+//        cleared (a carry out of the mantissa moves into the exponent, which
+//        is the rounded value at a binade boundary); bit-identical to
+//        cvt.rna.tf32.f32 for every finite x;
+//   lo = x - hi, exact in FP32 (x and hi are within a factor of two), passed
+//        unrounded: the MMA reads its leading 11 bits, so |x - hi - lo_mma| <
+//        2^-22 |x|.  The sign of lo is that of the rounding of hi, not of x,
+//        so this truncation adds no coherent bias to the product.
+// A non-finite x gives a NaN lo (inf - inf, NaN - anything), so it reaches the
+// sum as a NaN, as with the rounded split.
+__device__ __forceinline__ void split_tf32_exact_lo(float x, uint32_t& hi, uint32_t& lo) {
+    hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void load_split_row_exact_lo(const uint8_t* tile, int r, uint32_t (&hi)[32],
+                                                        uint32_t (&lo)[32]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 v = *reinterpret_cast<const float4*>(tile + r * 128 + ((j ^ (r & 7)) << 4));
+        split_tf32_exact_lo(v.x, hi[4 * j + 0], lo[4 * j + 0]);
+        split_tf32_exact_lo(v.y, hi[4 * j + 1], lo[4 * j + 1]);
+        split_tf32_exact_lo(v.z, hi[4 * j + 2], lo[4 * j + 2]);
+        split_tf32_exact_lo(v.w, hi[4 * j + 3], lo[4 * j + 3]);
     }
 }
 
@@ -927,8 +960,10 @@ struct FinalLaunch {
 // Work item = (256-row group g: one 128-row tile per CTA, a K range of KW).
 // Per 32-wide K chunk each CTA stages its A box and its Np/2 rows of vK (hi
 // and lo) in one of eight pipeline stages; a converter warpgroup splits the A
-// box into TF32 hi and lo in the CTA's tensor memory; the MMA warp of the even
-// CTA issues M = 256, N = Np MMAs for the pair.
+// box into TF32 hi and lo in the CTA's tensor memory (split_tf32_exact_lo:
+// full-rate instructions only, the split with the conversion instruction
+// bounded this stage); the MMA warp of the even CTA issues M = 256, N = Np
+// MMAs for the pair.
 //
 // Accuracy: the tensor core truncates its FP32 accumulator additions toward
 // zero.  Over the N^3-long sum of this stage that bias is not uniform: it
@@ -985,6 +1020,35 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                  : W8(v, 0)
                  : "r"(taddr)
                  : "memory");
+}
+
+// Packed FP32 pairs (sm_100 family): one add.f32x2 / sub.f32x2 performs two
+// independent round-to-nearest FP32 operations, so the Kahan update of two
+// columns takes the issue slots of one (bitwise the scalar update on each).
+__device__ __forceinline__ unsigned long long f2_pack(uint32_t a, uint32_t b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long x, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// Kahan: sum + cmp carries the exact running sum to about 2 ulp
+__device__ __forceinline__ void kahan2(unsigned long long& sum, unsigned long long& cmp, unsigned long long v) {
+    const unsigned long long y = f2_sub(v, cmp);
+    const unsigned long long t = f2_add(sum, y);
+    cmp = f2_sub(f2_sub(t, sum), y);
+    sum = t;
 }
 
 template <bool GROUPED>
@@ -1169,7 +1233,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                 if (pend >= 0 && !__all_sync(0xffffffffu, mbar_try(bar(FULL + s), st.ph))) finish_pending();
                 if (!warp_wait_cl(bar(FULL + s), st.ph, abort_flag, peer_abort, p.err, 14)) { ok = false; break; }
                 uint32_t hi[32], lo[32];
-                load_split_row(stA(s), r, hi, lo);
+                load_split_row_exact_lo(stA(s), r, hi, lo);
                 finish_pending();
                 const int j = sl.i;
                 // the slot (and chunk c - 2's stage) is free once chunk c - 2's MMAs
@@ -1204,9 +1268,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
             const int g = (int)(item % p.ngroups), ks = (int)(item / p.ngroups);
             const long long k0 = (long long)ks * p.KW;
             const long long k1 = k0 + p.KW < p.K ? k0 + p.KW : p.K;
-            float sum[kMaxC], cmp[kMaxC];
+            // column pairs (2 i, 2 i + 1) packed in one 64-bit register each
+            unsigned long long sum[kMaxC / 2], cmp[kMaxC / 2];
 #pragma unroll
-            for (int j = 0; j < kMaxC; ++j) sum[j] = cmp[j] = 0.0f;
+            for (int j = 0; j < kMaxC / 2; ++j) sum[j] = cmp[j] = 0ull;
             for (long long kw = k0; kw < k1; kw += kFinKC, sl.next()) {
                 const int b = sl.i;
                 if (!warp_wait_cl(bar(DONE + b), sl.ph, abort_flag, peer_abort, p.err, 16)) { ok = false; break; }
@@ -1220,13 +1285,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                         tmem_ld16(col + (uint32_t)(q * 16), v);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            // Kahan: sum + cmp carries the exact running sum to ~2 ulp
-                            const float y = __uint_as_float(v[j]) - cmp[q * 16 + j];
-                            const float t = sum[q * 16 + j] + y;
-                            cmp[q * 16 + j] = (t - sum[q * 16 + j]) - y;
-                            sum[q * 16 + j] = t;
-                        }
+                        for (int j = 0; j < 8; ++j)
+                            kahan2(sum[q * 8 + j], cmp[q * 8 + j], f2_pack(v[2 * j], v[2 * j + 1]));
                     }
                 }
                 if (cw & 8) {
@@ -1234,15 +1294,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
                     tmem_ld8(col + (uint32_t)(cw - 8), v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < 4; ++j) {
 #pragma unroll
                         for (int q = 0; q < kMaxC / 8; ++q) {
-                            if (q * 8 == cw - 8) {
-                                const float y = __uint_as_float(v[j]) - cmp[q * 8 + j];
-                                const float t = sum[q * 8 + j] + y;
-                                cmp[q * 8 + j] = (t - sum[q * 8 + j]) - y;
-                                sum[q * 8 + j] = t;
-                            }
+                            if (q * 8 == cw - 8)
+                                kahan2(sum[q * 4 + j], cmp[q * 4 + j], f2_pack(v[2 * j], v[2 * j + 1]));
                         }
                     }
                 }
@@ -1254,8 +1310,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFinThreads, 1)
             float* base = p.part + (long long)ks * Np * p.Rld;
             const long long row = (long long)g * 2 * kBM + (long long)rank * kBM + rloc;
 #pragma unroll
-            for (int j = 0; j < kMaxC; ++j)
-                if (j < cw) base[(long long)(c0 + j) * p.Rld + row] = sum[j];
+            for (int j = 0; j < kMaxC / 2; ++j) {
+                if (2 * j < cw) {
+                    float a, b;
+                    f2_unpack(sum[j], a, b);
+                    base[(long long)(c0 + 2 * j) * p.Rld + row] = a;
+                    base[(long long)(c0 + 2 * j + 1) * p.Rld + row] = b;
+                }
+            }
         }
     }
     tc_fence_before();
