@@ -33,6 +33,7 @@
 #include <cstdlib>
 
 #include "gkba_internal.cuh"
+#include "tf32_round.h"
 
 namespace gkba {
 
@@ -305,10 +306,8 @@ __device__ __forceinline__ void load_split_row(const uint8_t* tile, int r, uint3
 // The split of the last contraction's streamed operand, on full-rate integer
 // and FP32 instructions only (the conversion instruction issues at a fraction
 // of that rate, and this split bounded the S4 converter):
-//   hi = x rounded to TF32, to nearest with ties away from zero: half a TF32
-//        ulp (bit 12) added to the sign-magnitude bits, the 13 dropped bits
-//        cleared (a carry out of the mantissa moves into the exponent, which
-//        is the rounded value at a binade boundary); bit-identical to
+//   hi = x rounded to TF32, to nearest with ties away from zero, on integer
+//        instructions (tf32_rna_bits, tf32_round.h); bit-identical to
 //        cvt.rna.tf32.f32 for every finite x;
 //   lo = x - hi, exact in FP32 (x and hi are within a factor of two), passed
 //        unrounded: the MMA reads its leading 11 bits, so |x - hi - lo_mma| <
@@ -317,7 +316,7 @@ __device__ __forceinline__ void load_split_row(const uint8_t* tile, int r, uint3
 // A non-finite x gives a NaN lo (inf - inf, NaN - anything), so it reaches the
 // sum as a NaN, as with the rounded split.
 __device__ __forceinline__ void split_tf32_exact_lo(float x, uint32_t& hi, uint32_t& lo) {
-    hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+    hi = tf32_rna_bits(__float_as_uint(x));
     lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
