@@ -310,9 +310,12 @@ __device__ __forceinline__ void load_split_row(const uint8_t* tile, int r, uint3
 //        instructions (tf32_rna_bits, tf32_round.h); bit-identical to
 //        cvt.rna.tf32.f32 for every finite x;
 //   lo = x - hi, exact in FP32 (x and hi are within a factor of two), passed
-//        unrounded: the MMA reads its leading 11 bits, so |x - hi - lo_mma| <
-//        2^-22 |x|.  The sign of lo is that of the rounding of hi, not of x,
-//        so this truncation adds no coherent bias to the product.
+//        unrounded: the MMA reads its leading 11 bits.  lo is a multiple of
+//        x's ulp no larger than half a TF32 ulp of x, so it has at most 12
+//        significant bits and the MMA drops at most the last one, the bit a
+//        rounding of lo would round away: |x - hi - lo_mma| <= 2^-23 |x|, as
+//        with a rounded lo.  The sign of lo is that of the rounding of hi,
+//        not of x, so this truncation adds no coherent bias to the product.
 // A non-finite x gives a NaN lo (inf - inf, NaN - anything), so it reaches the
 // sum as a NaN, as with the rounded split.
 __device__ __forceinline__ void split_tf32_exact_lo(float x, uint32_t& hi, uint32_t& lo) {

@@ -10,6 +10,7 @@ import re
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -36,3 +37,38 @@ def test_tf32_rounding_and_split_exhaustive(tmp_path):
     # only |x| >= (2 - 2^-11) 2^127 rounds past the largest TF32 value:
     # 2^12 mantissa patterns of the top binade, both signs
     assert vals["overflow_to_inf"] == 2 * 4096, out
+
+
+def _tf32_rna(u):
+    # the header's expression on uint32 arrays (its exhaustive check is above)
+    return (u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
+
+
+def test_split_error_bound_and_no_coherent_bias():
+    # The tensor core reads a TF32 operand's leading bits, i.e. it truncates
+    # the unrounded lo = x - hi to TF32.  Under that model the represented
+    # value hi + trunc(lo) is within 2^-23 |x| of x (lo has at most 12
+    # significant bits, the MMA drops at most the last), and since lo's sign
+    # follows the rounding direction of hi (not the sign of x) the error has
+    # no coherent sign: its mean relative to x vanishes, where a split that
+    # truncates hi itself shrinks x by about 0.3 x 2^-22 on average.
+    rng = np.random.default_rng(0)
+    n = 1 << 22
+    # normal FP32 values of both signs over a wide exponent range, random mantissas
+    x = (rng.uniform(1.0, 2.0, n) * np.exp2(rng.integers(-60, 60, n))).astype(np.float32)
+    x *= np.where(rng.random(n) < 0.5, -1.0, 1.0).astype(np.float32)
+    u = x.view(np.uint32)
+    hi = _tf32_rna(u).view(np.float32)
+    lo = (x - hi).astype(np.float32)
+    assert np.array_equal(hi.astype(np.float64) + lo.astype(np.float64), x.astype(np.float64))
+    lo_mma = (lo.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    rel = (x.astype(np.float64) - hi - lo_mma) / np.abs(x.astype(np.float64))
+    assert np.abs(rel).max() <= 2.0 ** -23
+    # signed error toward zero, relative to |x|: positive = shrink
+    shrink = rel * np.sign(x.astype(np.float64))
+    # the truncating split for comparison: hi = trunc(x), lo = x - hi, lo truncated
+    hi_t = (u & np.uint32(0xFFFFE000)).view(np.float32)
+    lo_t = ((x - hi_t).astype(np.float32).view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    shrink_t = (x.astype(np.float64) - hi_t - lo_t) / np.abs(x.astype(np.float64)) * np.sign(x)
+    assert shrink_t.mean() > 0.25 * 2.0 ** -22                 # coherent shrink
+    assert abs(shrink.mean()) < 0.01 * shrink_t.mean()         # none for this split
