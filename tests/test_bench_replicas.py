@@ -55,3 +55,31 @@ def test_roofline_traffic_comes_from_the_committed_profiles():
         assert src is not None and src.startswith("k_tc_pair"), stage
         assert 1e9 < t / 2.0 < 3e9  # ~1.33 GB per unit at N = 96 (X in + out)
     assert bench.captured_traffic("no_such_stage", 1.0) == (None, None)
+
+
+def test_reference_arm_line_carries_the_contract_keys():
+    # the reference arm times the CPU oracle on the host cores and prints one
+    # JSON line with the same metric, config and unit as the GPU arm, marked
+    # impl=reference, with its cpu_baseline and an e2e block of zero copies
+    # (a small basis here so that the check takes seconds)
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--N", "6"], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
+    import bench
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "TFLOP/s" and line["higher_is_better"] is True
+    assert line["steps"] == 1 and line["warmup"] == 0 and line["n_gpus"] == 1
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["config"]["N"] == 6 and line["config"]["workload"].startswith("gkba2b_heun_step")
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
